@@ -1,0 +1,484 @@
+#!/usr/bin/env python
+"""Throughput benchmark: degree-6 complex polynomials rooted and binned per second.
+
+Workload: the 2^26 Littlewood-type polynomials (a_0..a_6 i.i.d. in {1,-1,i,-i},
+SplitMix64 seed 2), complex64 coefficient-major, resident in HBM (3.76 GB per
+step, larger than the 129 MB L2, so no L2 flush is needed between steps),
+rooted by single-shift QR on the 6x6 companion matrix and binned into a
+1920x1080 uint32 histogram over [-2,2]x[-1.125,1.125].
+
+One step = clear the histogram and counters + one fused roots+density launch
+over the whole batch. The headline ``value`` is the mixed mode (FP32 sweeps,
+3 FP64 Newton steps, FP64 residual check); the plain FP64 GPU path is timed on
+the same batch and reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) each rank solves its own 2^26 polynomials (weak
+scaling), the per-rank histograms are summed once after the timed region, and
+the time is the maximum over ranks. ``--impl reference`` times the FP64 CPU
+oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "deg-6 complex polys rooted+binned/s, mixed vs plain FP64, ≤1e-9 err; % of peak"
+UNIT = "polys/s"
+SEED = 2
+DEGREE = 6
+WINDOW = (-2.0, 2.0, -1.125, 1.125)
+W_PIX, H_PIX = 1920, 1080
+E2E_CHUNK_LOG2 = 22
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "solve_mixed_littlewood_deg6.md")
+# files that define the timed solve kernel; the ncu traffic figure is valid only for this source
+KERNEL_SOURCES = ["paper_2507_02164_gb300/csrc/rd_solve.cuh", "paper_2507_02164_gb300/csrc/rd_common.cuh",
+                  "paper_2507_02164_gb300/csrc/rd_solve_launch.cuh", "paper_2507_02164_gb300/csrc/rd_solve_mixed.cu"]
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 SMSPs x 32)
+FP64_FMA_PER_SM_CLK = 2   # FP64 FMA per SM per clock: 1.25 TFLOP/s / (152 SMs x 2 flop x 2.07 GHz)
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--log2n", type=int, default=26, help="polynomials per GPU = 2^log2n")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """Per-launch DRAM bytes of the solve kernel from the committed ncu summary,
+    or None when the summary is missing or was taken on other kernel source."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    if not m or not s or s.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while running (the timed region)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        load = [v for v in sm if smax and v >= 0.3 * smax] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_rate(seconds: float, start_index: int = 0):
+    """Oracle solve + histogram on the host cores for about `seconds`; returns
+    (polys/s, threads used, polys done)."""
+    import numpy as np
+
+    import oracle
+    from paper_2507_02164_gb300 import workloads as WL
+    oracle.build()
+    chunk = 1 << 16
+    done, elapsed, threads, k = 0, 0.0, 0, 0
+    while elapsed < seconds:
+        idx = np.arange(start_index + k * chunk, start_index + (k + 1) * chunk, dtype=np.uint64)
+        co = WL.littlewood(SEED, idx).astype(np.complex128)
+        t0 = time.perf_counter()
+        roots, _, _, threads = oracle.solve(co, tol=1e-13)
+        oracle.hist(roots, WINDOW, W_PIX, H_PIX)
+        elapsed += time.perf_counter() - t0
+        done += chunk
+        k += 1
+    return done / elapsed, threads, done
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2507_02164_gb300 import workloads as WL
+    oracle.build()
+    S = 1 << 18
+    times = []
+    threads = 0
+    for step in range(args.warmup + args.steps):
+        idx = np.arange(step * S, (step + 1) * S, dtype=np.uint64)
+        co = WL.littlewood(SEED, idx).astype(np.complex128)
+        t0 = time.perf_counter()
+        roots, _, _, threads = oracle.solve(co, tol=1e-13)
+        oracle.hist(roots, WINDOW, W_PIX, H_PIX)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = S * len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: seeded Littlewood {1,-1,i,-i} degree-6 polynomials (SplitMix64 seed 2)",
+        "config": workload_config(args, ref_sample=S),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{S} polynomials per step (indices step*{S}..), FP64 oracle solve + histogram, "
+                                   f"OpenMP over {threads} host threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, ref_sample=None):
+    cfg = {
+        "workload": f"littlewood-deg6-2^{args.log2n}: a_k in {{1,-1,i,-i}} complex64, fused roots + "
+                    f"{W_PIX}x{H_PIX} uint32 histogram over [-2,2]x[-1.125,1.125]",
+        "polys_per_gpu": 1 << args.log2n,
+        "degree": DEGREE,
+        "mixed": "FP32 QR sweeps (Wilkinson shift, deflation 4*2^-24, <=40 sweeps/root) + 3 FP64 Newton steps "
+                 "+ FP64 residual/separation check",
+        "plain": "FP64 QR sweeps (Wilkinson shift, deflation 1e-13, <=40 sweeps/root)",
+        "l2_flush": "inputs larger than L2 (3.76 GB of coefficients per GPU per step)",
+        "parallelism": f"dp{args.gpus}",
+    }
+    if ref_sample:
+        cfg["reference_sample_per_step"] = ref_sample
+    return cfg
+
+
+# ---------------------------------------------------------------- GPU leg
+
+def algorithmic_flops(st: dict, mode: str):
+    """(FP32 flops, FP64 flops) of one solve launch from its own counters.
+
+    Sweep arithmetic (in the sweep precision): 20 flops per rotated entry pair
+    (real cosine: c x + s y and -conj(s) x + c y), 24 per Givens generation,
+    60 per sweep for shift, unshift, Wilkinson shift and deflation test.
+    Polish (mixed, per Newton step): p(z) by FP64 Horner, 8d + 2 FP64 flops;
+    p'(z) and the step size in FP32, 8d + 3. Final check per root: FP64
+    residual 8d, FP32 denominator 2d + 4. Binning: 4 FP64 flops per root.
+    """
+    d = DEGREE
+    sweep = 20.0 * st["pair_updates"] + 24.0 * st["rotations"] + 60.0 * st["sweeps"]
+    roots = d * st["polys"]
+    if mode == "mixed":
+        f32 = sweep + (8 * d + 3) * st["newton_steps"] + (2 * d + 4) * roots
+        f64 = (8 * d + 2) * st["newton_steps"] + 8 * d * roots + 4 * roots
+    else:
+        f32 = 0.0
+        f64 = sweep + 4 * roots
+    return f32, f64
+
+
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2507_02164_gb300 import api, build, workloads as WL
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n = 1 << args.log2n
+    start = rank * n
+    coeffs = WL.littlewood_soa_torch(SEED, start, n, dev)
+    win = api.Window(*WINDOW)
+    hist = api.new_hist(W_PIX, H_PIX, dev)
+    stats = api.new_stats(dev)
+    stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed_leg(mode: str):
+        p = api.params(mode)
+        k_start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        k_end = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        for _ in range(args.warmup):
+            api.hist_clear(hist)
+            api.hist_clear(stats)
+            api.roots_density(coeffs, win, hist, mode=mode, params_=p, stats=stats)
+        barrier()
+        with ClockSampler(local_rank) as clk:
+            t0.record(stream)
+            for s in range(args.steps):
+                api.hist_clear(hist)
+                api.hist_clear(stats)
+                k_start[s].record(stream)
+                api.roots_density(coeffs, win, hist, mode=mode, params_=p, stats=stats)
+                k_end[s].record(stream)
+            t1.record(stream)
+            torch.cuda.synchronize()
+        elapsed_ms = t0.elapsed_time(t1)
+        kern_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(k_start, k_end))
+        if world > 1:
+            t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            elapsed_ms = float(t.item())
+        st = api.stats_dict(stats)
+        return elapsed_ms, kern_ms, st, clk.summary()
+
+    sm_max_mhz = None
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        try:
+            sm_max_mhz = float(json.load(open(peaks_path)).get("sm_max_mhz"))
+        except (ValueError, TypeError):
+            sm_max_mhz = None
+
+    elapsed_mx, kern_mx, st_mx, clk_mx = timed_leg("mixed")
+    launches_per_step = 3  # histogram clear, counter clear, fused solve
+    polys_total = n * world * args.steps
+    value = polys_total / (elapsed_mx * 1e-3)
+
+    plain = None
+    if not args.no_plain:
+        elapsed_pl, kern_pl, st_pl, clk_pl = timed_leg("plain")
+        plain = {"elapsed_ms": elapsed_pl, "kern_ms": kern_pl, "stats": st_pl, "clocks": clk_pl}
+
+    # one exchange step: sum the per-rank images (after the timed region)
+    reduce_ms = None
+    if world > 1:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        dist.reduce(hist, dst=0, op=dist.ReduceOp.SUM)
+        torch.cuda.synchronize()
+        reduce_ms = 1e3 * (time.perf_counter() - t)
+
+    # ---- end to end from pinned host memory through the public API
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, coeffs, win, dev, world)
+
+    if rank != 0:
+        return
+    mhz = clk_mx.get("sm_max_mhz") or sm_max_mhz or 2070.0
+    p32 = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6
+    p64 = sms * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6
+    f32, f64 = algorithmic_flops(st_mx, "mixed")
+    t_k = kern_mx * 1e-3
+    frac32, frac64 = f32 / p32 / t_k, f64 / p64 / t_k
+    traffic = profiled_traffic()
+    roofline = {
+        "bound": "alu", "kernel": "rd::solve_kernel<6, float, float2, MIXED>",
+        "achieved": (f32 + f64 * p32 / p64) / t_k / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
+        "frac": frac32 + frac64, "traffic": traffic,
+        "note": "FP32-equivalent: FP64 flops weighted by the FP32/FP64 peak ratio; frac = fp32_frac + fp64_frac",
+        "fp32_frac": frac32, "fp64_frac": frac64,
+        "fp32_tflops": f32 / t_k / 1e12, "fp64_tflops": f64 / t_k / 1e12,
+        "peak_fp32_tflops": p32 / 1e12, "peak_fp64_tflops": p64 / 1e12,
+        "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes (FP64: {FP64_FMA_PER_SM_CLK} FMA/SM/clk) "
+                       f"x 2 flop x {mhz:.0f} MHz",
+        "kernel_ms": kern_mx,
+        "algorithmic_flops_per_launch": {"fp32": f32, "fp64": f64},
+    }
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_mx / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic: seeded Littlewood {1,-1,i,-i} degree-6 polynomials (SplitMix64 seed 2), generated on device",
+        "config": workload_config(args),
+        "roofline": roofline,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk_mx,
+        "mixed": {"status": {k: st_mx[k] for k in ("status_ok", "status_not_converged", "status_rejected",
+                                                   "status_degenerate")},
+                  "sweeps_per_poly": st_mx["sweeps"] / max(1, st_mx["polys"]),
+                  "binned": st_mx["binned"], "out_of_window": st_mx["out_of_window"],
+                  "paper_equiv_gflops": value * 41.9e3 / 1e9,
+                  "equiv_qr_sweeps_per_s": value * st_mx["sweeps"] / max(1, st_mx["polys"])},
+    }
+    if plain is not None:
+        pv = polys_total / (plain["elapsed_ms"] * 1e-3)
+        _, g64 = algorithmic_flops(plain["stats"], "plain")
+        line["plain_fp64"] = {
+            "value": pv, "unit": UNIT, "ms_per_step": plain["elapsed_ms"] / args.steps,
+            "kernel_ms": plain["kern_ms"], "fp64_frac": g64 / p64 / (plain["kern_ms"] * 1e-3),
+            "fp64_tflops": g64 / (plain["kern_ms"] * 1e-3) / 1e12,
+            "sweeps_per_poly": plain["stats"]["sweeps"] / max(1, plain["stats"]["polys"]),
+            "status_not_converged": plain["stats"]["status_not_converged"], "clocks": plain["clocks"]}
+        line["mixed_over_plain"] = value / pv
+    if e2e is not None:
+        line["e2e"] = e2e
+    if reduce_ms is not None:
+        line["hist_reduce_ms"] = reduce_ms
+    if not args.no_cpu:
+        v, threads, done = cpu_oracle_rate(args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"first {done} polynomials of the same Littlewood stream, FP64 oracle "
+                                          f"solve (tol 1e-13) + histogram, chunks of 65536, ~{args.cpu_seconds:.0f} s"}
+    print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, coeffs_dev, win, dev, world):
+    """Same metric through the public API with the inputs in pinned host memory:
+    per step, the chunks are copied host-to-device on a copy stream while the
+    previous chunk is solved, and the histogram and counters are read back."""
+    import torch
+
+    from paper_2507_02164_gb300 import api
+
+    n = coeffs_dev.shape[1]
+    chunk = min(n, 1 << E2E_CHUNK_LOG2)
+    nchunks = (n + chunk - 1) // chunk
+    host = []
+    for c in range(nchunks):
+        part = coeffs_dev[:, c * chunk:(c + 1) * chunk].contiguous().cpu().pin_memory()
+        host.append(part)
+    bufs = [torch.empty((DEGREE + 1) * chunk, dtype=torch.complex64, device=dev) for _ in range(2)]
+    hist = api.new_hist(W_PIX, H_PIX, dev)
+    stats = api.new_stats(dev)
+    hist_h = torch.empty_like(hist, device="cpu").pin_memory()
+    stats_h = torch.empty_like(stats, device="cpu").pin_memory()
+    comp = torch.cuda.current_stream()
+    copy = torch.cuda.Stream(device=dev)
+    p = api.params("mixed")
+    freed = [torch.cuda.Event() for _ in range(2)]
+    loaded = [torch.cuda.Event() for _ in range(2)]
+
+    def step():
+        api.hist_clear(hist)
+        api.hist_clear(stats)
+        start_ev = torch.cuda.Event()
+        start_ev.record(comp)
+        copy.wait_event(start_ev)
+        for c in range(nchunks):
+            b = c % 2
+            m = host[c].shape[1]
+            dst = bufs[b][:(DEGREE + 1) * m].view(DEGREE + 1, m)  # contiguous [d+1, m]
+            with torch.cuda.stream(copy):
+                if c >= 2:
+                    copy.wait_event(freed[b])
+                dst.copy_(host[c], non_blocking=True)
+                loaded[b].record(copy)
+            comp.wait_event(loaded[b])
+            api.roots_density(dst, win, hist, mode="mixed", params_=p, stats=stats)
+            freed[b].record(comp)
+        hist_h.copy_(hist, non_blocking=True)
+        stats_h.copy_(stats, non_blocking=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(comp)
+    for _ in range(args.steps):
+        step()
+    t1.record(comp)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    h2d = sum(h.numel() * h.element_size() for h in host)
+    d2h = hist_h.numel() * hist_h.element_size() + stats_h.numel() * stats_h.element_size()
+    return {"value": n * world * args.steps / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": ms / args.steps, "chunks_per_step": nchunks,
+            "gpu_launches_per_step": 2 + nchunks}
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * rootdensity.h -- C ABI of libroots, the GB300 (sm_103a) library for
+ * batched complex polynomial roots and root-density histograms.
+ *
+ * Method: R. Tang, C. Quan, "Hardware-Accelerated Algorithm for Complex
+ * Function Roots Density Graph Plotting", arXiv 2507.02164.
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked "device" must point to device memory of the current
+ *     CUDA device; the caller owns it. The library never frees, keeps or
+ *     reallocates caller memory, and never allocates device memory itself.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Calls only enqueue work on it; none synchronises.
+ *   - Complex numbers are interleaved (re, im): rd_c64 = 2 x float (8 B),
+ *     rd_c128 = 2 x double (16 B).
+ *   - Uniform-degree batches are coefficient-major ("structure of arrays"):
+ *     coefficient k (of z^k, k = 0..d) of polynomial i is element k*n + i;
+ *     root j of polynomial i is element j*n + i. Consecutive polynomials are
+ *     consecutive in memory, so a warp reads 32 neighbours in one transaction.
+ *   - Return value: RD_OK, or a negative error code. rd_last_error() gives a
+ *     thread-local message for the most recent failure on the calling thread.
+ *     On error nothing has been enqueued.
+ */
+#ifndef ROOTDENSITY_H
+#define ROOTDENSITY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RD_ABI_VERSION 1
+
+/* ---- return codes ---------------------------------------------------- */
+#define RD_OK 0
+#define RD_EINVAL (-1)        /* null pointer, bad size, degree or window   */
+#define RD_ECUDA (-2)         /* CUDA launch or device query failed          */
+#define RD_EUNSUPPORTED (-3)  /* dtype / mode / degree combination not built */
+
+/* ---- per-polynomial status (uint8) ----------------------------------- */
+#define RD_STATUS_OK 0
+#define RD_STATUS_NOT_CONVERGED 1 /* a level used max_iters sweeps; its diagonal entry is still returned */
+#define RD_STATUS_REJECTED 2      /* mixed: residual or separation check failed; backward: p'(z) singular */
+#define RD_STATUS_DEGENERATE 3    /* a_d == 0 or a non-finite coefficient; roots are NaN */
+
+typedef enum { RD_C64 = 0, RD_C128 = 1 } rd_dtype;
+
+/* RD_PLAIN_FP64: every QR sweep in FP64.
+ * RD_MIXED: QR sweeps in FP32, then `polish_steps` FP64 Newton steps per root
+ * on the original coefficients and an FP64 residual / separation check. */
+typedef enum { RD_PLAIN_FP64 = 0, RD_MIXED = 1 } rd_mode;
+
+/* RD_SHIFT_WILKINSON: eigenvalue of the trailing 2x2 nearer h[m-1][m-1] on
+ * every sweep. RD_SHIFT_RAYLEIGH: the paper's shift s = h[m-1][m-1] (Alg. 1),
+ * with the Wilkinson shift every exc_period sweeps without deflation. */
+typedef enum { RD_SHIFT_WILKINSON = 0, RD_SHIFT_RAYLEIGH = 1 } rd_shift;
+
+typedef struct {
+    double tol;            /* deflation: |h[m-1][m-2]| <= tol (|h[m-1][m-1]| + |h[m-2][m-2]|), 1-norms of re/im */
+    int32_t max_iters;     /* sweeps per eigenvalue before giving up (>= 1)                     */
+    int32_t shift;         /* rd_shift                                                          */
+    int32_t exc_period;    /* RD_SHIFT_RAYLEIGH only; 0 = never use the Wilkinson shift        */
+    int32_t polish_steps;  /* RD_MIXED: FP64 Newton steps per root (0..8)                       */
+    double residual_tol;   /* RD_MIXED: reject when |p(z)| > residual_tol * sum_k |a_k||z|^k;
+                              <= 0 means 64 * d * 2^-53                                         */
+    double collapse_tol;   /* RD_MIXED: reject when two roots lie within collapse_tol * max(1,|z|) */
+    int32_t block;         /* threads per CTA, multiple of 32 in [32, 1024]; 0 = tuned default   */
+    int32_t ctas_per_sm;   /* grid = ctas_per_sm x SM count; 0 = tuned default                   */
+} rd_params;
+
+/* Defaults: plain tol 1e-13, mixed tol 4 * 2^-24, max_iters 40, Wilkinson
+ * shift, exc_period 10, 3 polish steps, residual 64 d 2^-53, collapse 1e-9. */
+void rd_default_params(rd_mode mode, rd_params *out);
+
+/* Root-density window: pixel column ix = floor((x - xmin) * W / (xmax - xmin)),
+ * row iy = floor((ymax - y) * H / (ymax - ymin)) (row 0 at the top), both in
+ * FP64; a root is counted when 0 <= ix < W and 0 <= iy < H (half-open bins:
+ * x = xmax or y = ymin is outside), otherwise it is out of the window.
+ * The paper converts solved roots to screen pixels and counts them in video
+ * memory (Sec. III, "Roots to Pixels" and "Video Memory" of Table I). */
+typedef struct {
+    double xmin, xmax, ymin, ymax;
+} rd_window;
+
+/* Counters a solve or binning call adds to (device, all uint64, += semantics). */
+typedef struct {
+    uint64_t polys;          /* polynomials processed                                    */
+    uint64_t status[4];      /* polynomials per status code                              */
+    uint64_t sweeps;         /* QR sweeps, summed over polynomials                       */
+    uint64_t pair_updates;   /* rotated row/column entry pairs of the Hessenberg sweeps  */
+    uint64_t rotations;      /* Givens rotations generated                               */
+    uint64_t newton_steps;   /* RD_MIXED: Newton steps taken                             */
+    uint64_t binned;         /* roots counted in the histogram                           */
+    uint64_t out_of_window;  /* roots outside the window (NaN included)                  */
+    uint64_t clipped;        /* roots dropped by a tile clip                             */
+} rd_stats;
+
+/* Optional per-polynomial tile clip of the full pipeline (Sec. II, domain
+ * split into subregions D_i): roots are first mapped z = centre_i + radius *
+ * w, then kept only if their tile, computed like a pixel on an nx x ny grid
+ * over `tiles`, equals tile_index[i]. */
+typedef struct {
+    const double *centres;     /* device, rd_c128 [n]: centre of polynomial i's sub-disk     */
+    double radius;             /* sub-disk radius (the tile half-diagonal)                    */
+    const int64_t *tile_index; /* device, [n]; NULL = polynomial i lies in tile i             */
+    int32_t nx, ny;            /* tile grid                                                   */
+    rd_window tiles;           /* window the tile grid covers                                 */
+} rd_clip;
+
+int rd_abi_version(void);
+const char *rd_last_error(void);
+
+/* Number of streaming multiprocessors of the current device (0 on failure). */
+int rd_device_sm_count(void);
+
+/* ---- roots of a uniform-degree batch (Sec. II-B, Alg. 1 / Alg. 2) ----------
+ * Roots of p_i(z) = sum_k a_ik z^k for i < n: eigenvalues of the Frobenius
+ * companion matrix of the monic p_i / a_id, by single-shift QR sweeps built
+ * from complex Givens rotations (Sec. II-C) applied in place to the Hessenberg
+ * matrix, with bottom deflation (tol) and at most max_iters sweeps per root.
+ *   coeffs  device, [degree+1][n] of `dtype` (rd_c64 or rd_c128)
+ *   degree  1..12
+ *   n       >= 0 (n = 0 is a no-op)
+ *   params  host pointer; NULL = rd_default_params(mode)
+ *   roots   device, rd_c128 [degree][n], or NULL
+ *   status  device, uint8 [n], or NULL
+ *   stats   device rd_stats (accumulated), or NULL
+ * Order of the roots of one polynomial is unspecified. */
+int rd_roots_batched(const void *coeffs, rd_dtype dtype, int degree, int64_t n, rd_mode mode,
+                     const rd_params *params, double *roots, uint8_t *status, rd_stats *stats,
+                     void *stream);
+
+/* ---- fused roots + root-density histogram ---------------------------------
+ * rd_roots_batched, then every root is binned into hist (+=, uint32, row-major
+ * [H][W]) with warp-aggregated atomics, without a trip through memory. clip
+ * (host pointer, may be NULL) selects the full-pipeline tile clip. roots and
+ * status may be NULL. The caller zeroes hist (rd_hist_clear) when it wants a
+ * fresh image: calls accumulate, so a long batch may be split into chunks. */
+int rd_roots_density(const void *coeffs, rd_dtype dtype, int degree, int64_t n, rd_mode mode,
+                     const rd_params *params, const rd_clip *clip, rd_window window, int W, int H,
+                     uint32_t *hist, double *roots, uint8_t *status, rd_stats *stats,
+                     void *stream);
+
+/* ---- standalone binning (Sec. III, Roots to Pixels) -------------------------
+ * hist[iy*W + ix] += 1 for each of the n_roots roots (device rd_c128 array)
+ * inside the window; others (NaN included) add to stats->out_of_window. */
+int rd_density_accumulate(const double *roots, int64_t n_roots, rd_window window, int W, int H,
+                          uint32_t *hist, rd_stats *stats, void *stream);
+
+/* Zero `words` 32-bit words of device memory (histogram or rd_stats). */
+int rd_hist_clear(uint32_t *hist, int64_t words, void *stream);
+
+/* ---- implicit-differentiation adjoint ---------------------------------------
+ * grad_coeffs[k*n+i] = sum_j conj(-z_ij^k / p_i'(z_ij)) * grad_roots[j*n+i],
+ * k = 0..degree (p(z) = 0 defines z(a); dz/da_k = -z^k / p'(z)), the gradient
+ * convention of PyTorch (grad = dL/dRe + i dL/dIm). Nothing from the forward
+ * QR sweeps is needed. A root with |p'(z)| <= 1e-300 (or non-finite) adds
+ * nothing and sets status RD_STATUS_REJECTED.
+ *   coeffs, grad_coeffs  device, [degree+1][n] of dtype (grad_coeffs overwritten)
+ *   roots, grad_roots    device, rd_c128 [degree][n]
+ *   status               device uint8 [n] or NULL
+ * rd_c128 computes in FP64, rd_c64 in FP32. */
+int rd_roots_backward(const void *coeffs, rd_dtype dtype, int degree, int64_t n,
+                      const double *roots, const double *grad_roots, void *grad_coeffs,
+                      uint8_t *status, void *stream);
+
+/* ---- L2 approximation on sub-disks (Sec. II-A) ------------------------------
+ * Nodes of the quadrature on the unit disk: radii r_p (Gauss-Legendre on
+ * [0,1], p < nr, ascending) with weights w_p, and angles theta_q = 2 pi q / nt.
+ * Host function; r and w are host arrays of nr doubles. */
+int rd_l2_nodes(int nr, double *r, double *w);
+
+/* For each sub-disk s < n, samples[s][p*nt + q] = g_s(r_p e^{i theta_q})
+ * (device rd_c128; g_s(w) = f(c_s + rho w)). Computes the degree-`degree`
+ * least-squares polynomial of g_s on the unit disk for the inner product
+ * <g, h> = integral g conj(h) dA, whose Gram matrix is diagonal:
+ * a_j = (j+1)/pi <g, w^j>. coeffs: device rd_c128, coefficient-major
+ * [degree+1][n] (ready for rd_roots_*). nt must be 32; nr <= 32; degree <= 12. */
+int rd_l2_approx(const double *samples, int64_t n, int nr, int nt, int degree, double *coeffs,
+                 void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ROOTDENSITY_H */

@@ -1,0 +1,210 @@
+"""Python binding of libroots over torch tensors.
+
+PyTorch supplies device memory and the current CUDA stream; every step of the
+computation runs in the library's CUDA kernels. Layouts follow
+include/rootdensity.h: uniform-degree batches are coefficient-major,
+``coeffs[k, i]`` is a_k of polynomial i (shape [d+1, n]) and ``roots[j, i]``
+is root j of polynomial i (shape [d, n], complex128).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _native as N
+
+
+@dataclass(frozen=True)
+class Window:
+    xmin: float
+    xmax: float
+    ymin: float
+    ymax: float
+
+    def c(self) -> N.Window:
+        return N.Window(self.xmin, self.xmax, self.ymin, self.ymax)
+
+    def tuple(self):
+        return (self.xmin, self.xmax, self.ymin, self.ymax)
+
+
+MODES = {"plain": N.PLAIN_FP64, "plain_fp64": N.PLAIN_FP64, "mixed": N.MIXED}
+DTYPES = {torch.complex64: N.C64, torch.complex128: N.C128}
+
+
+def _mode(mode) -> int:
+    return MODES[mode] if isinstance(mode, str) else int(mode)
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _check_cuda(name: str, t: torch.Tensor, dtype=None, contiguous=True):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if contiguous and not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def params(mode="mixed", **overrides) -> N.Params:
+    """rd_params with the library defaults for `mode`, then `overrides` applied."""
+    p = N.default_params(_mode(mode))
+    for k, v in overrides.items():
+        if k == "shift" and isinstance(v, str):
+            v = {"wilkinson": N.SHIFT_WILKINSON, "rayleigh": N.SHIFT_RAYLEIGH}[v]
+        setattr(p, k, v)
+    return p
+
+
+def new_stats(device="cuda") -> torch.Tensor:
+    """A zeroed rd_stats block (int64 words, read as unsigned)."""
+    return torch.zeros(N.STATS_WORDS, dtype=torch.int64, device=device)
+
+
+def stats_dict(stats: torch.Tensor) -> dict:
+    vals = stats.cpu().tolist()
+    return dict(zip(N.STATS_FIELDS, vals))
+
+
+def _coeff_args(coeffs: torch.Tensor):
+    _check_cuda("coeffs", coeffs)
+    if coeffs.dtype not in DTYPES:
+        raise ValueError("coeffs must be complex64 or complex128")
+    if coeffs.dim() != 2 or coeffs.shape[0] < 2:
+        raise ValueError("coeffs must have shape [degree+1, n]")
+    return DTYPES[coeffs.dtype], coeffs.shape[0] - 1, coeffs.shape[1]
+
+
+def roots_batched(coeffs: torch.Tensor, mode="mixed", params_=None, roots=None, status=None, stats=None,
+                  want_roots=True, want_status=True, stream=None):
+    """Roots of every column of coeffs ([d+1, n]). Returns (roots [d, n] c128, status [n] u8)."""
+    dt, d, n = _coeff_args(coeffs)
+    dev = coeffs.device
+    if want_roots and roots is None:
+        roots = torch.empty((d, n), dtype=torch.complex128, device=dev)
+    if want_status and status is None:
+        status = torch.empty(n, dtype=torch.uint8, device=dev)
+    p = params_ if params_ is not None else params(mode)
+    N.call("rd_roots_batched", _ptr(coeffs), dt, d, n, _mode(mode), ctypes.byref(p), _ptr(roots),
+           _ptr(status), _ptr(stats), _stream(stream))
+    return roots, status
+
+
+def hist_clear(t: torch.Tensor, stream=None):
+    _check_cuda("buffer", t)
+    words = t.numel() * t.element_size() // 4
+    N.call("rd_hist_clear", _ptr(t), words, _stream(stream))
+    return t
+
+
+def new_hist(W=1920, H=1080, device="cuda") -> torch.Tensor:
+    h = torch.empty((H, W), dtype=torch.int32, device=device)
+    return hist_clear(h)
+
+
+def make_clip(centres: torch.Tensor, radius: float, nx: int, ny: int, tiles: Window, tile_index=None):
+    _check_cuda("centres", centres, torch.complex128)
+    c = N.Clip()
+    c.centres = centres.data_ptr()
+    c.radius = float(radius)
+    c.tile_index = tile_index.data_ptr() if tile_index is not None else None
+    c.nx, c.ny = nx, ny
+    c.tiles = tiles.c()
+    return c
+
+
+def roots_density(coeffs: torch.Tensor, window: Window, hist: torch.Tensor, mode="mixed", params_=None,
+                  clip=None, roots=None, status=None, stats=None, stream=None):
+    """Fused roots + binning into hist ([H, W] int32 viewed as uint32, accumulated)."""
+    dt, d, n = _coeff_args(coeffs)
+    _check_cuda("hist", hist)
+    H, W = hist.shape
+    p = params_ if params_ is not None else params(mode)
+    N.call("rd_roots_density", _ptr(coeffs), dt, d, n, _mode(mode), ctypes.byref(p),
+           ctypes.byref(clip) if clip is not None else None, window.c(), W, H, _ptr(hist), _ptr(roots),
+           _ptr(status), _ptr(stats), _stream(stream))
+    return hist
+
+
+def density_accumulate(roots: torch.Tensor, window: Window, hist: torch.Tensor, stats=None, stream=None):
+    _check_cuda("roots", roots, torch.complex128)
+    _check_cuda("hist", hist)
+    H, W = hist.shape
+    N.call("rd_density_accumulate", _ptr(roots), roots.numel(), window.c(), W, H, _ptr(hist), _ptr(stats),
+           _stream(stream))
+    return hist
+
+
+def roots_backward(coeffs: torch.Tensor, roots: torch.Tensor, grad_roots: torch.Tensor, status=None,
+                   stream=None):
+    """grad_coeffs [d+1, n] (dtype of coeffs) from grad_roots [d, n] (complex128)."""
+    dt, d, n = _coeff_args(coeffs)
+    _check_cuda("roots", roots, torch.complex128)
+    _check_cuda("grad_roots", grad_roots, torch.complex128)
+    grad = torch.empty_like(coeffs)
+    N.call("rd_roots_backward", _ptr(coeffs), dt, d, n, _ptr(roots), _ptr(grad_roots), _ptr(grad),
+           _ptr(status), _stream(stream))
+    return grad
+
+
+def l2_nodes(nr: int = 16):
+    """Gauss-Legendre radii and weights on [0, 1] (host lists), from the library."""
+    r = (ctypes.c_double * nr)()
+    w = (ctypes.c_double * nr)()
+    N.call("rd_l2_nodes", nr, ctypes.cast(r, ctypes.c_void_p), ctypes.cast(w, ctypes.c_void_p))
+    return list(r), list(w)
+
+
+def l2_sample_points(nr: int = 16, nt: int = 32, device="cuda") -> torch.Tensor:
+    """w_pq = r_p e^{i 2 pi q / nt} as a [nr*nt] complex128 tensor (index p*nt + q)."""
+    r, _ = l2_nodes(nr)
+    rr = torch.tensor(r, dtype=torch.float64, device=device)
+    th = 2.0 * torch.pi * torch.arange(nt, dtype=torch.float64, device=device) / nt
+    return (rr[:, None] * torch.exp(1j * th)[None, :]).reshape(-1)
+
+
+def l2_approx(samples: torch.Tensor, nr: int = 16, nt: int = 32, degree: int = 6, coeffs=None, stream=None):
+    """samples [n, nr*nt] complex128 -> coeffs [degree+1, n] complex128 (local variable w)."""
+    _check_cuda("samples", samples, torch.complex128)
+    n = samples.shape[0]
+    if samples.shape[1] != nr * nt:
+        raise ValueError("samples must have shape [n, nr*nt]")
+    if coeffs is None:
+        coeffs = torch.empty((degree + 1, n), dtype=torch.complex128, device=samples.device)
+    N.call("rd_l2_approx", _ptr(samples), n, nr, nt, degree, _ptr(coeffs), _stream(stream))
+    return coeffs
+
+
+class RootsFn(torch.autograd.Function):
+    """roots = RootsFn.apply(coeffs [d+1, n], mode): forward by the QR solver,
+    backward by the implicit-differentiation adjoint (no QR history kept)."""
+
+    @staticmethod
+    def forward(ctx, coeffs, mode="mixed"):
+        roots, status = roots_batched(coeffs.detach().contiguous(), mode=mode)
+        ctx.save_for_backward(coeffs, roots)
+        ctx.mark_non_differentiable(status)
+        return roots, status
+
+    @staticmethod
+    def backward(ctx, grad_roots, grad_status):
+        coeffs, roots = ctx.saved_tensors
+        if grad_roots is None:
+            return None, None
+        g = roots_backward(coeffs.detach().contiguous(), roots, grad_roots.contiguous().to(torch.complex128))
+        return g, None
+
+
+def roots(coeffs: torch.Tensor, mode="mixed"):
+    """Differentiable roots: (roots [d, n] complex128, status [n] uint8)."""
+    return RootsFn.apply(coeffs, mode)

@@ -1,0 +1,260 @@
+// rd_abi.cu -- the extern "C" entry points of libroots: argument checks,
+// defaults and dispatch to the kernels. Every call only enqueues work on the
+// caller's stream; nothing here allocates device memory or synchronises.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "rd_common.cuh"
+#include "rd_solve.cuh"
+
+namespace rd {
+int launch_solve_mixed(int degree, rd_dtype dt, const SolveArgs &a, int block, int ctas_per_sm, cudaStream_t st);
+int launch_solve_plain(int degree, rd_dtype dt, const SolveArgs &a, int block, int ctas_per_sm, cudaStream_t st);
+int launch_density(const double *roots, int64_t n, const Binner &bin, uint32_t *hist, rd_stats *stats,
+                   cudaStream_t st);
+int launch_clear(uint32_t *p, int64_t words, cudaStream_t st);
+int launch_backward(int degree, rd_dtype dt, const void *coeffs, const double *roots, const double *grad_roots,
+                    void *grad_coeffs, uint8_t *status, int64_t n, cudaStream_t st);
+int l2_nodes_host(int nr, double *r, double *w);
+int launch_l2(const double *samples, int64_t n, int nr, int degree, double *coeffs, cudaStream_t st);
+}  // namespace rd
+
+static thread_local char g_err[512] = "";
+
+int rd_set_error(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int rd_check_launch(const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return rd_set_error(RD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    return RD_OK;
+}
+
+// SM count of the current device, queried once per device.
+int rd_sm_count_cached()
+{
+    static std::mutex mu;
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    std::lock_guard<std::mutex> lk(mu);
+    if (cache[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+
+namespace {
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+bool window_ok(const rd_window &w)
+{
+    return std::isfinite(w.xmin) && std::isfinite(w.xmax) && std::isfinite(w.ymin) && std::isfinite(w.ymax) &&
+           w.xmin < w.xmax && w.ymin < w.ymax;
+}
+
+rd::Binner make_binner(const rd_window &w, int W, int H)
+{
+    rd::Binner b;
+    b.xmin = w.xmin;
+    b.ymax = w.ymax;
+    b.sx = (double)W / (w.xmax - w.xmin);
+    b.sy = (double)H / (w.ymax - w.ymin);
+    b.W = W;
+    b.H = H;
+    return b;
+}
+
+int check_params(const rd_params &p)
+{
+    if (!(p.tol >= 0.0) || !std::isfinite(p.tol)) return rd_set_error(RD_EINVAL, "params.tol must be finite and >= 0");
+    if (p.max_iters < 1 || p.max_iters > 100000) return rd_set_error(RD_EINVAL, "params.max_iters must be in [1, 100000]");
+    if (p.shift != RD_SHIFT_WILKINSON && p.shift != RD_SHIFT_RAYLEIGH) return rd_set_error(RD_EINVAL, "params.shift invalid");
+    if (p.exc_period < 0) return rd_set_error(RD_EINVAL, "params.exc_period must be >= 0");
+    if (p.polish_steps < 0 || p.polish_steps > 8) return rd_set_error(RD_EINVAL, "params.polish_steps must be in [0, 8]");
+    if (!std::isfinite(p.residual_tol) || !std::isfinite(p.collapse_tol) || p.collapse_tol < 0)
+        return rd_set_error(RD_EINVAL, "params.residual_tol / collapse_tol invalid");
+    if (p.block != 0 && (p.block < 32 || p.block > 256 || p.block % 32 != 0))
+        return rd_set_error(RD_EINVAL, "params.block must be 0 or a multiple of 32 in [32, 256]");
+    if (p.ctas_per_sm < 0 || p.ctas_per_sm > 64) return rd_set_error(RD_EINVAL, "params.ctas_per_sm must be in [0, 64]");
+    return RD_OK;
+}
+
+int solve_common(const void *coeffs, rd_dtype dtype, int degree, int64_t n, rd_mode mode, const rd_params *params,
+                 const rd_clip *clip, const rd_window *window, int W, int H, uint32_t *hist, double *roots,
+                 uint8_t *status, rd_stats *stats, void *stream)
+{
+    if (dtype != RD_C64 && dtype != RD_C128) return rd_set_error(RD_EINVAL, "dtype must be RD_C64 or RD_C128");
+    if (mode != RD_PLAIN_FP64 && mode != RD_MIXED) return rd_set_error(RD_EINVAL, "mode must be RD_PLAIN_FP64 or RD_MIXED");
+    if (degree < 1 || degree > 12) return rd_set_error(RD_EUNSUPPORTED, "degree %d outside 1..12", degree);
+    if (n < 0) return rd_set_error(RD_EINVAL, "n < 0");
+    if (n > ((int64_t)1 << 40)) return rd_set_error(RD_EINVAL, "n too large");
+    size_t el = dtype == RD_C64 ? 8 : 16;
+    if (n > 0 && (!coeffs || !aligned(coeffs, el))) return rd_set_error(RD_EINVAL, "coeffs null or misaligned");
+    if (roots && !aligned(roots, 16)) return rd_set_error(RD_EINVAL, "roots misaligned (16 B)");
+    if (stats && !aligned(stats, 8)) return rd_set_error(RD_EINVAL, "stats misaligned (8 B)");
+    rd_params p;
+    if (params) p = *params;
+    else rd_default_params(mode, &p);
+    int rc = check_params(p);
+    if (rc) return rc;
+
+    rd::SolveArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.coeffs = coeffs;
+    a.n = n;
+    a.tol = p.tol;
+    a.max_iters = p.max_iters;
+    a.shift = p.shift;
+    a.exc_period = p.exc_period;
+    a.polish_steps = p.polish_steps;
+    a.residual_tol = p.residual_tol > 0 ? p.residual_tol : 64.0 * degree * std::ldexp(1.0, -53);
+    a.collapse_tol = p.collapse_tol;
+    a.roots = roots;
+    a.status = status;
+    a.stats = stats;
+    if (hist) {
+        if (!window || !window_ok(*window)) return rd_set_error(RD_EINVAL, "window must be finite with xmin < xmax, ymin < ymax");
+        if (W < 1 || H < 1 || (int64_t)W * H > ((int64_t)1 << 31)) return rd_set_error(RD_EINVAL, "bad histogram size %d x %d", W, H);
+        if (!aligned(hist, 4)) return rd_set_error(RD_EINVAL, "hist misaligned");
+        a.hist = hist;
+        a.bin = make_binner(*window, W, H);
+        if (clip) {
+            if (!clip->centres || !aligned(clip->centres, 16)) return rd_set_error(RD_EINVAL, "clip.centres null or misaligned");
+            if (!(clip->radius > 0) || !std::isfinite(clip->radius)) return rd_set_error(RD_EINVAL, "clip.radius must be > 0");
+            if (clip->nx < 1 || clip->ny < 1 || !window_ok(clip->tiles)) return rd_set_error(RD_EINVAL, "clip tile grid invalid");
+            if (!clip->tile_index && n > (int64_t)clip->nx * clip->ny) return rd_set_error(RD_EINVAL, "clip: n exceeds nx*ny without tile_index");
+            a.clip_on = 1;
+            a.centres = clip->centres;
+            a.radius = clip->radius;
+            a.tile_index = clip->tile_index;
+            a.tiles = make_binner(clip->tiles, clip->nx, clip->ny);
+        }
+    } else if (clip) {
+        return rd_set_error(RD_EINVAL, "clip needs a histogram");
+    }
+    if (n == 0) return RD_OK;
+    int block = p.block ? p.block : 128;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (mode == RD_MIXED) return rd::launch_solve_mixed(degree, dtype, a, block, p.ctas_per_sm, st);
+    return rd::launch_solve_plain(degree, dtype, a, block, p.ctas_per_sm, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int rd_abi_version(void) { return RD_ABI_VERSION; }
+
+const char *rd_last_error(void) { return g_err; }
+
+int rd_device_sm_count(void)
+{
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return v;
+}
+
+void rd_default_params(rd_mode mode, rd_params *out)
+{
+    if (!out) return;
+    std::memset(out, 0, sizeof(*out));
+    out->tol = mode == RD_MIXED ? 4.0 * std::ldexp(1.0, -24) : 1e-13;
+    out->max_iters = 40;
+    out->shift = RD_SHIFT_WILKINSON;
+    out->exc_period = 10;
+    out->polish_steps = 3;
+    out->residual_tol = 0.0;
+    out->collapse_tol = 1e-9;
+    out->block = 0;
+    out->ctas_per_sm = 0;
+}
+
+int rd_roots_batched(const void *coeffs, rd_dtype dtype, int degree, int64_t n, rd_mode mode, const rd_params *params,
+                     double *roots, uint8_t *status, rd_stats *stats, void *stream)
+{
+    return solve_common(coeffs, dtype, degree, n, mode, params, nullptr, nullptr, 0, 0, nullptr, roots, status, stats,
+                        stream);
+}
+
+int rd_roots_density(const void *coeffs, rd_dtype dtype, int degree, int64_t n, rd_mode mode, const rd_params *params,
+                     const rd_clip *clip, rd_window window, int W, int H, uint32_t *hist, double *roots,
+                     uint8_t *status, rd_stats *stats, void *stream)
+{
+    if (!hist) return rd_set_error(RD_EINVAL, "hist is null");
+    return solve_common(coeffs, dtype, degree, n, mode, params, clip, &window, W, H, hist, roots, status, stats,
+                        stream);
+}
+
+int rd_density_accumulate(const double *roots, int64_t n_roots, rd_window window, int W, int H, uint32_t *hist,
+                          rd_stats *stats, void *stream)
+{
+    if (n_roots < 0) return rd_set_error(RD_EINVAL, "n_roots < 0");
+    if (!hist || !aligned(hist, 4)) return rd_set_error(RD_EINVAL, "hist null or misaligned");
+    if (n_roots > 0 && (!roots || !aligned(roots, 16))) return rd_set_error(RD_EINVAL, "roots null or misaligned");
+    if (!window_ok(window)) return rd_set_error(RD_EINVAL, "window must be finite with xmin < xmax, ymin < ymax");
+    if (W < 1 || H < 1 || (int64_t)W * H > ((int64_t)1 << 31)) return rd_set_error(RD_EINVAL, "bad histogram size");
+    if (stats && !aligned(stats, 8)) return rd_set_error(RD_EINVAL, "stats misaligned");
+    if (n_roots == 0) return RD_OK;
+    return rd::launch_density(roots, n_roots, make_binner(window, W, H), hist, stats,
+                              reinterpret_cast<cudaStream_t>(stream));
+}
+
+int rd_hist_clear(uint32_t *hist, int64_t words, void *stream)
+{
+    if (words < 0) return rd_set_error(RD_EINVAL, "words < 0");
+    if (words == 0) return RD_OK;
+    if (!hist || !aligned(hist, 4)) return rd_set_error(RD_EINVAL, "hist null or misaligned");
+    return rd::launch_clear(hist, words, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int rd_roots_backward(const void *coeffs, rd_dtype dtype, int degree, int64_t n, const double *roots,
+                      const double *grad_roots, void *grad_coeffs, uint8_t *status, void *stream)
+{
+    if (dtype != RD_C64 && dtype != RD_C128) return rd_set_error(RD_EINVAL, "dtype must be RD_C64 or RD_C128");
+    if (degree < 1 || degree > 12) return rd_set_error(RD_EUNSUPPORTED, "degree %d outside 1..12", degree);
+    if (n < 0) return rd_set_error(RD_EINVAL, "n < 0");
+    if (n == 0) return RD_OK;
+    size_t el = dtype == RD_C64 ? 8 : 16;
+    if (!coeffs || !aligned(coeffs, el) || !grad_coeffs || !aligned(grad_coeffs, el))
+        return rd_set_error(RD_EINVAL, "coeffs / grad_coeffs null or misaligned");
+    if (!roots || !aligned(roots, 16) || !grad_roots || !aligned(grad_roots, 16))
+        return rd_set_error(RD_EINVAL, "roots / grad_roots null or misaligned");
+    return rd::launch_backward(degree, dtype, coeffs, roots, grad_roots, grad_coeffs, status, n,
+                               reinterpret_cast<cudaStream_t>(stream));
+}
+
+int rd_l2_nodes(int nr, double *r, double *w)
+{
+    if (nr < 1 || nr > 32) return rd_set_error(RD_EINVAL, "nr must be in 1..32");
+    if (!r || !w) return rd_set_error(RD_EINVAL, "r / w null");
+    return rd::l2_nodes_host(nr, r, w);
+}
+
+int rd_l2_approx(const double *samples, int64_t n, int nr, int nt, int degree, double *coeffs, void *stream)
+{
+    if (nt != 32) return rd_set_error(RD_EUNSUPPORTED, "nt must be 32 (one angle per lane)");
+    if (nr < 1 || nr > 32) return rd_set_error(RD_EINVAL, "nr must be in 1..32");
+    if (degree < 0 || degree > 12) return rd_set_error(RD_EINVAL, "degree must be in 0..12");
+    if (n < 0) return rd_set_error(RD_EINVAL, "n < 0");
+    if (n == 0) return RD_OK;
+    if (!samples || !aligned(samples, 16) || !coeffs || !aligned(coeffs, 16))
+        return rd_set_error(RD_EINVAL, "samples / coeffs null or misaligned");
+    return rd::launch_l2(samples, n, nr, degree, coeffs, reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// rd_l2.cu -- least-squares (L2) polynomial approximation on sub-disks.
+//
+// Paper: Tang & Quan, arXiv 2507.02164, Sec. II: the domain is split into
+// small subregions and f is approximated on each by a polynomial g; Sec. II-A:
+// with <g, h> = integral over the unit disk of g conj(h), the coefficients
+// solve G a = b with G_jk = <z^j, z^k>, b_j = <f, z^j>. Taking the measure as
+// area (dA = r dr dtheta), G is diagonal with G_jj = pi/(j+1), so
+//   a_j = (j+1)/pi * <g, w^j>.
+// Quadrature: Gauss-Legendre in r on [0,1] (nr nodes, the Jacobian r folded
+// into the weights), the trapezoid rule in theta (nt = 32 equispaced angles,
+// exact for trigonometric degree < 32). Per sub-disk:
+//   <g, w^j> ~ sum_p w_p r_p^{j+1} (2 pi / nt) sum_q g(r_p e^{i theta_q}) e^{-i j theta_q}.
+//
+// Kernel: one warp per sub-disk, lane q owns angle theta_q; the radial sums
+// u_j(q) = sum_p (w_p r_p^{j+1}) g_pq use real weights (2 FMA per term), then
+// v_j = sum_q u_j(q) e^{-i j theta_q} is a warp butterfly. The 512 samples of a
+// sub-disk (8 KB) are read once, 32 consecutive doubles2 per load.
+#include <cmath>
+
+#include "rd_common.cuh"
+
+namespace rd {
+
+constexpr int L2_NT = 32;
+constexpr int L2_MAX_NR = 32;
+constexpr int L2_MAX_DEG = 12;
+
+struct L2Tables {
+    double wr[L2_MAX_NR][L2_MAX_DEG + 1];   // w_p r_p^{j+1} * (2 pi / nt) * (j+1) / pi
+    double tw[L2_MAX_DEG + 1][L2_NT][2];    // e^{-i j theta_q}
+};
+
+// Legendre P_n(x) and P_{n-1}(x) by the three-term recurrence.
+static void legendre_pair(int n, double x, double &pn, double &pn1)
+{
+    double pm1 = 1.0, p = x;  // P_0, P_1
+    if (n == 0) {
+        pn = 1.0;
+        pn1 = 0.0;
+        return;
+    }
+    for (int k = 2; k <= n; ++k) {
+        double next = ((2 * k - 1) * x * p - (k - 1) * pm1) / k;
+        pm1 = p;
+        p = next;
+    }
+    pn = p;
+    pn1 = pm1;
+}
+
+// Gauss-Legendre on [0, 1]: nodes are the zeros of P_n mapped from [-1, 1],
+// found by Newton's method from Tricomi's first-order estimate; the weights are
+// 2 / ((1 - x^2) P_n'(x)^2) on [-1, 1], halved for [0, 1], with
+// P_n'(x) = n (P_{n-1}(x) - x P_n(x)) / (1 - x^2).
+int l2_nodes_host(int nr, double *r, double *w)
+{
+    const double pi = 3.14159265358979323846;
+    for (int k = 1; k <= nr; ++k) {
+        double x = (1.0 - (nr - 1.0) / (8.0 * nr * nr * nr)) * std::cos(pi * (4.0 * k - 1.0) / (4.0 * nr + 2.0));
+        for (int it = 0; it < 60; ++it) {
+            double pn, pn1;
+            legendre_pair(nr, x, pn, pn1);
+            double dpn = nr * (pn1 - x * pn) / ((1.0 - x) * (1.0 + x));
+            double dx = pn / dpn;
+            x -= dx;
+            if (std::fabs(dx) < 1e-17) break;
+        }
+        double pn, pn1;
+        legendre_pair(nr, x, pn, pn1);
+        double omx2 = (1.0 - x) * (1.0 + x);
+        double dpn = nr * (pn1 - x * pn) / omx2;
+        double wt = 2.0 / (omx2 * dpn * dpn);
+        // k = 1 is the largest node: fill from the top so r ascends
+        r[nr - k] = 0.5 * (1.0 + x);
+        w[nr - k] = 0.5 * wt;
+    }
+    return 0;
+}
+
+__global__ void __launch_bounds__(256) l2_kernel(const double2 *__restrict__ samples, int64_t n, int nr,
+                                                 int degree, double2 *coeffs, const L2Tables T)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+    // this lane's twiddles, read once (lanes read different entries, which
+    // the constant bank would serialise inside the loop)
+    double twr[L2_MAX_DEG + 1], twi[L2_MAX_DEG + 1];
+#pragma unroll
+    for (int j = 0; j <= L2_MAX_DEG; ++j) {
+        twr[j] = T.tw[j][lane][0];
+        twi[j] = T.tw[j][lane][1];
+    }
+    for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n; s += warps_total) {
+        const double2 *g = samples + s * (int64_t)nr * L2_NT;
+        double ur[L2_MAX_DEG + 1], ui[L2_MAX_DEG + 1];
+#pragma unroll
+        for (int j = 0; j <= L2_MAX_DEG; ++j) ur[j] = ui[j] = 0.0;
+        for (int p = 0; p < nr; ++p) {
+            double2 v = __ldg(g + p * L2_NT + lane);
+#pragma unroll
+            for (int j = 0; j <= L2_MAX_DEG; ++j)
+                if (j <= degree) {
+                    ur[j] = fma(T.wr[p][j], v.x, ur[j]);
+                    ui[j] = fma(T.wr[p][j], v.y, ui[j]);
+                }
+        }
+#pragma unroll
+        for (int j = 0; j <= L2_MAX_DEG; ++j)
+            if (j <= degree) {
+                double c = twr[j], sn = twi[j];
+                double vr = fma(ur[j], c, -ui[j] * sn);
+                double vi = fma(ur[j], sn, ui[j] * c);
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) {
+                    vr += __shfl_xor_sync(0xffffffffu, vr, off);
+                    vi += __shfl_xor_sync(0xffffffffu, vi, off);
+                }
+                if (lane == j) coeffs[(int64_t)j * n + s] = make_double2(vr, vi);
+            }
+    }
+}
+
+int launch_l2(const double *samples, int64_t n, int nr, int degree, double *coeffs, cudaStream_t st)
+{
+    L2Tables T;
+    double r[L2_MAX_NR], w[L2_MAX_NR];
+    l2_nodes_host(nr, r, w);
+    const double pi = 3.14159265358979323846;
+    for (int p = 0; p < L2_MAX_NR; ++p)
+        for (int j = 0; j <= L2_MAX_DEG; ++j) {
+            double v = 0.0;
+            if (p < nr && j <= degree) v = w[p] * std::pow(r[p], j + 1) * (2.0 * pi / L2_NT) * (j + 1) / pi;
+            T.wr[p][j] = v;
+        }
+    for (int j = 0; j <= L2_MAX_DEG; ++j)
+        for (int q = 0; q < L2_NT; ++q) {
+            // e^{-i j theta_q}, theta_q = 2 pi q / nt, reduced exactly: (j q) mod nt
+            int t = (j * q) % L2_NT;
+            double ang = 2.0 * pi * t / L2_NT;
+            T.tw[j][q][0] = std::cos(ang);
+            T.tw[j][q][1] = -std::sin(ang);
+        }
+    const int block = 256;
+    int64_t ctas = (n + 7) / 8;
+    int64_t cap = (int64_t)rd_sm_count_cached() * 8;
+    if (ctas > cap) ctas = cap;
+    if (ctas < 1) ctas = 1;
+    l2_kernel<<<(unsigned)ctas, block, 0, st>>>(reinterpret_cast<const double2 *>(samples), n, nr, degree,
+                                                reinterpret_cast<double2 *>(coeffs), T);
+    return rd_check_launch("l2_kernel");
+}
+
+}  // namespace rd

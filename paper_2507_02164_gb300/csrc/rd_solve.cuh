@@ -1,0 +1,389 @@
+// rd_solve.cuh -- batched roots of uniform-degree complex polynomials by
+// single-shift QR on the companion matrix, held in registers (sm_103a).
+//
+// Paper: Tang & Quan, arXiv 2507.02164.
+//   Sec. II-B  roots of the monic P = eigenvalues of its Frobenius companion
+//              matrix; Alg. 1 (QR iteration with single shift, deflation of
+//              the bottom eigenvalue, the active block shrinks by one).
+//   Sec. II-C  the matrix stays upper Hessenberg (Appendix A), so a sweep is
+//              m-1 Givens row rotations followed by m-1 column rotations.
+//   Alg. 2     the CPU/GPU restatement the sweep order follows.
+//
+// GPU design (one thread = one polynomial):
+//   * the Hessenberg matrix h[N][N] lives in registers; every index is a
+//     compile-time constant (N is a template parameter, all loops unrolled),
+//     entries below the subdiagonal are never touched, so the compiler keeps
+//     only the N(N+1)/2 + N-1 live entries;
+//   * each lane has its own active size m; a warp runs a sweep of size
+//     M = max over its lanes of m, and a lane whose m < M applies identity
+//     rotations for r >= m (no divergent code paths, no dynamic register
+//     indexing); the frozen part of a finished lane is not changed;
+//   * deflation |h[m-1][m-2]| <= tol (|h[m-1][m-1]| + |h[m-2][m-2]|) with
+//     1-norms of (re, im), at most max_iters sweeps per eigenvalue;
+//   * RD_MIXED: sweeps in FP32, then FP64 Newton polish of every root on the
+//     original coefficients (FP64 p(z), FP32 p'(z)), an FP64 residual check
+//     |p(z)| <= residual_tol sum |a_k||z|^k and a root-separation check;
+//   * optional fused binning with warp-aggregated atomics.
+#pragma once
+
+#include <type_traits>
+
+#include "rd_common.cuh"
+
+namespace rd {
+
+struct SolveArgs {
+    const void *coeffs;  // [N+1][n]
+    int64_t n;
+    double tol;
+    int max_iters;
+    int shift;       // rd_shift
+    int exc_period;
+    int polish_steps;
+    double residual_tol;
+    double collapse_tol;
+    double *roots;    // [N][n] c128 or null
+    uint8_t *status;  // [n] or null
+    uint32_t *hist;   // or null
+    Binner bin;
+    // tile clip (full pipeline): clip_on => z = centre + radius * w and keep
+    // only roots whose tile (nx x ny over the tile window) is the polynomial's
+    int clip_on;
+    const double *centres;
+    double radius;
+    const int64_t *tile_index;
+    Binner tiles;
+    rd_stats *stats;
+};
+
+template <typename In>
+struct InLoad;
+template <>
+struct InLoad<float2> {
+    __device__ static cx<double> ld(const void *p, int64_t idx)
+    {
+        float2 v = __ldg(reinterpret_cast<const float2 *>(p) + idx);
+        return {(double)v.x, (double)v.y};
+    }
+    __device__ static cx<float> ldf(const void *p, int64_t idx)
+    {
+        float2 v = __ldg(reinterpret_cast<const float2 *>(p) + idx);
+        return {v.x, v.y};
+    }
+};
+template <>
+struct InLoad<double2> {
+    __device__ static cx<double> ld(const void *p, int64_t idx)
+    {
+        double2 v = __ldg(reinterpret_cast<const double2 *>(p) + idx);
+        return {v.x, v.y};
+    }
+    __device__ static cx<float> ldf(const void *p, int64_t idx)
+    {
+        double2 v = __ldg(reinterpret_cast<const double2 *>(p) + idx);
+        return {(float)v.x, (float)v.y};
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ bool finite_c(cx<T> z) { return isfinite(z.re) && isfinite(z.im); }
+
+// One shifted QR sweep of size M (warp-uniform) on h; this lane's rotations
+// r >= m are the identity and its diagonal is shifted only for i < m.
+template <int N, typename T>
+__device__ __forceinline__ void qr_sweep(cx<T> (&h)[N][N], int m, int M, cx<T> shift)
+{
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        if (i < M) {
+            bool a = i < m;
+            h[i][i].re -= a ? shift.re : T(0);
+            h[i][i].im -= a ? shift.im : T(0);
+        }
+    T c[N];
+    cx<T> s[N];
+    // left rotations Q_r, r = 1..M-1: zero h[r][r-1], update rows r-1, r
+#pragma unroll
+    for (int r = 1; r < N; ++r) {
+        if (r < M) {
+            cx<T> top;
+            givens(h[r - 1][r - 1], h[r][r - 1], c[r], s[r], top);
+            bool act = r < m;
+            c[r] = act ? c[r] : T(1);
+            s[r] = sel(act, s[r], cx<T>{T(0), T(0)});
+            h[r - 1][r - 1] = sel(act, top, h[r - 1][r - 1]);
+            h[r][r - 1] = sel(act, cx<T>{T(0), T(0)}, h[r][r - 1]);
+#pragma unroll
+            for (int j = r; j < N; ++j)
+                if (j < M) rot_rows(c[r], s[r], h[r - 1][j], h[r][j]);
+        }
+    }
+    // right rotations Q_r^H: columns r-1, r over rows 0..r (the matrix is
+    // upper triangular before them, Appendix A)
+#pragma unroll
+    for (int r = 1; r < N; ++r) {
+        if (r < M) {
+#pragma unroll
+            for (int i = 0; i <= r; ++i) rot_cols(c[r], s[r], h[i][r - 1], h[i][r]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        if (i < M) {
+            bool a = i < m;
+            h[i][i].re += a ? shift.re : T(0);
+            h[i][i].im += a ? shift.im : T(0);
+        }
+}
+
+// Trailing 2x2 of the active block [[a, b], [c, d]] for this lane's m.
+template <int N, typename T>
+__device__ __forceinline__ void trailing(const cx<T> (&h)[N][N], int m, cx<T> &a, cx<T> &b,
+                                         cx<T> &c, cx<T> &d)
+{
+    a = h[0][0];
+    b = h[0][1 < N ? 1 : 0];
+    c = h[1 < N ? 1 : 0][0];
+    d = h[1 < N ? 1 : 0][1 < N ? 1 : 0];
+#pragma unroll
+    for (int k = 2; k < N; ++k)
+        if (m == k + 1) {
+            a = h[k - 1][k - 1];
+            b = h[k - 1][k];
+            c = h[k][k - 1];
+            d = h[k][k];
+        }
+}
+
+// Eigenvalue of [[a, b], [c, d]] nearer d: with t = (a - d)/2 and
+// disc = sqrt(t^2 + bc), the two are d + t +- disc; the nearer one is
+// d - bc / (t + disc') with disc' the sign of disc that makes |t + disc'|
+// largest (no cancellation).
+template <typename T>
+__device__ __forceinline__ cx<T> wilkinson(cx<T> a, cx<T> b, cx<T> c, cx<T> d)
+{
+    cx<T> t = scale(T(0.5), sub(a, d));
+    cx<T> bc = mul(b, c);
+    cx<T> disc = csqrt(cfma(t, t, bc));
+    T dir = fma(t.re, disc.re, t.im * disc.im);  // Re(conj(t) disc)
+    cx<T> den = dir >= T(0) ? add(t, disc) : sub(t, disc);
+    if (den.re == T(0) && den.im == T(0)) return d;
+    return sub(d, cdiv(bc, den));
+}
+
+template <int N, typename T, typename In, bool MIXED>
+__global__ void __launch_bounds__(256) solve_kernel(SolveArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t warp_id = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t n = A.n;
+    const T tol = (T)A.tol;
+    LaneStats S;
+
+    for (int64_t base = warp_id * 32; base < n; base += warps_total * 32) {
+        const int64_t i = base + lane;
+        const bool valid = i < n;
+
+        // ---- load a_0..a_N (coefficient-major, coalesced) and normalise
+        cx<T> b[N];
+        bool degenerate = !valid;
+        if (valid) {
+            if constexpr (MIXED && std::is_same<In, float2>::value) {
+                // complex64 storage: FP32 normalisation is exact enough for the sweeps
+                cx<float> a[N + 1];
+#pragma unroll
+                for (int k = 0; k <= N; ++k) a[k] = InLoad<In>::ldf(A.coeffs, (int64_t)k * n + i);
+#pragma unroll
+                for (int k = 0; k <= N; ++k) degenerate |= !finite_c(a[k]);
+                degenerate |= (a[N].re == 0.0f && a[N].im == 0.0f);
+                cx<float> inv = cdiv(cx<float>{1.0f, 0.0f}, degenerate ? cx<float>{1.0f, 0.0f} : a[N]);
+#pragma unroll
+                for (int k = 0; k < N; ++k) b[k] = mul(a[k], inv);
+            } else {
+                // FP64 coefficients: test and normalise in FP64 (a coefficient outside
+                // the FP32 range is still a valid input), then round for FP32 sweeps
+                cx<double> a[N + 1];
+#pragma unroll
+                for (int k = 0; k <= N; ++k) a[k] = InLoad<In>::ld(A.coeffs, (int64_t)k * n + i);
+#pragma unroll
+                for (int k = 0; k <= N; ++k) degenerate |= !finite_c(a[k]);
+                degenerate |= (a[N].re == 0.0 && a[N].im == 0.0);
+                cx<double> inv = cdiv(cx<double>{1.0, 0.0}, degenerate ? cx<double>{1.0, 0.0} : a[N]);
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    cx<double> q = mul(a[k], inv);
+                    b[k] = {(T)q.re, (T)q.im};
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < N; ++k) b[k] = {T(0), T(0)};
+        }
+
+        // ---- Frobenius companion matrix: subdiagonal ones, last column -b
+        cx<T> h[N][N];
+#pragma unroll
+        for (int r = 0; r < N; ++r)
+#pragma unroll
+            for (int j = 0; j < N; ++j) h[r][j] = {T(0), T(0)};
+#pragma unroll
+        for (int r = 0; r + 1 < N; ++r) h[r + 1][r] = {T(1), T(0)};
+#pragma unroll
+        for (int r = 0; r < N; ++r) h[r][N - 1] = degenerate ? cx<T>{T(0), T(0)} : cx<T>{-b[r].re, -b[r].im};
+
+        // ---- QR iteration with deflation (Alg. 1)
+        int m = degenerate ? 0 : N;
+        int its = 0;
+        bool not_conv = false;
+        for (;;) {
+            // deflate while the bottom subdiagonal is negligible (at most once per pass)
+            if (m >= 2) {
+                cx<T> ta, tb, tc, td;
+                trailing<N, T>(h, m, ta, tb, tc, td);
+                bool small = abs1(tc) <= tol * (abs1(ta) + abs1(td));
+                if (small || its >= A.max_iters) {
+                    not_conv |= !small;
+                    m -= 1;
+                    its = 0;
+                }
+            }
+            int mm = m >= 2 ? m : 0;
+            int M = __reduce_max_sync(0xffffffffu, mm);
+            if (M < 2) break;
+            cx<T> ta, tb, tc, td;
+            trailing<N, T>(h, mm >= 2 ? mm : 2, ta, tb, tc, td);
+            bool wilk = (A.shift == RD_SHIFT_WILKINSON) ||
+                        (A.exc_period > 0 && its > 0 && (its % A.exc_period) == 0);
+            cx<T> shift = wilk ? wilkinson(ta, tb, tc, td) : td;
+            qr_sweep<N, T>(h, mm, M, shift);
+            if (mm >= 2) {
+                its += 1;
+                S.sweeps += 1;
+                S.pairs += (unsigned)(mm * (mm + 1) - 2);
+                S.rots += (unsigned)(mm - 1);
+            }
+        }
+
+        // ---- roots: the diagonal; MIXED polishes them in FP64
+        uint8_t st = degenerate ? RD_STATUS_DEGENERATE : (not_conv ? RD_STATUS_NOT_CONVERGED : RD_STATUS_OK);
+        cx<double> z[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) z[j] = {(double)h[j][j].re, (double)h[j][j].im};
+
+        if constexpr (MIXED) {
+            if (!degenerate) {
+                // the original coefficients again (an L1/L2 hit: this warp read them
+                // at the start of the sweep), in FP64 and rounded to FP32
+                cx<double> ad[N + 1];
+                cx<float> af[N + 1];
+#pragma unroll
+                for (int k = 0; k <= N; ++k) {
+                    ad[k] = InLoad<In>::ld(A.coeffs, (int64_t)k * n + i);
+                    af[k] = {(float)ad[k].re, (float)ad[k].im};
+                }
+                bool reject = false;
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    cx<float> zf = {h[j][j].re, h[j][j].im};
+                    for (int step = 0; step < A.polish_steps; ++step) {
+                        // p(z) in FP64 (Horner)
+                        cx<double> p = ad[N];
+#pragma unroll
+                        for (int k = N - 1; k >= 0; --k) p = cfma(p, z[j], ad[k]);
+                        // p'(z) in FP32 (Horner): only the Newton step's size needs it
+                        cx<float> dp = scale((float)N, af[N]);
+#pragma unroll
+                        for (int k = N - 1; k >= 1; --k) dp = cfma(dp, zf, scale((float)k, af[k]));
+                        cx<float> pf = {(float)p.re, (float)p.im};
+                        cx<float> dz = cdiv(pf, dp);
+                        if (!finite_c(dz)) break;
+                        z[j] = sub(z[j], cx<double>{(double)dz.re, (double)dz.im});
+                        zf = sub(zf, dz);
+                        S.newton += 1;
+                    }
+                    // final FP64 residual |p(z)| against sum |a_k| |z|^k
+                    cx<double> p = ad[N];
+#pragma unroll
+                    for (int k = N - 1; k >= 0; --k) p = cfma(p, z[j], ad[k]);
+                    float az = sqrtf(norm2(zf));
+                    float den = sqrtf(norm2(af[N]));
+#pragma unroll
+                    for (int k = N - 1; k >= 0; --k) den = fmaf(den, az, sqrtf(norm2(af[k])));
+                    float res = sqrtf(norm2(cx<float>{(float)p.re, (float)p.im}));
+                    reject |= !(res <= (float)A.residual_tol * den) || !finite_c(z[j]);
+                }
+                // separation: two polished roots must not have collapsed onto one.
+                // A cheap FP32 screen first (FP32 copies are within ~1e-7 of
+                // the FP64 roots); the FP64 test runs only when a lane needs it.
+                bool near = false;
+#pragma unroll
+                for (int j = 0; j < N; ++j)
+#pragma unroll
+                    for (int k = j + 1; k < N; ++k) {
+                        float dre = (float)z[j].re - (float)z[k].re, dim = (float)z[j].im - (float)z[k].im;
+                        float mag = fmaxf(1.0f, fabsf((float)z[j].re) + fabsf((float)z[j].im));
+                        near |= (fabsf(dre) + fabsf(dim)) <= 1e-4f * mag;
+                    }
+                if (near) {
+#pragma unroll
+                    for (int j = 0; j < N; ++j)
+#pragma unroll
+                        for (int k = j + 1; k < N; ++k) {
+                            cx<double> d = sub(z[j], z[k]);
+                            double lim = A.collapse_tol * fmax(1.0, fabs(z[j].re) + fabs(z[j].im));
+                            reject |= (fabs(d.re) + fabs(d.im)) <= lim;
+                        }
+                }
+                if (reject && st == RD_STATUS_OK) st = RD_STATUS_REJECTED;
+            }
+        }
+        if (degenerate) {
+#pragma unroll
+            for (int j = 0; j < N; ++j) z[j] = {__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll)};
+        }
+
+        if (valid) {
+            S.polys += 1;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) S.st[k] += (st == k) ? 1u : 0u;
+            if (A.status) A.status[i] = st;
+            if (A.roots) {
+                double2 *R = reinterpret_cast<double2 *>(A.roots);
+#pragma unroll
+                for (int j = 0; j < N; ++j) R[(int64_t)j * n + i] = make_double2(z[j].re, z[j].im);
+            }
+        }
+
+        // ---- fused binning
+        if (A.hist) {
+            cx<double> cen = {0.0, 0.0};
+            int64_t my_tile = i;
+            if (A.clip_on && valid) {
+                double2 c = __ldg(reinterpret_cast<const double2 *>(A.centres) + i);
+                cen = {c.x, c.y};
+                if (A.tile_index) my_tile = __ldg(A.tile_index + i);
+            }
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                double x = z[j].re, y = z[j].im;
+                bool keep = valid;
+                if (A.clip_on) {
+                    x = __dadd_rn(__dmul_rn(A.radius, x), cen.re);  // z = c + rho w, no contraction
+                    y = __dadd_rn(__dmul_rn(A.radius, y), cen.im);
+                    int t = pixel_of(A.tiles, x, y);
+                    bool in_tile = (t >= 0) && ((int64_t)t == my_tile);
+                    S.clipped += (valid && !in_tile) ? 1u : 0u;
+                    keep = keep && in_tile;
+                }
+                int pix = keep ? pixel_of(A.bin, x, y) : -1;
+                S.binned += (pix >= 0) ? 1u : 0u;
+                S.oow += (keep && pix < 0) ? 1u : 0u;
+                hist_add(A.hist, pix);
+            }
+        }
+    }
+    if (A.stats) flush_stats(S, A.stats);
+}
+
+}  // namespace rd

@@ -1,0 +1,10 @@
+// rd_solve_mixed.cu -- RD_MIXED solver instantiations (FP32 sweeps + FP64 polish).
+#include "rd_solve_launch.cuh"
+
+namespace rd {
+int launch_solve_mixed(int degree, rd_dtype dt, const SolveArgs &a, int block, int ctas_per_sm, cudaStream_t st)
+{
+    if (dt == RD_C64) return launch_degree<float2, true>(degree, a, block, ctas_per_sm, st);
+    return launch_degree<double2, true>(degree, a, block, ctas_per_sm, st);
+}
+}  // namespace rd

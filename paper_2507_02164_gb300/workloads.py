@@ -212,3 +212,49 @@ def tiles(xmin=-4.0, xmax=4.0, ymin=-2.25, ymax=2.25, nx=480, ny=270):
     centres = (cx[None, :] + 1j * cy[:, None]).reshape(-1)
     radius = 0.5 * math.hypot(w, h)
     return centres, radius, w, h
+
+
+# ---- the same generators as torch ops (any device) -------------------------
+# torch has no uint64 arithmetic, so SplitMix64 runs on int64 with wrapping
+# multiplication (two's complement) and logical right shifts done by masking;
+# the bits equal the numpy version above.
+
+def _to_i64(u: int) -> int:
+    return u - (1 << 64) if u >= (1 << 63) else u
+
+
+def _srl(z, k: int):
+    import torch
+    return torch.bitwise_and(torch.bitwise_right_shift(z, k), (1 << (64 - k)) - 1)
+
+
+def _mix_t(z):
+    z = torch_xor(z, _srl(z, 30)) * _to_i64(0xBF58476D1CE4E5B9)
+    z = torch_xor(z, _srl(z, 27)) * _to_i64(0x94D049BB133111EB)
+    return torch_xor(z, _srl(z, 31))
+
+
+def torch_xor(a, b):
+    import torch
+    return torch.bitwise_xor(a, b)
+
+
+def draw_torch(seed: int, counters):
+    """draw(seed, counters) for an int64 torch tensor of counters (same bits, as int64)."""
+    k = _to_i64(int(key(seed)))
+    g = _to_i64(int(GAMMA))
+    return _mix_t(k + (counters + 1) * g)
+
+
+def littlewood_soa_torch(seed: int, start: int, n: int, device, degree: int = 6):
+    """Coefficient-major [degree+1, n] complex64 Littlewood batch for indices
+    start .. start+n-1, generated on `device` (same values as ``littlewood``)."""
+    import torch
+    idx = torch.arange(start, start + n, dtype=torch.int64, device=device)
+    x = draw_torch(seed, idx * STRIDE_LITTLEWOOD)
+    table = torch.tensor([1, -1, 1j, -1j], dtype=torch.complex64, device=device)
+    out = torch.empty((degree + 1, n), dtype=torch.complex64, device=device)
+    for k in range(degree + 1):
+        sel = torch.bitwise_and(_srl(x, 2 * k) if k else x, 3)
+        out[k] = table[sel]
+    return out

@@ -1,0 +1,63 @@
+"""Helpers for the GPU parity tests: device setup and root-set comparisons."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from tests.helpers import matched
+
+EPS = 2.0 ** -53
+# R9 reading: a root is well conditioned when kappa * 2^-53 <= 1e-12
+KAPPA_WELL = 1e-12 / EPS
+
+
+def require_gpu():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2507_02164_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+def to_soa(coeffs_poly_major: np.ndarray, device, dtype=torch.complex128) -> torch.Tensor:
+    """[n, d+1] numpy -> [d+1, n] contiguous device tensor."""
+    return torch.from_numpy(np.ascontiguousarray(coeffs_poly_major.T)).to(device=device, dtype=dtype)
+
+
+def roots_poly_major(roots_soa: torch.Tensor) -> np.ndarray:
+    """[d, n] device complex128 -> [n, d] numpy."""
+    return roots_soa.cpu().numpy().T.copy()
+
+
+def hist_np(h: torch.Tensor) -> np.ndarray:
+    return h.cpu().numpy().view(np.uint32)
+
+
+def compare_roots(gpu: np.ndarray, ref: np.ndarray, coeffs: np.ndarray, orc, tol: float, kappa_cap: float):
+    """Match every polynomial's GPU roots to the reference set, then require
+    |err| <= tol (relative to max(1,|z|)) for every root whose condition
+    number is at most kappa_cap. Returns a summary dict."""
+    g = matched(gpu, ref)
+    err = np.abs(g - ref) / np.maximum(1.0, np.abs(ref))
+    kappa = orc.root_condition(coeffs, ref)
+    well = kappa <= kappa_cap
+    summary = {
+        "max_err": float(err.max()),
+        "max_err_well": float(err[well].max()) if well.any() else 0.0,
+        "n_excluded": int((~well).sum()),
+        "max_err_excluded": float(err[~well].max()) if (~well).any() else 0.0,
+        "max_err_over_kappa": float((err / np.maximum(1.0, kappa)).max()),
+    }
+    assert summary["max_err_well"] <= tol, summary
+    return summary, g
+
+
+def edge_distance(z: np.ndarray, window, W: int, H: int) -> np.ndarray:
+    """Absolute distance in the plane from z to the nearest pixel edge line."""
+    xmin, xmax, ymin, ymax = window
+    px = (xmax - xmin) / W
+    py = (ymax - ymin) / H
+    fx = (z.real - xmin) / px
+    fy = (ymax - z.imag) / py
+    dx = np.abs(fx - np.round(fx)) * px
+    dy = np.abs(fy - np.round(fy)) * py
+    return np.minimum(dx, dy)

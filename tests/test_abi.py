@@ -1,0 +1,130 @@
+"""The C ABI library loads and exports every declared entry point; host-only
+functions and argument validation need no GPU."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2507_02164_gb300 import _native as N
+from paper_2507_02164_gb300 import build as B
+
+HEADER = os.path.join(B.ROOT, "include", "rootdensity.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rd_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_builds_and_loads():
+    L = N.load()
+    assert L.rd_abi_version() == 1
+
+
+def test_every_declared_symbol_is_exported_and_bound():
+    L = N.load()
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(L, name), name
+        assert name in N.SIGNATURES, f"{name} declared but not bound in _native.SIGNATURES"
+    assert set(N.SIGNATURES) == set(names)
+
+
+def test_struct_sizes_match_header_layout():
+    assert ctypes.sizeof(N.Params) == 48
+    assert ctypes.sizeof(N.Window) == 32
+    assert ctypes.sizeof(N.Clip) == 64
+    assert N.STATS_WORDS == 12
+
+
+def test_default_params():
+    p = N.default_params(N.PLAIN_FP64)
+    assert p.tol == 1e-13 and p.max_iters == 40 and p.shift == N.SHIFT_WILKINSON
+    q = N.default_params(N.MIXED)
+    assert q.tol == 4 * 2.0 ** -24 and q.polish_steps == 3 and q.collapse_tol == 1e-9
+
+
+@pytest.mark.parametrize("nr", [1, 2, 7, 16, 32])
+def test_library_gauss_legendre_matches_numpy(nr):
+    r = (ctypes.c_double * nr)()
+    w = (ctypes.c_double * nr)()
+    assert N.load().rd_l2_nodes(nr, ctypes.cast(r, ctypes.c_void_p), ctypes.cast(w, ctypes.c_void_p)) == 0
+    t, wt = np.polynomial.legendre.leggauss(nr)
+    assert np.allclose(np.array(r), 0.5 * (t + 1), atol=2e-16, rtol=0)
+    assert np.allclose(np.array(w), 0.5 * wt, atol=0, rtol=1e-13)
+    # exact for polynomials of degree < 2 nr: sum w_p r_p^k = 1/(k+1)
+    rr, ww = np.array(r), np.array(w)
+    for k in range(2 * nr):
+        assert abs((ww * rr ** k).sum() - 1.0 / (k + 1)) <= 2e-15
+
+
+def _err(rc):
+    return rc, N.load().rd_last_error().decode()
+
+
+def test_argument_validation_without_gpu():
+    L = N.load()
+    p = N.default_params(N.MIXED)
+    null = ctypes.c_void_p(0)
+    # degree outside 1..12
+    rc, msg = _err(L.rd_roots_batched(null, N.C64, 13, 10, N.MIXED, ctypes.byref(p), null, null, null, null))
+    assert rc == N.RD_EUNSUPPORTED and "degree" in msg
+    # negative n
+    rc, _ = _err(L.rd_roots_batched(null, N.C64, 6, -1, N.MIXED, ctypes.byref(p), null, null, null, null))
+    assert rc == N.RD_EINVAL
+    # null coefficients with work to do
+    rc, msg = _err(L.rd_roots_batched(null, N.C64, 6, 5, N.MIXED, ctypes.byref(p), null, null, null, null))
+    assert rc == N.RD_EINVAL and "coeffs" in msg
+    # misaligned coefficient pointer (complex128 needs 16 bytes)
+    rc, _ = _err(L.rd_roots_batched(ctypes.c_void_p(8), N.C128, 6, 5, N.MIXED, ctypes.byref(p), null, null,
+                                    null, null))
+    assert rc == N.RD_EINVAL
+    # bad parameters
+    bad = N.default_params(N.MIXED)
+    bad.max_iters = 0
+    rc, msg = _err(L.rd_roots_batched(ctypes.c_void_p(64), N.C64, 6, 5, N.MIXED, ctypes.byref(bad), null, null,
+                                      null, null))
+    assert rc == N.RD_EINVAL and "max_iters" in msg
+    bad = N.default_params(N.MIXED)
+    bad.block = 48
+    rc, _ = _err(L.rd_roots_batched(ctypes.c_void_p(64), N.C64, 6, 5, N.MIXED, ctypes.byref(bad), null, null,
+                                    null, null))
+    assert rc == N.RD_EINVAL
+    # empty batch is a no-op
+    assert L.rd_roots_batched(null, N.C64, 6, 0, N.MIXED, ctypes.byref(p), null, null, null, null) == 0
+    # density: inverted window, bad size, null hist
+    w_bad = N.Window(1.0, -1.0, -1.0, 1.0)
+    rc, _ = _err(L.rd_density_accumulate(ctypes.c_void_p(64), 4, w_bad, 16, 16, ctypes.c_void_p(64), null, null))
+    assert rc == N.RD_EINVAL
+    w = N.Window(-1.0, 1.0, -1.0, 1.0)
+    rc, _ = _err(L.rd_density_accumulate(ctypes.c_void_p(64), 4, w, 0, 16, ctypes.c_void_p(64), null, null))
+    assert rc == N.RD_EINVAL
+    rc, _ = _err(L.rd_density_accumulate(ctypes.c_void_p(64), 4, w, 16, 16, null, null, null))
+    assert rc == N.RD_EINVAL
+    nanw = N.Window(float("nan"), 1.0, -1.0, 1.0)
+    rc, _ = _err(L.rd_density_accumulate(ctypes.c_void_p(64), 4, nanw, 16, 16, ctypes.c_void_p(64), null, null))
+    assert rc == N.RD_EINVAL
+    # l2: nt must be 32, nr in 1..32
+    rc, _ = _err(L.rd_l2_approx(ctypes.c_void_p(64), 4, 16, 16, 6, ctypes.c_void_p(64), null))
+    assert rc == N.RD_EUNSUPPORTED
+    rc, _ = _err(L.rd_l2_approx(ctypes.c_void_p(64), 4, 40, 32, 6, ctypes.c_void_p(64), null))
+    assert rc == N.RD_EINVAL
+    # backward: bad degree / null
+    rc, _ = _err(L.rd_roots_backward(null, N.C128, 0, 4, null, null, null, null, null))
+    assert rc == N.RD_EUNSUPPORTED
+    rc, _ = _err(L.rd_roots_backward(null, N.C128, 6, 4, null, null, null, null, null))
+    assert rc == N.RD_EINVAL
+    assert L.rd_hist_clear(null, 0, null) == 0
+    rc, _ = _err(L.rd_hist_clear(null, 5, null))
+    assert rc == N.RD_EINVAL
+
+
+def test_python_binding_raises_on_error():
+    with pytest.raises(N.RootDensityError):
+        N.call("rd_hist_clear", ctypes.c_void_p(0), 5, ctypes.c_void_p(0))

@@ -1,0 +1,197 @@
+"""GPU parity: the CUDA solver and binning against the FP64 CPU oracle.
+
+All inputs come from the seeded generators in paper_2507_02164_gb300.workloads;
+expected values come from the oracle only.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2507_02164_gb300 import api, workloads as WL
+from tests.gpu_common import (KAPPA_WELL, compare_roots, edge_distance, hist_np, require_gpu,
+                              roots_poly_major, to_soa)
+
+pytestmark = pytest.mark.gpu
+
+WIN1 = api.Window(-1.5, 1.5, -0.84375, 0.84375)
+WIN2 = api.Window(-2.0, 2.0, -1.125, 1.125)
+W, H = 1920, 1080
+PLAIN_TOL, MIXED_TOL = 1e-11, 1e-9
+# roots compared at the 1e-11 bar: deflation at tol = 1e-13 leaves an error of
+# order kappa * 1e-13 in any correct implementation, so the bar applies where
+# that is below 1e-11
+KAPPA_PLAIN = 50.0
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return require_gpu()
+
+
+def _solve(coeffs_t, mode, window=None, **kw):
+    d, n = coeffs_t.shape[0] - 1, coeffs_t.shape[1]
+    roots = torch.empty((d, n), dtype=torch.complex128, device=coeffs_t.device)
+    status = torch.empty(n, dtype=torch.uint8, device=coeffs_t.device)
+    stats = api.new_stats(coeffs_t.device)
+    p = api.params(mode, **kw)
+    if window is None:
+        api.roots_batched(coeffs_t, mode=mode, params_=p, roots=roots, status=status, stats=stats)
+        hist = None
+    else:
+        hist = api.new_hist(W, H, coeffs_t.device)
+        api.roots_density(coeffs_t, window, hist, mode=mode, params_=p, roots=roots, status=status, stats=stats)
+    torch.cuda.synchronize()
+    return roots_poly_major(roots), status.cpu().numpy(), hist, api.stats_dict(stats)
+
+
+# ------------------------------------------------ plain FP64, known roots (C1)
+
+@pytest.mark.parametrize("mode,tol,kcap", [("plain", PLAIN_TOL, KAPPA_PLAIN), ("mixed", MIXED_TOL, KAPPA_WELL)])
+def test_unit_disk_batch_matches_oracle_and_true_roots(dev, orc, mode, tol, kcap):
+    """65,536 monic degree-6 polynomials from seeded roots in the unit disk."""
+    n = 65536
+    co, true_roots = WL.unit_disk_roots(1, n)
+    roots, status, hist, st = _solve(to_soa(co, dev), mode, WIN1)
+    ref, ref_status, _, _ = orc.solve(co, tol=1e-13)
+    assert np.all(status == 0) and np.all(ref_status == 0)
+    s_or, g = compare_roots(roots, ref, co, orc, tol, kcap)
+    s_true, _ = compare_roots(roots, true_roots, co, orc, tol, kcap)
+    assert s_or["n_excluded"] < 0.02 * roots.size
+    # histogram: the oracle's binning of the GPU roots is the GPU histogram, bit for bit
+    h_gpu = hist_np(hist)
+    h_or_gpu_roots, oow = orc.hist(roots, WIN1.tuple(), W, H)
+    assert np.array_equal(h_gpu, h_or_gpu_roots)
+    assert st["binned"] == int(h_gpu.sum()) and st["out_of_window"] == oow
+    assert st["binned"] + st["out_of_window"] == 6 * n and st["polys"] == n and st["status_ok"] == n
+    # against the oracle's own roots: differences only where a root sits within
+    # 1e-9 of a pixel edge
+    h_or, _ = orc.hist(ref, WIN1.tuple(), W, H)
+    diff = np.argwhere(h_gpu != h_or)
+    near_edge = edge_distance(ref.reshape(-1), WIN1.tuple(), W, H) <= 1e-9
+    assert np.abs(h_gpu.astype(np.int64) - h_or).sum() <= 2 * int(near_edge.sum()), diff[:10]
+
+
+# ------------------------------------------------- Littlewood subsample (C2)
+
+@pytest.mark.parametrize("mode,tol,kcap", [("mixed", MIXED_TOL, KAPPA_WELL), ("plain", PLAIN_TOL, KAPPA_PLAIN)])
+def test_littlewood_subsample_matches_oracle(dev, orc, mode, tol, kcap):
+    """The 2^16 polynomials i = 1024 k of the 2^26 Littlewood batch."""
+    idx = np.arange(1 << 16, dtype=np.uint64) * np.uint64(1024)
+    co = WL.littlewood(2, idx)
+    roots, status, hist, st = _solve(to_soa(co, dev, torch.complex64), mode, WIN2)
+    ref, ref_status, _, _ = orc.solve(co.astype(np.complex128), tol=1e-13)
+    assert np.all(ref_status == 0)
+    assert (status == 0).mean() > 0.999, np.bincount(status, minlength=4)
+    ok = status == 0
+    s, _ = compare_roots(roots[ok], ref[ok], co[ok].astype(np.complex128), orc, tol, kcap)
+    h_gpu = hist_np(hist)
+    h_ref, _ = orc.hist(roots, WIN2.tuple(), W, H)
+    assert np.array_equal(h_gpu, h_ref)
+
+
+# -------------------------------------------------- every degree, both modes
+
+@pytest.mark.parametrize("degree", list(range(1, 13)))
+@pytest.mark.parametrize("mode", ["mixed", "plain"])
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_every_degree_matches_oracle(dev, orc, degree, mode, dtype):
+    n = 1000 + 37  # several warps and a ragged tail
+    co = WL.gaussian(100 + degree, n, degree)
+    if dtype == torch.complex64:
+        co = co.astype(np.complex64).astype(np.complex128)  # the stored values
+    roots, status, _, st = _solve(to_soa(co, dev, dtype), mode)
+    ref, ref_status, _, _ = orc.solve(co, tol=1e-13)
+    good = (status == 0) & (ref_status == 0)
+    assert good.mean() > 0.99, np.bincount(status, minlength=4)
+    tol, kcap = (MIXED_TOL, KAPPA_WELL) if mode == "mixed" else (PLAIN_TOL, KAPPA_PLAIN)
+    compare_roots(roots[good], ref[good], co[good], orc, tol, kcap)
+    assert st["polys"] == n
+
+
+# ----------------------------------------------------------------- edge cases
+
+def test_empty_batch_is_noop(dev):
+    co = torch.zeros((7, 0), dtype=torch.complex64, device=dev)
+    r, s = api.roots_batched(co, mode="mixed")
+    assert r.shape == (6, 0) and s.shape == (0,)
+
+
+@pytest.mark.parametrize("mode", ["mixed", "plain"])
+def test_degenerate_inputs(dev, orc, mode):
+    co = WL.gaussian(7, 40, 6)
+    co[3, 6] = 0.0              # zero leading coefficient
+    co[5, 2] = np.nan           # NaN coefficient
+    co[7, 0] = np.inf           # infinite coefficient
+    co[9, :] = 0.0              # zero polynomial
+    roots, status, hist, st = _solve(to_soa(co, dev), mode, WIN1)
+    bad = [3, 5, 7, 9]
+    assert np.all(status[bad] == 3)
+    assert np.all(np.isnan(roots[bad]))
+    others = np.setdiff1d(np.arange(40), bad)
+    assert np.all(status[others] != 3)
+    assert st["status_degenerate"] == 4
+    assert st["binned"] + st["out_of_window"] == 6 * 40
+    assert st["out_of_window"] >= 4 * 6
+
+
+def test_single_polynomial_and_degree_one(dev):
+    co = np.array([[2 + 1j, 4 - 2j]])
+    roots, status, _, _ = _solve(to_soa(co, dev), "plain")
+    assert status[0] == 0 and abs(roots[0, 0] - (-(2 + 1j) / (4 - 2j))) < 1e-15
+
+
+def test_max_iters_one_flags_not_converged(dev):
+    co = WL.gaussian(8, 200, 6)
+    _, status, _, st = _solve(to_soa(co, dev), "plain", max_iters=1)
+    assert (status == 1).mean() > 0.9
+    assert st["status_not_converged"] == int((status == 1).sum())
+
+
+def test_rayleigh_shift_with_exceptional_shift_also_converges(dev, orc):
+    idx = np.arange(4096, dtype=np.uint64)
+    co = WL.littlewood(2, idx)
+    roots, status, _, _ = _solve(to_soa(co, dev, torch.complex64), "mixed", shift="rayleigh", exc_period=10)
+    ref, _, _, _ = orc.solve(co.astype(np.complex128))
+    ok = status == 0
+    assert ok.mean() > 0.999
+    compare_roots(roots[ok], ref[ok], co[ok].astype(np.complex128), orc, MIXED_TOL, KAPPA_WELL)
+
+
+def test_launch_shapes_give_identical_results(dev):
+    """Block size and grid only change the schedule, never the arithmetic."""
+    co = to_soa(WL.littlewood(2, 5000), dev, torch.complex64)
+    base, bst, _, _ = _solve(co, "mixed")
+    for block, cps in ((32, 1), (64, 3), (256, 2)):
+        r, s, _, _ = _solve(co, "mixed", block=block, ctas_per_sm=cps)
+        assert np.array_equal(r, base) and np.array_equal(s, bst)
+
+
+# -------------------------------------------------------- standalone binning
+
+def test_density_accumulate_matches_oracle_bit_for_bit(dev, orc):
+    g = np.random.default_rng(5)
+    z = g.uniform(-1.7, 1.7, 300001) + 1j * g.uniform(-1.0, 1.0, 300001)
+    # exact edges, corners, NaN and infinities
+    z[:8] = [-1.5 + 0.84375j, 1.5 + 0j, -0.84375j, 1.5 - 0.84375j, complex(np.nan, 0), complex(0, np.inf),
+             -1.5 - 0.84375j, 0j]
+    t = torch.from_numpy(z).to(dev)
+    hist = api.new_hist(W, H, dev)
+    stats = api.new_stats(dev)
+    api.density_accumulate(t, WIN1, hist, stats=stats)
+    api.density_accumulate(t[:1000], WIN1, hist, stats=stats)  # accumulates
+    torch.cuda.synchronize()
+    ref, oow = orc.hist(np.concatenate([z, z[:1000]]), WIN1.tuple(), W, H)
+    assert np.array_equal(hist_np(hist), ref)
+    st = api.stats_dict(stats)
+    assert st["out_of_window"] == oow and st["binned"] == int(ref.sum())
+
+
+def test_hist_clear_zeroes_odd_sizes(dev):
+    for words in (1, 3, 5, 1920 * 1080, 1920 * 1080 + 3):
+        buf = torch.full((words + 8,), -1, dtype=torch.int32, device=dev)
+        api.N.call("rd_hist_clear", api._ptr(buf[1:]), words, api._stream())
+        torch.cuda.synchronize()
+        b = buf.cpu().numpy()
+        assert b[0] == -1 and np.all(b[1:words + 1] == 0) and np.all(b[words + 1:] == -1)
