@@ -66,12 +66,16 @@ typedef struct {
     double residual_tol;   /* RD_MIXED: reject when |p(z)| > residual_tol * sum_k |a_k||z|^k;
                               <= 0 means 64 * d * 2^-53                                         */
     double collapse_tol;   /* RD_MIXED: reject when two roots lie within collapse_tol * max(1,|z|) */
-    int32_t block;         /* threads per CTA, multiple of 32 in [32, 1024]; 0 = tuned default   */
+    int32_t block;         /* threads per CTA, multiple of 32 in [32, 256]; 0 = tuned default    */
     int32_t ctas_per_sm;   /* grid = ctas_per_sm x SM count; 0 = tuned default                   */
+    int32_t polish_extra;  /* RD_MIXED: further Newton steps, p and p' both in FP64, for a root
+                              that fails the residual check after polish_steps (0..16)          */
+    int32_t reserved;      /* must be 0                                                         */
 } rd_params;
 
 /* Defaults: plain tol 1e-13, mixed tol 4 * 2^-24, max_iters 40, Wilkinson
- * shift, exc_period 10, 3 polish steps, residual 64 d 2^-53, collapse 1e-9. */
+ * shift, exc_period 10, 3 polish steps, 5 extra steps, residual 64 d 2^-53,
+ * collapse 1e-9. */
 void rd_default_params(rd_mode mode, rd_params *out);
 
 /* Root-density window: pixel column ix = floor((x - xmin) * W / (xmax - xmin)),

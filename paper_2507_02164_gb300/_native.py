@@ -22,7 +22,8 @@ class Params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int32), ("shift", ctypes.c_int32),
                 ("exc_period", ctypes.c_int32), ("polish_steps", ctypes.c_int32),
                 ("residual_tol", ctypes.c_double), ("collapse_tol", ctypes.c_double),
-                ("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+                ("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("polish_extra", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Window(ctypes.Structure):

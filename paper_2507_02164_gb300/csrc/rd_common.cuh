@@ -126,6 +126,58 @@ __device__ __forceinline__ void rot_cols(T c, cx<T> s, cx<T> &x, cx<T> &y)
     y = ny;
 }
 
+// ---- FP32 <-> FP64 without the FP64 pipe ---------------------------------
+// On GB300 the FP64 pipe runs 2 lane-ops per SM per clock and conversions
+// between float and double issue to it. These helpers build the result from
+// the IEEE-754 bit layouts with integer instructions instead.
+
+// Exact float -> double (normal, subnormal, zero, inf and NaN inputs).
+__device__ __forceinline__ double f2d(float f)
+{
+    unsigned u = __float_as_uint(f);
+    unsigned sign = u & 0x80000000u;
+    unsigned e = (u >> 23) & 0xffu;
+    unsigned m = u & 0x7fffffu;
+    unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);  // exponent bias 127 -> 1023
+    unsigned lo = m << 29;
+    if (e == 0u) {
+        // zero, or subnormal m * 2^-149: shift the leading one to bit 23
+        int sh = __clz((int)m) - 8;
+        unsigned mm = (m << (sh & 31)) & 0x7fffffu;
+        hi = m ? (sign | ((unsigned)(897 - sh) << 20) | (mm >> 3)) : sign;
+        lo = m ? (mm << 29) : 0u;
+    }
+    if (e == 255u) hi = sign | 0x7ff00000u | (m >> 3);  // inf / NaN (payload kept)
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// double -> float rounded to nearest (ties away from zero). Magnitudes below
+// the normal FP32 range become signed zero and above it +-FLT_MAX; inf and
+// NaN are kept. Used for Newton step sizes, residual magnitudes and pixel
+// screening, which need a correctly scaled FP32 value, not the last bit.
+__device__ __forceinline__ float d2f(double d)
+{
+    unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    unsigned sign = hi & 0x80000000u;
+    unsigned ed = (hi >> 20) & 0x7ffu;
+    int e = (int)ed - 1023 + 127;
+    unsigned bits = sign | ((unsigned)(e & 0xff) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    bits += (lo >> 28) & 1u;  // round on the first dropped bit (may carry into the exponent)
+    bits = e <= 0 ? sign : bits;
+    bits = e >= 255 ? (sign | 0x7f7fffffu) : bits;
+    if (ed == 0x7ffu) bits = sign | 0x7f800000u | ((((hi & 0xfffffu) | lo) != 0u) ? 0x400000u : 0u);
+    return __uint_as_float(bits);
+}
+
+// isfinite for a double, on its exponent bits
+__device__ __forceinline__ bool finite_bits(double d)
+{
+    return ((((unsigned)__double2hiint(d)) >> 20) & 0x7ffu) != 0x7ffu;
+}
+
+__device__ __forceinline__ cx<double> f2d(cx<float> a) { return {f2d(a.re), f2d(a.im)}; }
+__device__ __forceinline__ cx<float> d2f(cx<double> a) { return {d2f(a.re), d2f(a.im)}; }
+
 // ---- warp helpers --------------------------------------------------------
 
 __device__ __forceinline__ unsigned warp_sum_u32(unsigned v)
@@ -140,17 +192,20 @@ struct Binner {
     int W, H;
 };
 
-// Pixel index of z, or -1 when outside the window or NaN. FP64 throughout, no
-// contraction: fx = (x - xmin) * sx, fy = (ymax - y) * sy.
+// Pixel index of z, or -1 when outside the window or NaN. FP64, no
+// contraction: fx = (x - xmin) * sx, fy = (ymax - y) * sy, then
+// ix = floor(fx), iy = floor(fy). The window test 0 <= fx < W is done on the
+// floored integers (equivalent, as W is an integer; the conversion saturates
+// for huge values) so that no FP64 comparison is issued; NaN is caught on
+// the exponent bits.
 __device__ __forceinline__ int pixel_of(const Binner &b, double x, double y)
 {
     double fx = __dmul_rn(__dsub_rn(x, b.xmin), b.sx);
     double fy = __dmul_rn(__dsub_rn(b.ymax, y), b.sy);
-    bool in = (fx >= 0.0) && (fx < (double)b.W) && (fy >= 0.0) && (fy < (double)b.H);
-    if (!in) return -1;
-    int ix = (int)fx;  // fx >= 0, so truncation is floor
-    int iy = (int)fy;
-    return iy * b.W + ix;
+    int ix = __double2int_rd(fx);
+    int iy = __double2int_rd(fy);
+    bool in = finite_bits(x) && finite_bits(y) && ix >= 0 && ix < b.W && iy >= 0 && iy < b.H;
+    return in ? iy * b.W + ix : -1;
 }
 
 // Warp-aggregated histogram increment: lanes holding the same pixel elect one
@@ -166,33 +221,39 @@ __device__ __forceinline__ void hist_add(uint32_t *hist, int pix)
 }
 
 // ---- per-call counters ---------------------------------------------------
+// rd_stats word indices
+enum : int { ST_POLYS = 0, ST_STATUS0 = 1, ST_SWEEPS = 5, ST_PAIRS = 6, ST_ROTS = 7, ST_NEWTON = 8,
+             ST_BINNED = 9, ST_OOW = 10, ST_CLIPPED = 11, ST_WORDS = 12 };
 
-struct LaneStats {
-    unsigned polys = 0, st[4] = {0, 0, 0, 0}, sweeps = 0, pairs = 0, rots = 0, newton = 0,
-             binned = 0, oow = 0, clipped = 0;
+// Counters are summed over the warp as soon as they are produced and kept
+// per CTA in shared memory, so no thread carries them in registers through
+// the solve. Every member function must be reached by all 32 lanes together.
+struct CtaStats {
+    unsigned long long *acc;  // ST_WORDS entries in shared memory, or null
+    __device__ void add(int k, unsigned v) const
+    {
+        if (!acc) return;
+        unsigned w = __reduce_add_sync(0xffffffffu, v);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(acc + k, (unsigned long long)w);
+    }
 };
 
-// Sum the lane counters of the whole CTA and add them to *out (one atomic per
-// counter per CTA). Every thread of the CTA must call it.
-__device__ inline void flush_stats(const LaneStats &s, rd_stats *out)
+// Zero the CTA's counters (all threads of the CTA call this).
+__device__ inline CtaStats stats_begin(unsigned long long *smem, rd_stats *out)
 {
-    __shared__ unsigned long long acc[13];
-    if (threadIdx.x < 13) acc[threadIdx.x] = 0;
+    if (!out) return CtaStats{nullptr};
+    if (threadIdx.x < ST_WORDS) smem[threadIdx.x] = 0;
     __syncthreads();
-    unsigned v[13] = {s.polys, s.st[0], s.st[1], s.st[2], s.st[3], s.sweeps, s.pairs,
-                      s.rots, s.newton, s.binned, s.oow, s.clipped, 0};
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        unsigned w = warp_sum_u32(v[k]);
-        if ((threadIdx.x & 31) == 0 && w) atomicAdd(&acc[k], (unsigned long long)w);
-    }
+    return CtaStats{smem};
+}
+
+// Add the CTA's counters to *out, one atomic per non-zero word (all threads call this).
+__device__ inline void stats_end(const CtaStats &cs, rd_stats *out)
+{
+    if (!out) return;
     __syncthreads();
-    if (out && threadIdx.x < 12 && acc[threadIdx.x]) {
-        unsigned long long *o = reinterpret_cast<unsigned long long *>(out);
-        // rd_stats field order: polys, status[4], sweeps, pair_updates, rotations,
-        // newton_steps, binned, out_of_window, clipped
-        atomicAdd(o + threadIdx.x, acc[threadIdx.x]);
-    }
+    unsigned long long *o = reinterpret_cast<unsigned long long *>(out);
+    if (threadIdx.x < ST_WORDS && cs.acc[threadIdx.x]) atomicAdd(o + threadIdx.x, cs.acc[threadIdx.x]);
 }
 
 }  // namespace rd

@@ -15,19 +15,23 @@ __global__ void __launch_bounds__(256) density_kernel(const double2 *__restrict_
     const int lane = threadIdx.x & 31;
     const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t warp_id = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    LaneStats S;
+    __shared__ unsigned long long acc[ST_WORDS];
+    const CtaStats S = stats_begin(acc, stats);
+    unsigned binned = 0, oow = 0;
     for (int64_t base = warp_id * 32; base < n; base += warps_total * 32) {
         int64_t i = base + lane;
         int pix = -1;
         if (i < n) {
             double2 z = __ldg(roots + i);
             pix = pixel_of(bin, z.x, z.y);
-            S.binned += pix >= 0 ? 1u : 0u;
-            S.oow += pix < 0 ? 1u : 0u;
+            binned += pix >= 0 ? 1u : 0u;
+            oow += pix < 0 ? 1u : 0u;
         }
         hist_add(hist, pix);
     }
-    if (stats) flush_stats(S, stats);
+    S.add(ST_BINNED, binned);
+    S.add(ST_OOW, oow);
+    stats_end(S, stats);
 }
 
 __global__ void __launch_bounds__(256) clear_kernel(uint32_t *p, int64_t words)

