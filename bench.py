@@ -247,13 +247,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     import torch
     import torch.distributed as dist
 
-    from paper_2507_02164_gb300 import api, build, workloads as WL
+    from paper_2507_02164_gb300 import api, build, dist as D, workloads as WL
 
     build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     n = 1 << args.log2n
-    start = rank * n
+    start, _ = D.shard_range(n, rank)
     coeffs = WL.littlewood_soa_torch(SEED, start, n, dev)
     win = api.Window(*WINDOW)
     hist = api.new_hist(W_PIX, H_PIX, dev)
@@ -288,12 +288,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 k_end[s].record(stream)
             t1.record(stream)
             torch.cuda.synchronize()
-        elapsed_ms = t0.elapsed_time(t1)
+        elapsed_ms = D.max_over_ranks(t0.elapsed_time(t1), device=dev)
         kern_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(k_start, k_end))
-        if world > 1:
-            t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            elapsed_ms = float(t.item())
         st = api.stats_dict(stats)
         return elapsed_ms, kern_ms, st, clk.summary()
 
@@ -320,7 +316,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if world > 1:
         torch.cuda.synchronize()
         t = time.perf_counter()
-        dist.reduce(hist, dst=0, op=dist.ReduceOp.SUM)
+        D.reduce_images(hist, dst=0)
         torch.cuda.synchronize()
         reduce_ms = 1e3 * (time.perf_counter() - t)
 
@@ -446,12 +442,8 @@ def run_e2e(args, coeffs_dev, win, dev, world):
         step()
     t1.record(comp)
     torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    from paper_2507_02164_gb300 import dist as D
+    ms = D.max_over_ranks(t0.elapsed_time(t1), device=dev)
     h2d = sum(h.numel() * h.element_size() for h in host)
     d2h = hist_h.numel() * hist_h.element_size() + stats_h.numel() * stats_h.element_size()
     return {"value": n * world * args.steps / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,

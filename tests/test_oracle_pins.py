@@ -448,3 +448,35 @@ def test_paper_cycle_model_consistency():
     assert abs(rate - gold["fpga_polys_per_s"]) / gold["fpga_polys_per_s"] < 0.01
     # the paper prints 16.5M for 3.33e5 * 50 = 16.65M
     assert abs(rate * (n - 1) * T - gold["fpga_equiv_qr_per_s"]) / gold["fpga_equiv_qr_per_s"] < 0.02
+
+
+# ------------------------------------------- helpers of the full pipeline
+
+def test_affine_map_is_centre_plus_radius_times_w(orc):
+    g = rng(21)
+    w = crandn(g, 50, 6)
+    c = crandn(g, 50)
+    got = orc.affine(w, c, 0.25)
+    assert np.array_equal(got, c[:, None] + 0.25 * w)
+
+
+def test_tiled_histogram_keeps_only_roots_in_their_own_tile(orc):
+    """A 4 x 2 tile grid over [0,4) x (0,2]: tile t = row * 4 + col, rows from
+    the top. Hand-placed roots: in own tile, in a neighbour, outside."""
+    win = (0.0, 4.0, 0.0, 2.0)
+    roots = np.array([[0.5 + 1.5j, 1.5 + 1.5j],     # poly 0 (tile 0): kept, dropped (tile 1)
+                      [3.5 + 0.5j, 3.9 + 0.1j],     # poly 1 (tile 7): both kept
+                      [9.0 + 0.0j, 2.5 + 0.5j]])    # poly 2 (tile 6): outside, kept
+    tiles = np.array([0, 7, 6])
+    h, oow, dropped = orc.hist_tiled(roots, tiles, 4, 2, win, W=8, H=4)
+    assert dropped == 2 and oow == 0 and h.sum() == 4
+    # pixels are 0.5 x 0.5: 0.5+1.5i -> row 1, col 1; 3.5+0.5i and 3.9+0.1i -> row 3, col 7;
+    # 2.5+0.5i -> row 3, col 5
+    assert h[1, 1] == 1 and h[3, 7] == 2 and h[3, 5] == 1
+
+
+def test_root_condition_closed_form(orc):
+    """p = (z-1)(z-2) = 2 - 3z + z^2: at z = 1, sum |a_k| |z|^k = 6 and
+    |p'(1)| = 1, so kappa = 6; at z = 2, (2 + 6 + 4) / (2 * 1) = 6."""
+    k = orc.root_condition(np.array([[2, -3, 1]], complex), np.array([[1, 2]], complex))
+    assert np.allclose(k, [[6.0, 6.0]], rtol=1e-15)
