@@ -56,7 +56,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--log2n", type=int, default=26, help="polynomials per GPU = 2^log2n")
+    ap.add_argument("--workload", choices=["littlewood", "uneven"], default="littlewood",
+                    help="littlewood: the 2^26 degree-6 batch of the metric; uneven: 2^24 polynomials of "
+                         "degree 2..12 (complex Gaussian, seed 3) in one CUDA-graph replay per step")
+    ap.add_argument("--log2n", type=int, default=None, help="polynomials per GPU = 2^log2n")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -220,26 +223,13 @@ def workload_config(args, ref_sample=None):
 
 # ---------------------------------------------------------------- GPU leg
 
-def algorithmic_flops(st: dict, mode: str):
-    """(FP32 flops, FP64 flops) of one solve launch from its own counters.
-
-    Sweep arithmetic (in the sweep precision): 20 flops per rotated entry pair
-    (real cosine: c x + s y and -conj(s) x + c y), 24 per Givens generation,
-    60 per sweep for shift, unshift, Wilkinson shift and deflation test.
-    Polish (mixed, per Newton step): p(z) by FP64 Horner, 8d + 2 FP64 flops;
-    p'(z) and the step size in FP32, 8d + 3. Final check per root: FP64
-    residual 8d, FP32 denominator 2d + 4. Binning: 4 FP64 flops per root.
-    """
-    d = DEGREE
-    sweep = 20.0 * st["pair_updates"] + 24.0 * st["rotations"] + 60.0 * st["sweeps"]
-    roots = d * st["polys"]
-    if mode == "mixed":
-        f32 = sweep + (8 * d + 3) * st["newton_steps"] + (2 * d + 4) * roots
-        f64 = (8 * d + 2) * st["newton_steps"] + 8 * d * roots + 4 * roots
-    else:
-        f32 = 0.0
-        f64 = sweep + 4 * roots
-    return f32, f64
+def algorithmic_flops(st: dict):
+    """(FP32 flops, FP64 flops) of the counted launches, as the kernel counted
+    them (rd_stats flops_fp32 / flops_fp64; convention in include/rootdensity.h:
+    20 flop per rotated pair, 24 per Givens pair, 60 per sweep in the sweep
+    precision; 8d+2 FP64 + 8d+3 FP32 per Newton step; 8d+4 FP64 + 2d+4 FP32
+    per polished root; 4 FP64 per binned root in the plain mode)."""
+    return float(st["flops_fp32"]), float(st["flops_fp64"])
 
 
 def run_ours(args, rank: int, world: int, local_rank: int):
@@ -330,7 +320,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     mhz = clk_mx.get("sm_max_mhz") or sm_max_mhz or 2070.0
     p32 = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6
     p64 = sms * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6
-    f32, f64 = algorithmic_flops(st_mx, "mixed")
+    f32, f64 = algorithmic_flops(st_mx)
     t_k = kern_mx * 1e-3
     frac32, frac64 = f32 / p32 / t_k, f64 / p64 / t_k
     traffic = profiled_traffic()
@@ -365,7 +355,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     }
     if plain is not None:
         pv = polys_total / (plain["elapsed_ms"] * 1e-3)
-        _, g64 = algorithmic_flops(plain["stats"], "plain")
+        _, g64 = algorithmic_flops(plain["stats"])
         line["plain_fp64"] = {
             "value": pv, "unit": UNIT, "ms_per_step": plain["elapsed_ms"] / args.steps,
             "kernel_ms": plain["kern_ms"], "fp64_frac": g64 / p64 / (plain["kern_ms"] * 1e-3),
@@ -451,8 +441,164 @@ def run_e2e(args, coeffs_dev, win, dev, world):
             "gpu_launches_per_step": 2 + nchunks}
 
 
+UNEVEN_SEED = 3
+UNEVEN_WINDOW = (-3.0, 3.0, -1.6875, 1.6875)
+UNEVEN_METRIC = "uneven-degree (2..12) complex polys rooted+binned/s, mixed, one CUDA-graph replay per step"
+
+
+def cpu_oracle_rate_uneven(seconds: float):
+    """Oracle solve + histogram of the uneven stream on the host cores for about `seconds`."""
+    import numpy as np
+
+    import oracle
+    from paper_2507_02164_gb300 import workloads as WL
+    oracle.build()
+    chunk = 1 << 15
+    done, elapsed, threads, k = 0, 0.0, 0, 0
+    while elapsed < seconds:
+        idx = np.arange(k * chunk, (k + 1) * chunk, dtype=np.uint64)
+        packed, deg, off = WL.uneven_gaussian(UNEVEN_SEED, idx)
+        packed = packed.astype(np.complex128)
+        rows_by_deg = {}
+        for d in range(2, 13):
+            sel = np.nonzero(deg == d)[0]
+            if sel.size:
+                rows_by_deg[d] = packed[(off[sel][:, None] + np.arange(d + 1)[None, :])]
+        t0 = time.perf_counter()
+        for d, rows in rows_by_deg.items():
+            roots, _, _, threads = oracle.solve(rows, tol=1e-13)
+            oracle.hist(roots, UNEVEN_WINDOW, W_PIX, H_PIX)
+        elapsed += time.perf_counter() - t0
+        done += chunk
+        k += 1
+    return done / elapsed, threads, done
+
+
+def run_uneven(args, rank: int, world: int, local_rank: int):
+    import torch
+
+    from paper_2507_02164_gb300 import api, build, dist as D, workloads as WL
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n = 1 << args.log2n
+    start, _ = D.shard_range(n, rank)
+    packed, deg, off = WL.uneven_gaussian_torch(UNEVEN_SEED, start, n, dev)
+    ws = api.new_uneven_workspace(n, packed.numel(), torch.complex64, dev)
+    win = api.Window(*UNEVEN_WINDOW)
+    hist = api.new_hist(W_PIX, H_PIX, dev)
+    stats = api.new_stats(dev)
+    p = api.params("mixed")
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    def step_body():
+        api.hist_clear(hist)
+        api.hist_clear(stats)
+        api.roots_uneven(packed, deg, off, ws, mode="mixed", params_=p, window=win, hist=hist, stats=stats,
+                         want_roots=False, want_status=False)
+
+    step_body()  # eager once (loads the library, sizes the grids)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            step_body()
+    torch.cuda.current_stream().wait_stream(side)
+    launches_per_step = 2 + 16  # two clears; clear, count, scan, pack + 12 per-degree solvers
+    for _ in range(args.warmup):
+        graph.replay()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        t0.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        t1.record(stream)
+        torch.cuda.synchronize()
+    ms = D.max_over_ranks(t0.elapsed_time(t1), device=dev)
+    st = api.stats_dict(stats)
+    value = n * world * args.steps / (ms * 1e-3)
+    if world > 1:
+        D.reduce_images(hist, dst=0)
+
+    # end to end: inputs from pinned host memory, copied in every step
+    e2e = None
+    if not args.no_e2e:
+        hp, hd, ho = (packed.cpu().pin_memory(), deg.cpu().pin_memory(), off.cpu().pin_memory())
+        hist_h = torch.empty_like(hist, device="cpu").pin_memory()
+        stats_h = torch.empty_like(stats, device="cpu").pin_memory()
+
+        def e2e_step():
+            packed.copy_(hp, non_blocking=True)
+            deg.copy_(hd, non_blocking=True)
+            off.copy_(ho, non_blocking=True)
+            graph.replay()
+            hist_h.copy_(hist, non_blocking=True)
+            stats_h.copy_(stats, non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = D.max_over_ranks(e0.elapsed_time(e1), device=dev)
+        e2e = {"value": n * world * args.steps / (ems * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": hp.numel() * hp.element_size() + hd.numel() + ho.numel() * 8,
+               "d2h_bytes_per_step": hist_h.numel() * 4 + stats_h.numel() * 8, "ms_per_step": ems / args.steps}
+    if rank != 0:
+        return
+    mhz = clk.summary().get("sm_max_mhz") or 2070.0
+    p32 = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6
+    p64 = sms * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6
+    f32, f64 = algorithmic_flops(st)
+    t = ms * 1e-3 / args.steps
+    line = {
+        "metric": UNEVEN_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic: seeded complex-Gaussian polynomials of degree 2..12 (SplitMix64 seed 3), generated on device",
+        "config": {"workload": f"uneven-gaussian-2^{args.log2n}: degree uniform 2..12, complex64 packed + u8 degree + "
+                               f"i64 offsets, bin & pack + 12 persistent per-degree solvers, {W_PIX}x{H_PIX} histogram "
+                               f"over [-3,3]x[-1.6875,1.6875]", "polys_per_gpu": n,
+                   "coefficients": int(packed.numel()), "l2_flush": "inputs larger than L2 (0.94 GB per step)",
+                   "parallelism": f"dp{world}"},
+        "roofline": {"bound": "alu", "kernel": "whole step (pack + 12 uneven_solve_kernel launches)",
+                     "achieved": (f32 + f64 * p32 / p64) / t / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
+                     "frac": f32 / p32 / t + f64 / p64 / t, "traffic": None,
+                     "fp32_frac": f32 / p32 / t, "fp64_frac": f64 / p64 / t,
+                     "note": "FP32-equivalent over the whole graph replay"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+        "status": {k: st[k] for k in ("status_ok", "status_not_converged", "status_rejected", "status_degenerate")},
+        "sweeps_per_poly": st["sweeps"] / max(1, st["polys"]),
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if not args.no_cpu:
+        v, threads, done = cpu_oracle_rate_uneven(args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"first {done} polynomials of the same uneven stream, FP64 oracle solve + "
+                                          f"histogram per degree, ~{args.cpu_seconds:.0f} s"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.log2n is None:
+        args.log2n = 26 if args.workload == "littlewood" else 24
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -465,7 +611,10 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     try:
-        run_ours(args, rank, world, local_rank)
+        if args.workload == "uneven":
+            run_uneven(args, rank, world, local_rank)
+        else:
+            run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

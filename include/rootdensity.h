@@ -99,7 +99,16 @@ typedef struct {
     uint64_t binned;         /* roots counted in the histogram                           */
     uint64_t out_of_window;  /* roots outside the window (NaN included)                  */
     uint64_t clipped;        /* roots dropped by a tile clip                             */
+    uint64_t flops_fp32;     /* algorithmic FP32 flops of the solve (see below)          */
+    uint64_t flops_fp64;     /* algorithmic FP64 flops of the solve                      */
 } rd_stats;
+/* Algorithmic flop convention (the method's own work, not what the hardware
+ * executes): a sweep at active size m costs 20 (m(m+1) - 2) for its rotated
+ * entry pairs, 24 (m - 1) for its Givens pairs and 60 for shift, unshift,
+ * Wilkinson shift and deflation test, in the sweep precision. RD_MIXED adds
+ * per Newton step 8d + 2 FP64 (p(z)) and 8d + 3 FP32 (p'(z), step size), and
+ * per root 8d + 4 FP64 (final residual, binning) and 2d + 4 FP32 (denominator);
+ * RD_PLAIN_FP64 adds 4 FP64 per root (binning). */
 
 /* Optional per-polynomial tile clip of the full pipeline (Sec. II, domain
  * split into subregions D_i): roots are first mapped z = centre_i + radius *
@@ -155,6 +164,36 @@ int rd_density_accumulate(const double *roots, int64_t n_roots, rd_window window
 
 /* Zero `words` 32-bit words of device memory (histogram or rd_stats). */
 int rd_hist_clear(uint32_t *hist, int64_t words, void *stream);
+
+/* ---- uneven degrees (1..12) in one pass -------------------------------------
+ * Packed poly-major batch: polynomial i has degree degrees[i] and its
+ * coefficients a_0..a_d are coeffs[offsets[i] .. offsets[i+1]-1] (offsets has
+ * n+1 entries; n_coeffs = offsets[n] elements of `dtype`). Roots are packed
+ * the same way without the leading coefficient: root j of polynomial i is
+ * roots[offsets[i] - i + j] (rd_c128). The call bins the batch by degree
+ * into the workspace, then solves every degree bin with a persistent kernel
+ * that takes 32-polynomial tasks from the bin's atomic queue, binning roots
+ * into hist when it is given.
+ * A polynomial whose offsets do not hold degree+1 coefficients inside the
+ * array, or whose degree is outside 1..12, gets RD_STATUS_DEGENERATE (NaN
+ * roots when its offsets are consistent; nothing written otherwise).
+ *   ws        device scratch of at least rd_uneven_workspace_bytes(n, n_coeffs,
+ *             dtype) bytes, 256-byte aligned; overwritten; must not be shared
+ *             by two calls in flight at once
+ *   window    host pointer; NULL with hist NULL = no binning
+ *   tuning    host pointer or NULL (params.block / ctas_per_sm for all groups)
+ * n < 2^32. Only enqueues kernels on `stream` (16 launches), so the whole
+ * call can be captured in a CUDA graph. */
+typedef struct {
+    int32_t block[3];        /* threads per CTA for the degree-1..6, 7..9, 10..12 kernels (0 = default) */
+    int32_t ctas_per_sm[3];  /* resident CTAs per SM for each group (0 = occupancy maximum)     */
+} rd_uneven_tuning;
+
+size_t rd_uneven_workspace_bytes(int64_t n, int64_t n_coeffs, rd_dtype dtype);
+int rd_roots_uneven(const void *coeffs, rd_dtype dtype, const uint8_t *degrees, const int64_t *offsets,
+                    int64_t n, int64_t n_coeffs, rd_mode mode, const rd_params *params,
+                    const rd_uneven_tuning *tuning, const rd_window *window, int W, int H, uint32_t *hist,
+                    double *roots, uint8_t *status, rd_stats *stats, void *ws, size_t ws_bytes, void *stream);
 
 /* ---- implicit-differentiation adjoint ---------------------------------------
  * grad_coeffs[k*n+i] = sum_j conj(-z_ij^k / p_i'(z_ij)) * grad_roots[j*n+i],

@@ -36,8 +36,13 @@ class Clip(ctypes.Structure):
                 ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("tiles", Window)]
 
 
+class UnevenTuning(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32 * 3), ("ctas_per_sm", ctypes.c_int32 * 3)]
+
+
 STATS_FIELDS = ("polys", "status_ok", "status_not_converged", "status_rejected", "status_degenerate",
-                "sweeps", "pair_updates", "rotations", "newton_steps", "binned", "out_of_window", "clipped")
+                "sweeps", "pair_updates", "rotations", "newton_steps", "binned", "out_of_window", "clipped",
+                "flops_fp32", "flops_fp64")
 STATS_WORDS = len(STATS_FIELDS)  # uint64 words of rd_stats
 
 # entry point -> (restype, argtypes); every name here is declared in include/rootdensity.h
@@ -53,6 +58,9 @@ SIGNATURES = {
     "rd_density_accumulate": (I32, [P, I64, Window, I32, I32, P, P, P]),
     "rd_hist_clear": (I32, [P, I64, P]),
     "rd_roots_backward": (I32, [P, I32, I32, I64, P, P, P, P, P]),
+    "rd_uneven_workspace_bytes": (SZ, [I64, I64, I32]),
+    "rd_roots_uneven": (I32, [P, I32, P, P, I64, I64, I32, ctypes.POINTER(Params), ctypes.POINTER(UnevenTuning),
+                              ctypes.POINTER(Window), I32, I32, P, P, P, P, P, SZ, P]),
     "rd_l2_nodes": (I32, [I32, P, P]),
     "rd_l2_approx": (I32, [P, I64, I32, I32, I32, P, P]),
 }

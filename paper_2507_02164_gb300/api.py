@@ -145,6 +145,52 @@ def density_accumulate(roots: torch.Tensor, window: Window, hist: torch.Tensor, 
     return hist
 
 
+def uneven_workspace_bytes(n: int, n_coeffs: int, dtype=torch.complex64) -> int:
+    return int(N.load().rd_uneven_workspace_bytes(n, n_coeffs, DTYPES[dtype]))
+
+
+def new_uneven_workspace(n: int, n_coeffs: int, dtype=torch.complex64, device="cuda") -> torch.Tensor:
+    """A device scratch buffer for roots_uneven (torch allocations are 256-byte aligned)."""
+    return torch.empty(uneven_workspace_bytes(n, n_coeffs, dtype), dtype=torch.uint8, device=device)
+
+
+def uneven_tuning(block=(0, 0, 0), ctas_per_sm=(0, 0, 0)) -> N.UnevenTuning:
+    t = N.UnevenTuning()
+    for g in range(3):
+        t.block[g] = int(block[g])
+        t.ctas_per_sm[g] = int(ctas_per_sm[g])
+    return t
+
+
+def roots_uneven(coeffs: torch.Tensor, degrees: torch.Tensor, offsets: torch.Tensor, workspace: torch.Tensor,
+                 mode="mixed", params_=None, tuning=None, window: Window | None = None, hist=None, roots=None,
+                 status=None, stats=None, stream=None, want_roots=True, want_status=True):
+    """Roots of a packed uneven-degree batch (coefficients lowest power first,
+    polynomial i at coeffs[offsets[i]:offsets[i+1]]); roots packed without the
+    leading coefficient. Optionally bins them into hist over window."""
+    _check_cuda("coeffs", coeffs)
+    if coeffs.dtype not in DTYPES or coeffs.dim() != 1:
+        raise ValueError("coeffs must be a 1-D complex64/complex128 tensor")
+    _check_cuda("degrees", degrees, torch.uint8)
+    _check_cuda("offsets", offsets, torch.int64)
+    n = degrees.numel()
+    if offsets.numel() != n + 1:
+        raise ValueError("offsets must have n+1 entries")
+    ncoef = coeffs.numel()
+    if roots is None and want_roots:
+        roots = torch.empty(ncoef - n, dtype=torch.complex128, device=coeffs.device)
+    if status is None and want_status:
+        status = torch.empty(n, dtype=torch.uint8, device=coeffs.device)
+    p = params_ if params_ is not None else params(mode)
+    H, W = hist.shape if hist is not None else (0, 0)
+    win = ctypes.byref(window.c()) if window is not None else None
+    N.call("rd_roots_uneven", _ptr(coeffs), DTYPES[coeffs.dtype], _ptr(degrees), _ptr(offsets), n, ncoef,
+           _mode(mode), ctypes.byref(p), ctypes.byref(tuning) if tuning is not None else None, win, W, H,
+           _ptr(hist), _ptr(roots), _ptr(status), _ptr(stats), _ptr(workspace),
+           workspace.numel() * workspace.element_size(), _stream(stream))
+    return roots, status
+
+
 def roots_backward(coeffs: torch.Tensor, roots: torch.Tensor, grad_roots: torch.Tensor, status=None,
                    stream=None):
     """grad_coeffs [d+1, n] (dtype of coeffs) from grad_roots [d, n] (complex128)."""

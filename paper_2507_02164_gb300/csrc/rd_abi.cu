@@ -19,6 +19,9 @@ int launch_clear(uint32_t *p, int64_t words, cudaStream_t st);
 int launch_backward(int degree, rd_dtype dt, const void *coeffs, const double *roots, const double *grad_roots,
                     void *grad_coeffs, uint8_t *status, int64_t n, cudaStream_t st);
 int l2_nodes_host(int nr, double *r, double *w);
+size_t uneven_workspace_bytes(int64_t n, int64_t n_coeffs, rd_dtype dt);
+int launch_uneven(const SolveArgs &a, rd_dtype dt, const uint8_t *degrees, const int64_t *offsets, int64_t n,
+                  int64_t n_coeffs, bool mixed, void *ws, const int *block, const int *cps, cudaStream_t st);
 int launch_l2(const double *samples, int64_t n, int nr, int degree, double *coeffs, cudaStream_t st);
 }  // namespace rd
 
@@ -95,36 +98,28 @@ int check_params(const rd_params &p)
     return RD_OK;
 }
 
-int solve_common(const void *coeffs, rd_dtype dtype, int degree, int64_t n, rd_mode mode, const rd_params *params,
-                 const rd_clip *clip, const rd_window *window, int W, int H, uint32_t *hist, double *roots,
-                 uint8_t *status, rd_stats *stats, void *stream)
+// Validate the arguments shared by every solve entry point and fill the
+// kernel argument block (everything except the coefficient layout).
+int build_solve_args(rd_dtype dtype, int degree_for_tol, rd_mode mode, const rd_params *params, const rd_clip *clip,
+                     const rd_window *window, int W, int H, uint32_t *hist, double *roots, uint8_t *status,
+                     rd_stats *stats, rd::SolveArgs &a, rd_params &p)
 {
     if (dtype != RD_C64 && dtype != RD_C128) return rd_set_error(RD_EINVAL, "dtype must be RD_C64 or RD_C128");
     if (mode != RD_PLAIN_FP64 && mode != RD_MIXED) return rd_set_error(RD_EINVAL, "mode must be RD_PLAIN_FP64 or RD_MIXED");
-    if (degree < 1 || degree > 12) return rd_set_error(RD_EUNSUPPORTED, "degree %d outside 1..12", degree);
-    if (n < 0) return rd_set_error(RD_EINVAL, "n < 0");
-    if (n > ((int64_t)1 << 40)) return rd_set_error(RD_EINVAL, "n too large");
-    size_t el = dtype == RD_C64 ? 8 : 16;
-    if (n > 0 && (!coeffs || !aligned(coeffs, el))) return rd_set_error(RD_EINVAL, "coeffs null or misaligned");
     if (roots && !aligned(roots, 16)) return rd_set_error(RD_EINVAL, "roots misaligned (16 B)");
     if (stats && !aligned(stats, 8)) return rd_set_error(RD_EINVAL, "stats misaligned (8 B)");
-    rd_params p;
     if (params) p = *params;
     else rd_default_params(mode, &p);
     int rc = check_params(p);
     if (rc) return rc;
-
-    rd::SolveArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.coeffs = coeffs;
-    a.n = n;
     a.tol = p.tol;
     a.max_iters = p.max_iters;
     a.shift = p.shift;
     a.exc_period = p.exc_period;
     a.polish_steps = p.polish_steps;
     a.polish_extra = p.polish_extra;
-    a.residual_tol = p.residual_tol > 0 ? p.residual_tol : 64.0 * degree * std::ldexp(1.0, -53);
+    a.residual_tol = p.residual_tol > 0 ? p.residual_tol : 64.0 * degree_for_tol * std::ldexp(1.0, -53);
     a.collapse_tol = p.collapse_tol;
     a.roots = roots;
     a.status = status;
@@ -139,7 +134,6 @@ int solve_common(const void *coeffs, rd_dtype dtype, int degree, int64_t n, rd_m
             if (!clip->centres || !aligned(clip->centres, 16)) return rd_set_error(RD_EINVAL, "clip.centres null or misaligned");
             if (!(clip->radius > 0) || !std::isfinite(clip->radius)) return rd_set_error(RD_EINVAL, "clip.radius must be > 0");
             if (clip->nx < 1 || clip->ny < 1 || !window_ok(clip->tiles)) return rd_set_error(RD_EINVAL, "clip tile grid invalid");
-            if (!clip->tile_index && n > (int64_t)clip->nx * clip->ny) return rd_set_error(RD_EINVAL, "clip: n exceeds nx*ny without tile_index");
             a.clip_on = 1;
             a.centres = clip->centres;
             a.radius = clip->radius;
@@ -149,6 +143,26 @@ int solve_common(const void *coeffs, rd_dtype dtype, int degree, int64_t n, rd_m
     } else if (clip) {
         return rd_set_error(RD_EINVAL, "clip needs a histogram");
     }
+    return RD_OK;
+}
+
+int solve_common(const void *coeffs, rd_dtype dtype, int degree, int64_t n, rd_mode mode, const rd_params *params,
+                 const rd_clip *clip, const rd_window *window, int W, int H, uint32_t *hist, double *roots,
+                 uint8_t *status, rd_stats *stats, void *stream)
+{
+    if (degree < 1 || degree > 12) return rd_set_error(RD_EUNSUPPORTED, "degree %d outside 1..12", degree);
+    if (n < 0) return rd_set_error(RD_EINVAL, "n < 0");
+    if (n > ((int64_t)1 << 40)) return rd_set_error(RD_EINVAL, "n too large");
+    size_t el = dtype == RD_C64 ? 8 : 16;
+    if (n > 0 && (!coeffs || !aligned(coeffs, el))) return rd_set_error(RD_EINVAL, "coeffs null or misaligned");
+    rd::SolveArgs a;
+    rd_params p;
+    int rc = build_solve_args(dtype, degree, mode, params, clip, window, W, H, hist, roots, status, stats, a, p);
+    if (rc) return rc;
+    if (clip && !clip->tile_index && n > (int64_t)clip->nx * clip->ny)
+        return rd_set_error(RD_EINVAL, "clip: n exceeds nx*ny without tile_index");
+    a.coeffs = coeffs;
+    a.n = n;
     if (n == 0) return RD_OK;
     int block = p.block ? p.block : 128;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -225,6 +239,51 @@ int rd_hist_clear(uint32_t *hist, int64_t words, void *stream)
     if (words == 0) return RD_OK;
     if (!hist || !aligned(hist, 4)) return rd_set_error(RD_EINVAL, "hist null or misaligned");
     return rd::launch_clear(hist, words, reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t rd_uneven_workspace_bytes(int64_t n, int64_t n_coeffs, rd_dtype dtype)
+{
+    if (n < 0 || n_coeffs < 0 || (dtype != RD_C64 && dtype != RD_C128)) return 0;
+    return rd::uneven_workspace_bytes(n, n_coeffs, dtype);
+}
+
+int rd_roots_uneven(const void *coeffs, rd_dtype dtype, const uint8_t *degrees, const int64_t *offsets, int64_t n,
+                    int64_t n_coeffs, rd_mode mode, const rd_params *params, const rd_uneven_tuning *tuning,
+                    const rd_window *window, int W, int H, uint32_t *hist, double *roots, uint8_t *status,
+                    rd_stats *stats, void *ws, size_t ws_bytes, void *stream)
+{
+    if (n < 0 || n_coeffs < 0) return rd_set_error(RD_EINVAL, "n and n_coeffs must be >= 0");
+    if (n >= ((int64_t)1 << 32)) return rd_set_error(RD_EINVAL, "n must be below 2^32");
+    if ((hist == nullptr) != (window == nullptr)) return rd_set_error(RD_EINVAL, "hist and window go together");
+    rd::SolveArgs a;
+    rd_params p;
+    int rc = build_solve_args(dtype, 12, mode, params, nullptr, window, W, H, hist, roots, status, stats, a, p);
+    if (rc) return rc;
+    if (p.residual_tol <= 0) a.residual_tol = -1.0;  // per-degree default 64 d 2^-53, set in the kernel
+    if (n == 0) return RD_OK;
+    size_t el = dtype == RD_C64 ? 8 : 16;
+    if (!coeffs || !aligned(coeffs, el)) return rd_set_error(RD_EINVAL, "coeffs null or misaligned");
+    if (!degrees || !offsets || !aligned(offsets, 8)) return rd_set_error(RD_EINVAL, "degrees / offsets null or misaligned");
+    if (!ws || !aligned(ws, 256)) return rd_set_error(RD_EINVAL, "workspace null or not 256-byte aligned");
+    size_t need = rd::uneven_workspace_bytes(n, n_coeffs, dtype);
+    if (ws_bytes < need) return rd_set_error(RD_EINVAL, "workspace too small: %zu < %zu bytes", ws_bytes, need);
+    int block[3], cps[3];
+    for (int g = 0; g < 3; ++g) {
+        block[g] = p.block ? p.block : 128;
+        cps[g] = p.ctas_per_sm;
+        if (tuning) {
+            if (tuning->block[g] != 0 && (tuning->block[g] < 32 || tuning->block[g] > 256 || tuning->block[g] % 32))
+                return rd_set_error(RD_EINVAL, "tuning.block[%d] must be 0 or a multiple of 32 in [32, 256]", g);
+            if (tuning->ctas_per_sm[g] < 0 || tuning->ctas_per_sm[g] > 64)
+                return rd_set_error(RD_EINVAL, "tuning.ctas_per_sm[%d] must be in [0, 64]", g);
+            if (tuning->block[g]) block[g] = tuning->block[g];
+            if (tuning->ctas_per_sm[g]) cps[g] = tuning->ctas_per_sm[g];
+        }
+    }
+    a.coeffs = coeffs;
+    a.n = n;
+    return rd::launch_uneven(a, dtype, degrees, offsets, n, n_coeffs, mode == RD_MIXED, ws, block, cps,
+                             reinterpret_cast<cudaStream_t>(stream));
 }
 
 int rd_roots_backward(const void *coeffs, rd_dtype dtype, int degree, int64_t n, const double *roots,

@@ -175,20 +175,35 @@ __device__ __forceinline__ cx<T> wilkinson(cx<T> a, cx<T> b, cx<T> c, cx<T> d)
     return sub(d, cdiv(bc, den));
 }
 
-template <int N, typename T, typename In, bool MIXED>
-__global__ void __launch_bounds__(256, (MIXED && N <= 6) ? 2 : 1) solve_kernel(SolveArgs A)
+// Where the results of local polynomial i of a solved batch go.
+// Uniform batch: polynomial i itself, root j at j*n + i (coefficient-major).
+struct UniformMap {
+    int64_t n;
+    __device__ int64_t poly(int64_t i) const { return i; }
+    __device__ int64_t root(int64_t p, int j) const { return (int64_t)j * n + p; }
+};
+// Degree bin of a packed uneven batch: local slot i is polynomial perm[i];
+// its roots are packed like its coefficients without the leading one.
+struct PackedMap {
+    const uint32_t *perm;
+    const int64_t *offsets;
+    __device__ int64_t poly(int64_t i) const { return (int64_t)__ldg(perm + i); }
+    __device__ int64_t root(int64_t p, int j) const { return __ldg(offsets + p) - p + j; }
+};
+
+// One warp solves (and bins) the 32 polynomials base .. base+31 of a
+// coefficient-major batch `coeffs` of n polynomials of degree N. All 32
+// lanes must call it together.
+template <int N, typename T, typename In, bool MIXED, class Map>
+__device__ __forceinline__ void solve_warp(const SolveArgs &A, const void *coeffs, int64_t n, int64_t base,
+                                           const Map &map, const CtaStats &S)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t warp_id = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int64_t n = A.n;
     const T tol = (T)A.tol;
-    __shared__ unsigned long long acc[ST_WORDS];
-    const CtaStats S = stats_begin(acc, A.stats);
-
-    for (int64_t base = warp_id * 32; base < n; base += warps_total * 32) {
+    {
         const int64_t i = base + lane;
         const bool valid = i < n;
+        const int64_t pid = valid ? map.poly(i) : 0;  // the polynomial's index in the caller's batch
 
         // ---- load a_0..a_N (coefficient-major, coalesced) and normalise
         cx<T> b[N];
@@ -198,7 +213,7 @@ __global__ void __launch_bounds__(256, (MIXED && N <= 6) ? 2 : 1) solve_kernel(S
                 // complex64 storage: FP32 normalisation is exact enough for the sweeps
                 cx<float> a[N + 1];
 #pragma unroll
-                for (int k = 0; k <= N; ++k) a[k] = InLoad<In>::ldf(A.coeffs, (int64_t)k * n + i);
+                for (int k = 0; k <= N; ++k) a[k] = InLoad<In>::ldf(coeffs, (int64_t)k * n + i);
 #pragma unroll
                 for (int k = 0; k <= N; ++k) degenerate |= !finite_c(a[k]);
                 degenerate |= (a[N].re == 0.0f && a[N].im == 0.0f);
@@ -210,7 +225,7 @@ __global__ void __launch_bounds__(256, (MIXED && N <= 6) ? 2 : 1) solve_kernel(S
                 // the FP32 range is still a valid input), then round for FP32 sweeps
                 cx<double> a[N + 1];
 #pragma unroll
-                for (int k = 0; k <= N; ++k) a[k] = InLoad<In>::ld(A.coeffs, (int64_t)k * n + i);
+                for (int k = 0; k <= N; ++k) a[k] = InLoad<In>::ld(coeffs, (int64_t)k * n + i);
 #pragma unroll
                 for (int k = 0; k <= N; ++k) degenerate |= !finite_c(a[k]);
                 degenerate |= (a[N].re == 0.0 && a[N].im == 0.0);
@@ -273,6 +288,9 @@ __global__ void __launch_bounds__(256, (MIXED && N <= 6) ? 2 : 1) solve_kernel(S
         S.add(ST_SWEEPS, n_sweeps);
         S.add(ST_PAIRS, n_pairs);
         S.add(ST_ROTS, n_rots);
+        // algorithmic flops of the sweeps, in the sweep precision (rd_stats convention)
+        const unsigned sweep_flops = 20u * n_pairs + 24u * n_rots + 60u * n_sweeps;
+        S.add(MIXED ? ST_F32 : ST_F64, sweep_flops);
 
         // ---- roots: the diagonal; MIXED polishes them in FP64
         uint8_t st = degenerate ? RD_STATUS_DEGENERATE : (not_conv ? RD_STATUS_NOT_CONVERGED : RD_STATUS_OK);
@@ -297,10 +315,10 @@ __global__ void __launch_bounds__(256, (MIXED && N <= 6) ? 2 : 1) solve_kernel(S
 #pragma unroll
                     for (int k = 0; k <= N; ++k) {
                         if constexpr (std::is_same<In, float2>::value) {
-                            af[k] = InLoad<In>::ldf(A.coeffs, (int64_t)k * n + i);
+                            af[k] = InLoad<In>::ldf(coeffs, (int64_t)k * n + i);
                             ad[k] = f2d(af[k]);
                         } else {
-                            ad[k] = InLoad<In>::ld(A.coeffs, (int64_t)k * n + i);
+                            ad[k] = InLoad<In>::ld(coeffs, (int64_t)k * n + i);
                             af[k] = d2f(ad[k]);
                         }
                     }
@@ -313,7 +331,8 @@ __global__ void __launch_bounds__(256, (MIXED && N <= 6) ? 2 : 1) solve_kernel(S
                     ad[N] = {1.0, 0.0};
                     af[N] = {1.0f, 0.0f};
                 }
-                const float rtol = (float)A.residual_tol;
+                // residual_tol <= 0: the default 64 d 2^-53 for this degree
+                const float rtol = A.residual_tol > 0 ? (float)A.residual_tol : (float)(64.0 * N * 0x1p-53);
                 // residual test |p(z)| <= residual_tol * sum_k |a_k|_1 |z|^k (1-norms
                 // |re| + |im| of the coefficients, at most sqrt(2) above the moduli)
                 auto passes = [&](cx<double> p, cx<double> zj) {
@@ -415,24 +434,28 @@ __global__ void __launch_bounds__(256, (MIXED && N <= 6) ? 2 : 1) solve_kernel(S
                 if (reject && st == RD_STATUS_OK && !degenerate) st = RD_STATUS_REJECTED;
             }
             S.add(ST_NEWTON, degenerate ? 0u : newton);
+            const unsigned nw = degenerate ? 0u : newton, nr = degenerate ? 0u : (unsigned)N;
+            S.add(ST_F64, (8u * N + 2u) * nw + (8u * N + 4u) * nr);
+            S.add(ST_F32, (8u * N + 3u) * nw + (2u * N + 4u) * nr);
         }
         if (degenerate) {
 #pragma unroll
             for (int j = 0; j < N; ++j) z[j] = {__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll)};
         }
 
+        if constexpr (!MIXED) S.add(ST_F64, degenerate ? 0u : 4u * N);
         S.add(ST_POLYS, valid ? 1u : 0u);
 #pragma unroll
         for (int k = 0; k < 4; ++k) S.add(ST_STATUS0 + k, (valid && st == k) ? 1u : 0u);
-        if (valid && A.status) A.status[i] = st;
+        if (valid && A.status) A.status[pid] = st;
 
         // ---- store and bin the roots (runtime loop, rotating z)
         cx<double> cen = {0.0, 0.0};
-        int64_t my_tile = i;
+        int64_t my_tile = pid;
         if (A.hist && A.clip_on && valid) {
-            double2 c = __ldg(reinterpret_cast<const double2 *>(A.centres) + i);
+            double2 c = __ldg(reinterpret_cast<const double2 *>(A.centres) + pid);
             cen = {c.x, c.y};
-            if (A.tile_index) my_tile = __ldg(A.tile_index + i);
+            if (A.tile_index) my_tile = __ldg(A.tile_index + pid);
         }
         unsigned n_clipped = 0, n_binned = 0, n_oow = 0;
         double2 *R = reinterpret_cast<double2 *>(A.roots);
@@ -441,7 +464,7 @@ __global__ void __launch_bounds__(256, (MIXED && N <= 6) ? 2 : 1) solve_kernel(S
             cx<double> zj = z[0];
 #pragma unroll
             for (int k = 0; k + 1 < N; ++k) z[k] = z[k + 1];
-            if (R && valid) R[(int64_t)j * n + i] = make_double2(zj.re, zj.im);
+            if (R && valid) R[map.root(pid, j)] = make_double2(zj.re, zj.im);
             if (A.hist) {
                 double x = zj.re, y = zj.im;
                 bool keep = valid;
@@ -465,6 +488,19 @@ __global__ void __launch_bounds__(256, (MIXED && N <= 6) ? 2 : 1) solve_kernel(S
             S.add(ST_OOW, n_oow);
         }
     }
+}
+
+// Uniform batch: warps stride over A.n polynomials, 32 at a time.
+template <int N, typename T, typename In, bool MIXED>
+__global__ void __launch_bounds__(256, (MIXED && N <= 6) ? 2 : 1) solve_kernel(SolveArgs A)
+{
+    const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t warp_id = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    __shared__ unsigned long long acc[ST_WORDS];
+    const CtaStats S = stats_begin(acc, A.stats);
+    const UniformMap map{A.n};
+    for (int64_t base = warp_id * 32; base < A.n; base += warps_total * 32)
+        solve_warp<N, T, In, MIXED>(A, A.coeffs, A.n, base, map, S);
     stats_end(S, A.stats);
 }
 

@@ -1,0 +1,271 @@
+// rd_uneven.cu -- polynomials of uneven degree (1..12) in one pass: bin the
+// batch by degree, then solve every bin with persistent kernels that pull
+// 32-polynomial tasks from atomic queues.
+//
+// The paper solves one degree at a time (n <= 6, Sec. II-A, Table III). A
+// batch of mixed degrees would otherwise run every polynomial at the largest
+// degree's cost, or diverge inside warps; binning gives each warp one
+// compile-time degree, so the Hessenberg matrix stays in registers.
+//
+// Workspace (caller-allocated, contents overwritten, 256-byte aligned):
+//   [header 512 B][perm: uint32 per polynomial][bins: the coefficients again,
+//   coefficient-major within each degree bin]
+// Launch sequence on the caller's stream (graph-capturable, no allocation,
+// no synchronisation): clear header -> count -> scan -> pack -> one
+// persistent solve kernel per degree, largest degree first, each with its
+// own register allocation and its own task queue.
+#include "rd_solve.cuh"
+
+namespace rd {
+
+int launch_clear(uint32_t *p, int64_t words, cudaStream_t st);
+
+constexpr int UNEVEN_MAX_DEG = 12;
+
+struct UnevenHeader {
+    uint32_t count[16];      // polynomials per degree
+    uint32_t cursor[16];     // pack cursors per degree
+    uint32_t poly_base[16];  // first slot of each degree's bin in perm
+    uint32_t head[16];       // task queue head of each degree's solve kernel
+    uint32_t bad;            // polynomials whose offsets disagree with their degree
+    uint32_t pad[3];
+    int64_t coef_base[16];   // first element of each degree's bin in the bins region
+};
+static_assert(sizeof(UnevenHeader) <= 512, "header must fit its 512-byte slot");
+
+constexpr size_t UNEVEN_HEADER_BYTES = 512;
+
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct UnevenLayout {
+    UnevenHeader *hdr;
+    uint32_t *perm;
+    char *bins;
+};
+
+inline size_t uneven_bytes(int64_t n, int64_t n_coeffs, size_t elem)
+{
+    return UNEVEN_HEADER_BYTES + align256((size_t)n * 4) + align256((size_t)n_coeffs * elem);
+}
+
+inline UnevenLayout uneven_layout(void *ws, int64_t n)
+{
+    char *p = reinterpret_cast<char *>(ws);
+    UnevenLayout L;
+    L.hdr = reinterpret_cast<UnevenHeader *>(p);
+    L.perm = reinterpret_cast<uint32_t *>(p + UNEVEN_HEADER_BYTES);
+    L.bins = p + UNEVEN_HEADER_BYTES + align256((size_t)n * 4);
+    return L;
+}
+
+struct UnevenArgs {
+    const uint8_t *degrees;
+    const int64_t *offsets;
+    int64_t n;
+    int64_t n_coeffs;
+};
+
+// A polynomial is solvable when its offsets hold exactly degree + 1
+// coefficients inside the array and its degree is 1..12.
+__device__ __forceinline__ int checked_degree(const UnevenArgs &U, int64_t i, bool &consistent)
+{
+    int d = __ldg(U.degrees + i);
+    int64_t o0 = __ldg(U.offsets + i), o1 = __ldg(U.offsets + i + 1);
+    consistent = (o0 >= 0) && (o1 <= U.n_coeffs) && (o1 - o0 == (int64_t)d + 1);
+    return (consistent && d >= 1 && d <= UNEVEN_MAX_DEG) ? d : -1;
+}
+
+// Count polynomials per degree; mark the unsolvable ones DEGENERATE (NaN
+// roots where the offsets are consistent, nothing written where they are not).
+__global__ void __launch_bounds__(256) uneven_count_kernel(UnevenArgs U, UnevenHeader *hdr, double *roots,
+                                                           uint8_t *status, rd_stats *stats)
+{
+    __shared__ unsigned cnt[16];
+    __shared__ unsigned long long acc[ST_WORDS];
+    if (threadIdx.x < 16) cnt[threadIdx.x] = 0;
+    const CtaStats S = stats_begin(acc, stats);  // synchronises the CTA
+    __syncthreads();
+    const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t warp_id = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    unsigned bad = 0, invalid = 0;
+    for (int64_t base = warp_id * 32; base < U.n; base += warps_total * 32) {
+        int64_t i = base + lane;
+        if (i < U.n) {
+            bool consistent;
+            int d = checked_degree(U, i, consistent);
+            if (d > 0) {
+                atomicAdd(&cnt[d], 1u);
+            } else {
+                invalid += 1;
+                bad += consistent ? 0u : 1u;
+                if (status) status[i] = RD_STATUS_DEGENERATE;
+                if (roots && consistent) {
+                    int dd = __ldg(U.degrees + i);
+                    int64_t r0 = __ldg(U.offsets + i) - i;
+                    for (int j = 0; j < dd; ++j)
+                        reinterpret_cast<double2 *>(roots)[r0 + j] =
+                            make_double2(__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
+                }
+            }
+        }
+    }
+    S.add(ST_POLYS, invalid);
+    S.add(ST_STATUS0 + RD_STATUS_DEGENERATE, invalid);
+    unsigned wb = __reduce_add_sync(0xffffffffu, bad);
+    if (lane == 0 && wb) atomicAdd(&hdr->bad, wb);
+    __syncthreads();
+    if (threadIdx.x < 16 && cnt[threadIdx.x]) atomicAdd(&hdr->count[threadIdx.x], cnt[threadIdx.x]);
+    stats_end(S, stats);
+}
+
+// Bin bases: poly_base[d] = sum of count[d'] for d' < d, coef_base[d] = sum
+// of count[d'] (d' + 1). One warp.
+__global__ void uneven_scan_kernel(UnevenHeader *hdr)
+{
+    const int lane = threadIdx.x;
+    unsigned c = lane < 16 ? hdr->count[lane] : 0u;
+    int64_t e = lane < 16 ? (int64_t)c * (lane + 1) : 0;
+    unsigned pc = c;
+    int64_t pe = e;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        unsigned oc = __shfl_up_sync(0xffffffffu, pc, off);
+        int64_t oe = __shfl_up_sync(0xffffffffu, pe, off);
+        if (lane >= off) {
+            pc += oc;
+            pe += oe;
+        }
+    }
+    if (lane < 16) {
+        hdr->poly_base[lane] = pc - c;  // exclusive
+        hdr->coef_base[lane] = pe - e;
+        hdr->cursor[lane] = 0;
+    }
+    if (lane < 16) hdr->head[lane] = 0;
+}
+
+// Scatter every solvable polynomial into its degree's bin: a slot from a
+// warp-aggregated cursor, perm[slot] = its index, its coefficients
+// coefficient-major at bins[coef_base[d] + k * count[d] + slot].
+template <typename E>
+__global__ void __launch_bounds__(256) uneven_pack_kernel(UnevenArgs U, const E *__restrict__ coeffs,
+                                                          UnevenHeader *hdr, uint32_t *perm, E *bins)
+{
+    const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t warp_id = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = warp_id * 32; base < U.n; base += warps_total * 32) {
+        int64_t i = base + lane;
+        int d = -1;
+        if (i < U.n) {
+            bool consistent;
+            d = checked_degree(U, i, consistent);
+        }
+        unsigned act = __ballot_sync(0xffffffffu, d > 0);
+        if (d > 0) {
+            unsigned peers = __match_any_sync(act, d);
+            int leader = __ffs(peers) - 1;
+            unsigned rank = __popc(peers & ((1u << lane) - 1u));
+            unsigned b = 0;
+            if (lane == leader) b = atomicAdd(&hdr->cursor[d], (unsigned)__popc(peers));
+            b = __shfl_sync(peers, b, leader);
+            unsigned slot = b + rank;
+            unsigned cnt = hdr->count[d];
+            perm[hdr->poly_base[d] + slot] = (uint32_t)i;
+            const E *src = coeffs + __ldg(U.offsets + i);
+            E *dst = bins + hdr->coef_base[d] + slot;
+            for (int k = 0; k <= d; ++k) dst[(int64_t)k * cnt] = __ldg(src + k);
+        }
+    }
+}
+
+// Persistent solver for the degree-N bin: each warp takes the next task of
+// the bin's queue (task = 32 consecutive slots) until the queue is empty.
+// One kernel per degree keeps each degree's own register allocation.
+template <int N, typename In, bool MIXED>
+__global__ void __launch_bounds__(256, (MIXED && N <= 6) ? 2 : 1)
+    uneven_solve_kernel(SolveArgs A, UnevenHeader *hdr, const uint32_t *perm, const char *bins, const int64_t *offsets)
+{
+    using T = typename std::conditional<MIXED, float, double>::type;
+    __shared__ unsigned long long acc[ST_WORDS];
+    const CtaStats S = stats_begin(acc, A.stats);
+    const int lane = threadIdx.x & 31;
+    const int64_t cnt = hdr->count[N];
+    const unsigned tasks = (unsigned)((cnt + 31) / 32);
+    const PackedMap map{perm + hdr->poly_base[N], offsets};
+    const void *base = bins + (size_t)hdr->coef_base[N] * sizeof(In);
+    for (;;) {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(&hdr->head[N], 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= tasks) break;
+        solve_warp<N, T, In, MIXED>(A, base, cnt, (int64_t)t * 32, map, S);
+    }
+    stats_end(S, A.stats);
+}
+
+template <int N, typename In, bool MIXED>
+static int launch_degree_bin(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, int block,
+                             int ctas_per_sm, cudaStream_t st)
+{
+    auto kern = uneven_solve_kernel<N, In, MIXED>;
+    int per_sm = ctas_per_sm;
+    if (per_sm <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+    }
+    int grid = per_sm * rd_sm_count_cached();
+    kern<<<grid, block, 0, st>>>(a, L.hdr, L.perm, L.bins, offsets);
+    return rd_check_launch("uneven_solve_kernel");
+}
+
+// Degree bins largest first: the most expensive work starts first.
+template <typename In, bool MIXED>
+static int launch_bins(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, const int *block,
+                       const int *cps, cudaStream_t st)
+{
+    int rc = 0;
+#define RD_BIN(D, G) \
+    if (!rc) rc = launch_degree_bin<D, In, MIXED>(a, L, offsets, block[G], cps[G], st);
+    RD_BIN(12, 2) RD_BIN(11, 2) RD_BIN(10, 2) RD_BIN(9, 1) RD_BIN(8, 1) RD_BIN(7, 1)
+    RD_BIN(6, 0) RD_BIN(5, 0) RD_BIN(4, 0) RD_BIN(3, 0) RD_BIN(2, 0) RD_BIN(1, 0)
+#undef RD_BIN
+    return rc;
+}
+
+size_t uneven_workspace_bytes(int64_t n, int64_t n_coeffs, rd_dtype dt)
+{
+    return uneven_bytes(n, n_coeffs, dt == RD_C64 ? 8 : 16);
+}
+
+int launch_uneven(const SolveArgs &a, rd_dtype dt, const uint8_t *degrees, const int64_t *offsets, int64_t n,
+                  int64_t n_coeffs, bool mixed, void *ws, const int *block, const int *cps, cudaStream_t st)
+{
+    UnevenLayout L = uneven_layout(ws, n);
+    UnevenArgs U{degrees, offsets, n, n_coeffs};
+    int rc = launch_clear(reinterpret_cast<uint32_t *>(L.hdr), UNEVEN_HEADER_BYTES / 4, st);
+    if (rc) return rc;
+    const int tb = 256;
+    int64_t ctas = (n + tb - 1) / tb;
+    int64_t cap = (int64_t)rd_sm_count_cached() * 8;
+    if (ctas > cap) ctas = cap;
+    if (ctas < 1) ctas = 1;
+    uneven_count_kernel<<<(unsigned)ctas, tb, 0, st>>>(U, L.hdr, a.roots, a.status, a.stats);
+    if ((rc = rd_check_launch("uneven_count_kernel"))) return rc;
+    uneven_scan_kernel<<<1, 32, 0, st>>>(L.hdr);
+    if ((rc = rd_check_launch("uneven_scan_kernel"))) return rc;
+    if (dt == RD_C64)
+        uneven_pack_kernel<float2><<<(unsigned)ctas, tb, 0, st>>>(U, reinterpret_cast<const float2 *>(a.coeffs), L.hdr,
+                                                                  L.perm, reinterpret_cast<float2 *>(L.bins));
+    else
+        uneven_pack_kernel<double2><<<(unsigned)ctas, tb, 0, st>>>(U, reinterpret_cast<const double2 *>(a.coeffs),
+                                                                   L.hdr, L.perm, reinterpret_cast<double2 *>(L.bins));
+    if ((rc = rd_check_launch("uneven_pack_kernel"))) return rc;
+    if (dt == RD_C64) return mixed ? launch_bins<float2, true>(a, L, offsets, block, cps, st)
+                                   : launch_bins<float2, false>(a, L, offsets, block, cps, st);
+    return mixed ? launch_bins<double2, true>(a, L, offsets, block, cps, st)
+                 : launch_bins<double2, false>(a, L, offsets, block, cps, st);
+}
+
+}  // namespace rd

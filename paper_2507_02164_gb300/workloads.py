@@ -258,3 +258,38 @@ def littlewood_soa_torch(seed: int, start: int, n: int, device, degree: int = 6)
         sel = torch.bitwise_and(_srl(x, 2 * k) if k else x, 3)
         out[k] = table[sel]
     return out
+
+
+def uniform_torch(seed: int, counters):
+    """uniform(seed, counters) as float64 torch values (same values as the numpy version)."""
+    import torch
+    x = draw_torch(seed, counters)
+    return torch.bitwise_and(torch.bitwise_right_shift(x, 11), (1 << 53) - 1).to(torch.float64) * _TWO_M53
+
+
+def uneven_gaussian_torch(seed: int, start: int, n: int, device, dtype=None):
+    """``uneven_gaussian`` for indices start .. start+n-1, generated on `device`.
+
+    Degrees and offsets equal the numpy version exactly; the Gaussian values
+    come from the device's log1p / cos / sin and can differ from numpy's in
+    the last bits, so parity checks take the stored device values as input.
+    Returns (coeffs_packed [sum(d+1)], degrees [n] u8, offsets [n+1] i64).
+    """
+    import torch
+    dtype = dtype or torch.complex64
+    idx = torch.arange(start, start + n, dtype=torch.int64, device=device)
+    u = uniform_torch(seed, idx * STRIDE_UNEVEN)
+    deg = (UNEVEN_MIN_DEG + torch.floor(11.0 * u)).to(torch.int64)
+    offsets = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    torch.cumsum(deg + 1, dim=0, out=offsets[1:])
+    total = int(offsets[-1].item())
+    packed = torch.empty(total, dtype=torch.complex128, device=device)
+    for k in range(UNEVEN_MAX_DEG + 1):
+        have = deg >= k
+        sel = idx[have]
+        u1 = uniform_torch(seed, sel * STRIDE_UNEVEN + (1 + 2 * k))
+        u2 = uniform_torch(seed, sel * STRIDE_UNEVEN + (2 + 2 * k))
+        rad = torch.sqrt(-2.0 * torch.log1p(-u1))
+        th = 2.0 * math.pi * u2
+        packed[offsets[:-1][have] + k] = torch.complex(rad * torch.cos(th), rad * torch.sin(th))
+    return packed.to(dtype), deg.to(torch.uint8), offsets

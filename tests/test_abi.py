@@ -40,7 +40,7 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(N.Params) == 56
     assert ctypes.sizeof(N.Window) == 32
     assert ctypes.sizeof(N.Clip) == 64
-    assert N.STATS_WORDS == 12
+    assert N.STATS_WORDS == 14
 
 
 def test_default_params():

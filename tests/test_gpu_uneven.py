@@ -1,0 +1,166 @@
+"""GPU parity of the uneven-degree path (degree bin & pack + persistent
+per-degree solvers) against the FP64 CPU oracle, and its CUDA-graph capture."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2507_02164_gb300 import api, workloads as WL
+from tests.gpu_common import compare_roots, hist_np, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+WIN3 = api.Window(-3.0, 3.0, -1.6875, 1.6875)
+W, H = 1920, 1080
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return require_gpu()
+
+
+def _split(packed, deg, off):
+    """Per-degree lists of (poly indices, coefficient rows) of a packed batch."""
+    out = {}
+    for d in np.unique(deg):
+        idx = np.nonzero(deg == d)[0]
+        rows = np.stack([packed[off[i]:off[i + 1]] for i in idx])
+        out[int(d)] = (idx, rows)
+    return out
+
+
+def _check_against_oracle(orc, packed, deg, off, roots, status, tol, kcap, max_rejected=2e-3):
+    """Compare each degree bin's GPU roots with the oracle; return the OK mask."""
+    ok = status == 0
+    assert np.all((status == 0) | (status == 2)), np.bincount(status, minlength=4)
+    assert (status == 2).mean() <= max_rejected
+    for d, (idx, rows) in _split(packed, deg, off).items():
+        r_gpu = np.stack([roots[off[i] - i: off[i] - i + d] for i in idx])
+        ref, ref_st, _, _ = orc.solve(rows)
+        good = ok[idx] & (ref_st == 0)
+        assert good.mean() > 0.99, (d, good.mean())
+        compare_roots(r_gpu[good], ref[good], rows[good], orc, tol, kcap)
+    return ok
+
+
+@pytest.mark.parametrize("mode,dtype", [("mixed", torch.complex64), ("plain", torch.complex128)])
+def test_uneven_batch_matches_oracle(dev, orc, mode, dtype):
+    n = 20000 + 13
+    packed, deg, off = WL.uneven_gaussian(3, n, dtype=np.complex64 if dtype == torch.complex64 else np.complex128)
+    c_t = torch.from_numpy(packed).to(dev)
+    d_t = torch.from_numpy(deg).to(dev)
+    o_t = torch.from_numpy(off).to(dev)
+    ws = api.new_uneven_workspace(n, packed.size, dtype, dev)
+    hist = api.new_hist(W, H, dev)
+    stats = api.new_stats(dev)
+    roots, status = api.roots_uneven(c_t, d_t, o_t, ws, mode=mode, window=WIN3, hist=hist, stats=stats)
+    torch.cuda.synchronize()
+    r = roots.cpu().numpy()
+    s = status.cpu().numpy()
+    tol, kcap = (1e-9, 1e3) if mode == "mixed" else (1e-11, 100.0)
+    _check_against_oracle(orc, packed.astype(np.complex128), deg, off, r, s, tol, kcap)
+    h_ref, oow = orc.hist(r, WIN3.tuple(), W, H)
+    assert np.array_equal(hist_np(hist), h_ref)
+    st = api.stats_dict(stats)
+    assert st["polys"] == n and st["binned"] == int(h_ref.sum()) and st["out_of_window"] == oow
+    assert st["status_ok"] == int((s == 0).sum())
+
+
+def test_invalid_degrees_and_offsets(dev, orc):
+    packed, deg, off = WL.uneven_gaussian(3, 200)
+    deg = deg.copy()
+    off = off.copy()
+    # polynomial 5: degree 0 with one coefficient (consistent offsets, unsolvable)
+    # polynomial 9: degree field disagrees with its offsets (inconsistent)
+    # rebuild the packed arrays with polynomial 5 reduced to one coefficient
+    rows = [packed[off[i]:off[i + 1]] for i in range(200)]
+    rows[5] = rows[5][:1]
+    deg[5] = 0
+    off = np.zeros(201, np.int64)
+    off[1:] = np.cumsum([len(r) for r in rows])
+    packed = np.concatenate(rows).astype(np.complex64)
+    deg[9] = deg[9] + 1
+    ws = api.new_uneven_workspace(200, packed.size, torch.complex64, dev)
+    roots = torch.full((packed.size - 200,), 7.0 + 7.0j, dtype=torch.complex128, device=dev)
+    roots_out, status = api.roots_uneven(torch.from_numpy(packed).to(dev), torch.from_numpy(deg).to(dev),
+                                         torch.from_numpy(off).to(dev), ws, mode="mixed", roots=roots)
+    torch.cuda.synchronize()
+    s = status.cpu().numpy()
+    r = roots_out.cpu().numpy()
+    assert s[5] == 3 and s[9] == 3
+    others = np.setdiff1d(np.arange(200), [5, 9])
+    assert np.all(s[others] != 3)
+    # polynomial 9's root slots are left untouched (its offsets are not trusted)
+    d9 = int(deg[9]) - 1
+    assert np.all(r[off[9] - 9: off[9] - 9 + d9] == 7.0 + 7.0j)
+
+
+def test_workspace_too_small_is_rejected(dev):
+    packed, deg, off = WL.uneven_gaussian(3, 100)
+    ws = torch.empty(1024, dtype=torch.uint8, device=dev)
+    with pytest.raises(api.N.RootDensityError):
+        api.roots_uneven(torch.from_numpy(packed).to(dev), torch.from_numpy(deg).to(dev),
+                         torch.from_numpy(off).to(dev), ws)
+
+
+def test_uneven_call_captures_into_a_cuda_graph(dev):
+    n = 50000
+    packed, deg, off = WL.uneven_gaussian_torch(3, 0, n, dev)
+    ws = api.new_uneven_workspace(n, packed.numel(), torch.complex64, dev)
+    hist = api.new_hist(W, H, dev)
+    roots = torch.empty(packed.numel() - n, dtype=torch.complex128, device=dev)
+    status = torch.empty(n, dtype=torch.uint8, device=dev)
+    api.roots_uneven(packed, deg, off, ws, window=WIN3, hist=hist, roots=roots, status=status)
+    torch.cuda.synchronize()
+    eager_hist = hist.clone()
+    eager_roots = roots.clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            api.hist_clear(hist)
+            api.roots_uneven(packed, deg, off, ws, window=WIN3, hist=hist, roots=roots, status=status)
+    torch.cuda.current_stream().wait_stream(s)
+    roots.zero_()
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(hist, eager_hist)
+    assert torch.equal(roots, eager_roots)
+
+
+def test_full_size_batch_sampled(dev, orc):
+    """The 2^24-polynomial uneven batch in the benchmark's configuration:
+    every counter adds up, and a sample of 4096 polynomials spread over the
+    batch (their stored coefficients read back from the device) matches the
+    oracle."""
+    n = 1 << 24
+    packed, deg, off = WL.uneven_gaussian_torch(3, 0, n, dev)
+    ws = api.new_uneven_workspace(n, packed.numel(), torch.complex64, dev)
+    hist = api.new_hist(W, H, dev)
+    stats = api.new_stats(dev)
+    roots, status = api.roots_uneven(packed, deg, off, ws, window=WIN3, hist=hist, stats=stats)
+    torch.cuda.synchronize()
+    st = api.stats_dict(stats)
+    total_roots = packed.numel() - n
+    assert st["polys"] == n
+    assert st["binned"] + st["out_of_window"] == total_roots
+    assert int(hist_np(hist).sum(dtype=np.int64)) == st["binned"]
+    s = status.cpu().numpy()
+    assert (s == 0).mean() > 0.999 and np.all((s == 0) | (s == 2))
+    sample = np.linspace(0, n - 1, 4096).astype(np.int64)
+    off_h = off.cpu().numpy()
+    deg_h = deg.cpu().numpy()
+    pk = packed.cpu().numpy().astype(np.complex128)
+    r = roots.cpu().numpy()
+    for d in range(2, 13):
+        idx = sample[deg_h[sample] == d]
+        if idx.size == 0:
+            continue
+        rows = np.stack([pk[off_h[i]:off_h[i + 1]] for i in idx])
+        r_gpu = np.stack([r[off_h[i] - i: off_h[i] - i + d] for i in idx])
+        ref, ref_st, _, _ = orc.solve(rows)
+        good = (s[idx] == 0) & (ref_st == 0)
+        compare_roots(r_gpu[good], ref[good], rows[good], orc, 1e-9, 1e3)

@@ -60,3 +60,11 @@ def test_tiles_grid():
     assert c.size == 480 * 270 and abs(w - 1 / 60) < 1e-15 and abs(h - 1 / 60) < 1e-15
     assert abs(rho - 0.5 * np.hypot(1 / 60, 1 / 60)) < 1e-15
     assert abs(c[0] - (-4 + 0.5 / 60 + 1j * (2.25 - 0.5 / 60))) < 1e-12
+
+
+def test_torch_uneven_batch_matches_numpy():
+    import torch
+    packed_t, deg_t, off_t = W.uneven_gaussian_torch(3, 100, 2000, "cpu", dtype=torch.complex128)
+    packed, deg, off = W.uneven_gaussian(3, np.arange(100, 2100, dtype=np.uint64), dtype=np.complex128)
+    assert np.array_equal(deg_t.numpy(), deg) and np.array_equal(off_t.numpy(), off)
+    assert np.allclose(packed_t.numpy(), packed, rtol=1e-14, atol=1e-14)
