@@ -195,6 +195,32 @@ int rd_roots_uneven(const void *coeffs, rd_dtype dtype, const uint8_t *degrees, 
                     const rd_uneven_tuning *tuning, const rd_window *window, int W, int H, uint32_t *hist,
                     double *roots, uint8_t *status, rd_stats *stats, void *ws, size_t ws_bytes, void *stream);
 
+/* ---- uneven degrees without a caller-provided workspace ----------------------
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory where they need roots: code running under
+ * an allocator owned by a host framework, loops where cudaMalloc/cudaFree
+ * would synchronise the device, deployments with a device-memory budget
+ * fixed in advance. It behaves like rd_roots_uneven (same arguments without
+ * ws/ws_bytes, same results) but uses a scratch array of
+ * RD_STATIC_SCRATCH_BYTES bytes built into the library: that memory is held
+ * on every GPU that loads the library until the process exits, and the call
+ * itself allocates and frees nothing.
+ *   - A batch whose rd_uneven_workspace_bytes(n, n_coeffs, dtype) exceeds
+ *     RD_STATIC_SCRATCH_BYTES is rejected with RD_EINVAL and a message; split
+ *     it, or use rd_roots_uneven.
+ *   - The first call on each device looks up the scratch array's device
+ *     address (cudaGetSymbolAddress) with that device current; make that
+ *     first call before any stream capture begins.
+ *   - All calls on a device share the one array and each leaves its contents
+ *     behind (the next call clears what must start at zero). Two calls whose
+ *     work overlaps on the GPU (different streams, or different host threads)
+ *     race on it and give wrong results: serialise them. */
+#define RD_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int rd_roots_uneven_static(const void *coeffs, rd_dtype dtype, const uint8_t *degrees, const int64_t *offsets,
+                           int64_t n, int64_t n_coeffs, rd_mode mode, const rd_params *params,
+                           const rd_uneven_tuning *tuning, const rd_window *window, int W, int H,
+                           uint32_t *hist, double *roots, uint8_t *status, rd_stats *stats, void *stream);
+
 /* ---- implicit-differentiation adjoint ---------------------------------------
  * grad_coeffs[k*n+i] = sum_j conj(-z_ij^k / p_i'(z_ij)) * grad_roots[j*n+i],
  * k = 0..degree (p(z) = 0 defines z(a); dz/da_k = -z^k / p'(z)), the gradient

@@ -44,6 +44,7 @@ STATS_FIELDS = ("polys", "status_ok", "status_not_converged", "status_rejected",
                 "sweeps", "pair_updates", "rotations", "newton_steps", "binned", "out_of_window", "clipped",
                 "flops_fp32", "flops_fp64")
 STATS_WORDS = len(STATS_FIELDS)  # uint64 words of rd_stats
+STATIC_SCRATCH_BYTES = 32 * 1024 * 1024  # RD_STATIC_SCRATCH_BYTES
 
 # entry point -> (restype, argtypes); every name here is declared in include/rootdensity.h
 P, I32, I64, F64, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
@@ -61,6 +62,8 @@ SIGNATURES = {
     "rd_uneven_workspace_bytes": (SZ, [I64, I64, I32]),
     "rd_roots_uneven": (I32, [P, I32, P, P, I64, I64, I32, ctypes.POINTER(Params), ctypes.POINTER(UnevenTuning),
                               ctypes.POINTER(Window), I32, I32, P, P, P, P, P, SZ, P]),
+    "rd_roots_uneven_static": (I32, [P, I32, P, P, I64, I64, I32, ctypes.POINTER(Params),
+                                     ctypes.POINTER(UnevenTuning), ctypes.POINTER(Window), I32, I32, P, P, P, P, P]),
     "rd_l2_nodes": (I32, [I32, P, P]),
     "rd_l2_approx": (I32, [P, I64, I32, I32, I32, P, P]),
 }
