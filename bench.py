@@ -56,7 +56,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["littlewood", "uneven"], default="littlewood",
+    ap.add_argument("--workload", choices=["littlewood", "uneven", "paper", "pipeline", "adjoint"],
+                    default="littlewood",
                     help="littlewood: the 2^26 degree-6 batch of the metric; uneven: 2^24 polynomials of "
                          "degree 2..12 (complex Gaussian, seed 3) in one CUDA-graph replay per step")
     ap.add_argument("--log2n", type=int, default=None, help="polynomials per GPU = 2^log2n")
@@ -595,6 +596,203 @@ def run_uneven(args, rank: int, world: int, local_rank: int):
     print(json.dumps(line), flush=True)
 
 
+def _timed(step, args, dev, world, local_rank):
+    """W warm-up steps, then K timed steps between CUDA events on the current
+    stream (barrier + synchronize on both sides); returns (max-over-ranks ms,
+    clock summary)."""
+    import torch
+
+    from paper_2507_02164_gb300 import dist as D
+    for _ in range(args.warmup):
+        step()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        t0.record(stream)
+        for _ in range(args.steps):
+            step()
+        t1.record(stream)
+        torch.cuda.synchronize()
+    return D.max_over_ranks(t0.elapsed_time(t1), device=dev), clk.summary()
+
+
+PAPER_METRIC = "deg-6 complex polys rooted+binned/s with the paper's schedule (FP32, T=10 sweeps per root, Rayleigh shift)"
+
+
+def run_paper(args, rank, world, local_rank):
+    """The paper's own setting (Sec. IV: FP32, n = 6, T = 10, no convergence
+    test) on the 2^26 Littlewood batch, fused with the histogram."""
+    import torch
+
+    from paper_2507_02164_gb300 import api, build, dist as D, workloads as WL
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n = 1 << args.log2n
+    start, _ = D.shard_range(n, rank)
+    coeffs = WL.littlewood_soa_torch(SEED, start, n, dev)
+    win = api.Window(*WINDOW)
+    hist = api.new_hist(W_PIX, H_PIX, dev)
+    stats = api.new_stats(dev)
+    p = api.params("mixed", fixed_sweeps=10, shift="rayleigh", exc_period=0, polish_steps=0, polish_extra=0)
+
+    def step():
+        api.hist_clear(hist)
+        api.hist_clear(stats)
+        api.roots_density(coeffs, win, hist, mode="mixed", params_=p, stats=stats)
+
+    ms, clk = _timed(step, args, dev, world, local_rank)
+    if rank != 0:
+        return
+    st = api.stats_dict(stats)
+    value = n * world * args.steps / (ms * 1e-3)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_max_mhz") or 2070.0
+    p32 = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6
+    f32, f64 = algorithmic_flops(st)
+    t = ms * 1e-3 / args.steps
+    qr_per_s = value * st["sweeps"] / max(1, st["polys"])
+    print(json.dumps({
+        "metric": PAPER_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic: seeded Littlewood {1,-1,i,-i} degree-6 polynomials (SplitMix64 seed 2), generated on device",
+        "config": {"workload": f"littlewood-deg6-2^{args.log2n}, fixed schedule T=10 (Alg. 2), Rayleigh shift, FP32 "
+                               f"eigenvalues without polish, fused {W_PIX}x{H_PIX} histogram",
+                   "l2_flush": "inputs larger than L2", "parallelism": f"dp{world}"},
+        "roofline": {"bound": "alu", "kernel": "rd::solve_kernel<6, float, float2, MIXED> (fixed schedule)",
+                     "achieved": (f32 + f64 * 64) / t / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
+                     "frac": f32 / p32 / t + f64 * 64 / p32 / t, "traffic": None},
+        "gpu_launches": 3 * args.steps, "clocks": clk,
+        "equiv_qr_decompositions_per_s": qr_per_s,
+        "paper_context": {"fpga_qr_per_s": 16.5e6, "fpga_polys_per_s": 3.33e5, "rtx3060m_polys_per_s": 2.79e7,
+                          "note": "paper's inputs unspecified; other hardware"},
+    }), flush=True)
+
+
+PIPELINE_METRIC = "sub-disks/s through L2 approximation + mixed roots + tile clip + histogram, f = sin(z^3) + 0.5 z"
+
+
+def run_pipeline(args, rank, world, local_rank):
+    """The full pipeline: f(z) = sin(z^3) + 0.5 z on [-4,4]x[-2.25,2.25] in
+    480 x 270 tiles; samples at the 16 x 32 nodes of every sub-disk are made
+    on the device by torch outside the timed step; a step is L2
+    approximation + fused mixed roots, tile clip and histogram."""
+    import torch
+
+    from paper_2507_02164_gb300 import api, build, workloads as WL
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    win_t = (-4.0, 4.0, -2.25, 2.25)
+    centres, rho, _, _ = WL.tiles(*win_t, 480, 270)
+    c = torch.from_numpy(centres).to(dev)
+    w = api.l2_sample_points(16, 32, dev)
+    samples = WL.f_sin_cube(c[:, None] + rho * w[None, :]).contiguous()
+    n = c.numel()
+    coeffs = torch.empty((7, n), dtype=torch.complex128, device=dev)
+    hist = api.new_hist(W_PIX, H_PIX, dev)
+    stats = api.new_stats(dev)
+    win = api.Window(*win_t)
+    clip = api.make_clip(c, rho, 480, 270, win)
+    stream = torch.cuda.current_stream()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    split = []
+
+    def step():
+        api.hist_clear(hist)
+        api.hist_clear(stats)
+        e[0].record(stream)
+        api.l2_approx(samples, 16, 32, 6, coeffs=coeffs)
+        e[1].record(stream)
+        api.roots_density(coeffs, win, hist, mode="mixed", clip=clip, stats=stats)
+        e[2].record(stream)
+        split.append(e)
+
+    ms, clk = _timed(step, args, dev, world, local_rank)
+    l2_ms = e[0].elapsed_time(e[1])
+    solve_ms = e[1].elapsed_time(e[2])
+    if rank != 0:
+        return
+    st = api.stats_dict(stats)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_max_mhz") or 2070.0
+    p64 = sms * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6
+    # l2_approx algorithmic work per sub-disk: 512 samples x 16 B read, radial
+    # sums 7 x 512 x 4 real flop (2 FMA), angular sums 7 x 32 x 8 flop
+    l2_flops = n * (7 * 512 * 4 + 7 * 32 * 8)
+    print(json.dumps({
+        "metric": PIPELINE_METRIC, "value": n * world * args.steps / (ms * 1e-3), "unit": "sub-disks/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+        "data": "synthetic: f(z) = sin(z^3) + 0.5 z sampled on the device at the quadrature nodes of every sub-disk",
+        "config": {"workload": "480x270 tiles of 1/60 on [-4,4]x[-2.25,2.25], rho = tile half-diagonal, 16x32 polar "
+                               "nodes, degree 6, mixed roots, clip to own tile, 1920x1080 histogram",
+                   "sub_disks": n, "l2_flush": "inputs larger than L2 (1.06 GB of samples per step)",
+                   "parallelism": f"dp{world}"},
+        "l2_approx_ms": l2_ms, "roots_density_ms": solve_ms,
+        "l2_roofline": {"bound": "alu", "achieved": l2_flops / (l2_ms * 1e-3) / 1e12, "peak": p64 / 1e12,
+                        "unit": "TFLOP/s (FP64)", "frac": l2_flops / (l2_ms * 1e-3) / p64,
+                        "hbm_gbs": n * 512 * 16 / (l2_ms * 1e-3) / 1e9},
+        "kept_roots": st["binned"], "clipped": st["clipped"],
+        "status": {k: st[k] for k in ("status_ok", "status_not_converged", "status_rejected", "status_degenerate")},
+        "gpu_launches": 4 * args.steps, "clocks": clk,
+    }), flush=True)
+
+
+ADJOINT_METRIC = "deg-6 polys/s through forward roots + implicit-differentiation adjoint"
+
+
+def run_adjoint(args, rank, world, local_rank):
+    """2^20 complex-Gaussian degree-6 polynomials (seed 4): forward roots
+    (mixed) and the adjoint for L = sum |z|^2 (grad_z = 2 z), timed
+    separately, for complex128 and complex64 coefficients."""
+    import numpy as np
+    import torch
+
+    from paper_2507_02164_gb300 import api, build, workloads as WL
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n = 1 << 20
+    co = WL.gaussian(4, n, 6)
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name, dt in (("c128", torch.complex128), ("c64", torch.complex64)):
+        coeffs = torch.from_numpy(np.ascontiguousarray(co.T)).to(dev).to(dt)
+        roots = torch.empty((6, n), dtype=torch.complex128, device=dev)
+        status = torch.empty(n, dtype=torch.uint8, device=dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+        def step():
+            ev[0].record(stream)
+            api.roots_batched(coeffs, mode="mixed", roots=roots, status=status)
+            ev[1].record(stream)
+            api.roots_backward(coeffs, roots, 2.0 * roots)
+            ev[2].record(stream)
+
+        ms, clk = _timed(step, args, dev, world, local_rank)
+        out[name] = {"ms_per_step": ms / args.steps, "forward_ms": ev[0].elapsed_time(ev[1]),
+                     "backward_ms": ev[1].elapsed_time(ev[2]), "value": n * args.steps / (ms * 1e-3),
+                     "clocks": clk}
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": ADJOINT_METRIC, "value": out["c128"]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": out["c128"]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 (c128) / f32 (c64)",
+        "data": "synthetic: seeded complex-Gaussian degree-6 polynomials (SplitMix64 seed 4)",
+        "config": {"workload": "2^20 deg-6, forward mixed roots + adjoint of L = sum |z|^2",
+                   "l2_flush": "none (inputs 112 MB c128, 56 MB c64)", "parallelism": f"dp{world}"},
+        "c128": out["c128"], "c64": out["c64"], "gpu_launches": 2 * args.steps, "clocks": out["c128"]["clocks"],
+    }), flush=True)
+
+
 def main():
     args = parse_args()
     if args.log2n is None:
@@ -611,10 +809,9 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     try:
-        if args.workload == "uneven":
-            run_uneven(args, rank, world, local_rank)
-        else:
-            run_ours(args, rank, world, local_rank)
+        runner = {"uneven": run_uneven, "paper": run_paper, "pipeline": run_pipeline,
+                  "adjoint": run_adjoint}.get(args.workload, run_ours)
+        runner(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

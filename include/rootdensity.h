@@ -70,12 +70,14 @@ typedef struct {
     int32_t ctas_per_sm;   /* grid = ctas_per_sm x SM count; 0 = tuned default                   */
     int32_t polish_extra;  /* RD_MIXED: further Newton steps, p and p' both in FP64, for a root
                               that fails the residual check after polish_steps (0..16)          */
-    int32_t reserved;      /* must be 0                                                         */
+    int32_t fixed_sweeps;  /* 0: adaptive deflation (tol). T > 0: the paper's fixed schedule
+                              (Alg. 2): exactly T sweeps per eigenvalue, no deflation test       */
 } rd_params;
 
 /* Defaults: plain tol 1e-13, mixed tol 4 * 2^-24, max_iters 40, Wilkinson
  * shift, exc_period 10, 3 polish steps, 5 extra steps, residual 64 d 2^-53,
- * collapse 1e-9. */
+ * collapse 1e-9, adaptive deflation. RD_MIXED with polish_steps = 0 and
+ * polish_extra = 0 returns the FP32 eigenvalues without polish or check. */
 void rd_default_params(rd_mode mode, rd_params *out);
 
 /* Root-density window: pixel column ix = floor((x - xmin) * W / (xmax - xmin)),

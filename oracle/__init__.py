@@ -63,6 +63,7 @@ def lib() -> ctypes.CDLL:
                 "or_wilkinson_shift": (None, [P, i32, i32, P]),
                 "or_solve_one": (i32, [P, i32, f64, i32, i32, i32, P, P]),
                 "or_solve_batch": (i32, [P, i64, i32, f64, i32, i32, i32, P, P, P, i32]),
+                "or_solve_fixed": (i32, [P, i32, i32, i32, i32, P]),
                 "or_hist": (None, [P, i64, f64, f64, f64, f64, i32, i32, P, P]),
                 "or_hist_tiled": (None, [P, i64, i32, P, i32, i32, f64, f64, f64, f64, i32, i32, P, P, P]),
                 "or_affine": (None, [P, i64, i32, P, f64]),
@@ -140,6 +141,23 @@ def solve(coeffs, tol: float = 1e-13, max_its: int = 40, shift: int = SHIFT_RAYL
     if used < 0:
         raise ValueError(f"oracle solve: unsupported degree {d}")
     return roots, status, sweeps, used
+
+
+def solve_fixed(coeffs, T: int = 10, shift: int = SHIFT_RAYLEIGH, exc_period: int = 0):
+    """Alg. 2's fixed schedule: T sweeps per eigenvalue, no deflation test.
+    Returns (roots [n, d], status [n])."""
+    coeffs = _c128(coeffs)
+    if coeffs.ndim == 1:
+        coeffs = coeffs[None, :]
+    n, K = coeffs.shape
+    roots = np.zeros((n, K - 1), np.complex128)
+    status = np.zeros(n, np.uint8)
+    for i in range(n):
+        rc = lib().or_solve_fixed(_p(coeffs[i]), K - 1, T, shift, exc_period, _p(roots[i]))
+        if rc < 0:
+            raise ValueError("oracle solve_fixed: bad degree or T")
+        status[i] = rc
+    return roots, status
 
 
 def hist(roots, window, W: int = 1920, H: int = 1080):

@@ -196,6 +196,42 @@ int or_solve_one(const double *a, int d, double tol, int max_its, int shift_mode
     return status;
 }
 
+/* Alg. 2 exactly as printed: t = (n-1) T sweeps; sweep i works on the
+ * leading m = n - floor(i / T) rows and columns with the shift of that
+ * block; after each sweep eig[m-1] is the diagonal entry h[m-1][m-1] (the
+ * last write for each m stands); eig[0] = h[0][0]. No deflation test. */
+int or_solve_fixed(const double *a_in, int d, int T, int shift_mode, int exc_period, double *roots)
+{
+    cplx a[OR_MAX_DEGREE + 1], eig[OR_MAX_DEGREE];
+    if (d < 1 || d > OR_MAX_DEGREE || T < 1) return -1;
+    for (int k = 0; k <= d; ++k) a[k] = ld(a_in + 2 * k);
+    int degenerate = (a[d] == 0.0);
+    for (int k = 0; k <= d; ++k)
+        if (!finite_c(a[k])) degenerate = 1;
+    if (degenerate) {
+        for (int j = 0; j < d; ++j) st(roots + 2 * j, CMPLX(NAN, NAN));
+        return OR_DEGENERATE;
+    }
+    cplx b[OR_MAX_DEGREE], A[OR_MAX_DEGREE * OR_MAX_DEGREE];
+    for (int k = 0; k < d; ++k) b[k] = a[k] / a[d];
+    companion(b, d, A);
+    int n = d;
+    for (int i = 0; i < (n - 1) * T; ++i) {
+        int m = n - i / T;
+        int its = i % T;
+        cplx shift;
+        if (shift_mode == OR_SHIFT_WILKINSON || (its > 0 && exc_period > 0 && its % exc_period == 0))
+            shift = wilkinson(A, n, m);
+        else
+            shift = AT(A, n, m - 1, m - 1);
+        qr_sweep(A, n, m, shift);
+        eig[m - 1] = AT(A, n, m - 1, m - 1);
+    }
+    eig[0] = AT(A, n, 0, 0);
+    for (int j = 0; j < d; ++j) st(roots + 2 * j, eig[j]);
+    return OR_OK;
+}
+
 int or_max_threads(void)
 {
 #ifdef _OPENMP

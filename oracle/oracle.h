@@ -58,6 +58,10 @@ int or_solve_batch(const double *coef, int64_t n, int d, double tol, int max_its
                    int shift_mode, int exc_period, double *roots, uint8_t *status,
                    int32_t *sweeps, int threads);
 
+/* Alg. 2 as printed: (d-1) T sweeps, the active size dropping every T
+ * sweeps, no deflation test. Returns the status (OK or DEGENERATE). */
+int or_solve_fixed(const double *a, int d, int T, int shift_mode, int exc_period, double *roots);
+
 /* Root-density histogram: hist[iy*W + ix] += 1 for every root inside the
  * window, *oow += 1 for every other root (NaN included). */
 void or_hist(const double *roots, int64_t n_roots, double xmin, double xmax,

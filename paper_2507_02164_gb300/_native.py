@@ -23,7 +23,7 @@ class Params(ctypes.Structure):
                 ("exc_period", ctypes.c_int32), ("polish_steps", ctypes.c_int32),
                 ("residual_tol", ctypes.c_double), ("collapse_tol", ctypes.c_double),
                 ("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("polish_extra", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("polish_extra", ctypes.c_int32), ("fixed_sweeps", ctypes.c_int32)]
 
 
 class Window(ctypes.Structure):

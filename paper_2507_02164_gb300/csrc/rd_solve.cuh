@@ -44,6 +44,7 @@ struct SolveArgs {
     int exc_period;
     int polish_steps;
     int polish_extra;
+    int fixed_sweeps;  // > 0: exactly this many sweeps per eigenvalue, no deflation test
     double residual_tol;
     double collapse_tol;
     double *roots;    // [N][n] c128 or null
@@ -262,7 +263,9 @@ __device__ __forceinline__ void solve_warp(const SolveArgs &A, const void *coeff
             if (m >= 2) {
                 cx<T> ta, tb, tc, td;
                 trailing<N, T>(h, m, ta, tb, tc, td);
-                bool small = abs1(tc) <= tol * (abs1(ta) + abs1(td));
+                // adaptive: the bottom subdiagonal is negligible; fixed schedule
+                // (Alg. 2): this eigenvalue has had its T sweeps
+                bool small = A.fixed_sweeps > 0 ? (its >= A.fixed_sweeps) : (abs1(tc) <= tol * (abs1(ta) + abs1(td)));
                 if (small || its >= A.max_iters) {
                     not_conv |= !small;
                     m -= 1;
@@ -306,7 +309,12 @@ __device__ __forceinline__ void solve_warp(const SolveArgs &A, const void *coeff
 #pragma unroll
             for (int j = 0; j < N; ++j) zq[j] = {h[j][j].re, h[j][j].im};
             unsigned newton = 0;
-            if (!__all_sync(0xffffffffu, degenerate)) {
+            const bool polish = A.polish_steps > 0 || A.polish_extra > 0;
+            if (!polish) {
+                // FP32 eigenvalues as they are (the paper's precision), no check
+#pragma unroll
+                for (int j = 0; j < N; ++j) z[j] = f2d(zq[j]);
+            } else if (!__all_sync(0xffffffffu, degenerate)) {
                 // the original coefficients again (an L1/L2 hit: this warp read them
                 // at the start of the sweep), exactly in FP64 and rounded to FP32
                 cx<double> ad[N + 1];
@@ -434,7 +442,7 @@ __device__ __forceinline__ void solve_warp(const SolveArgs &A, const void *coeff
                 if (reject && st == RD_STATUS_OK && !degenerate) st = RD_STATUS_REJECTED;
             }
             S.add(ST_NEWTON, degenerate ? 0u : newton);
-            const unsigned nw = degenerate ? 0u : newton, nr = degenerate ? 0u : (unsigned)N;
+            const unsigned nw = degenerate ? 0u : newton, nr = (degenerate || !polish) ? 0u : (unsigned)N;
             S.add(ST_F64, (8u * N + 2u) * nw + (8u * N + 4u) * nr);
             S.add(ST_F32, (8u * N + 3u) * nw + (2u * N + 4u) * nr);
         }

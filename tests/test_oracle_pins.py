@@ -480,3 +480,30 @@ def test_root_condition_closed_form(orc):
     |p'(1)| = 1, so kappa = 6; at z = 2, (2 + 6 + 4) / (2 * 1) = 6."""
     k = orc.root_condition(np.array([[2, -3, 1]], complex), np.array([[1, 2]], complex))
     assert np.allclose(k, [[6.0, 6.0]], rtol=1e-15)
+
+
+# ------------------------------------------- Alg. 2's fixed schedule
+
+def test_fixed_schedule_converges_to_the_roots_with_enough_sweeps(orc):
+    """With T = 30 sweeps per eigenvalue and the Wilkinson shift, Alg. 2's
+    fixed schedule reaches the same roots as LAPACK."""
+    co = W.gaussian(81, 300, 6)
+    roots, status = orc.solve_fixed(co, T=30, shift=orc.SHIFT_WILKINSON)
+    assert np.all(status == 0)
+    ref = np.array([np.roots(c[::-1]) for c in co])
+    kappa = orc.root_condition(co, ref)
+    err = matched_errors(roots, ref)
+    assert np.all(err <= DEFL_BOUND * np.maximum(1.0, kappa))
+
+
+def test_fixed_schedule_with_paper_settings_mostly_converges(orc):
+    """T = 10 and the paper's Rayleigh shift (Sec. IV settings): about 90 % of
+    unit-disk polynomials have every root right to 1e-6, and doubling T
+    brings nearly all of them in; the fixed schedule has no test that would
+    stop a level early or keep it going."""
+    co, true_roots = W.unit_disk_roots(1, 2000)
+    roots, status = orc.solve_fixed(co, T=10)
+    ok10 = (matched_errors(roots, true_roots).max(axis=1) < 1e-6).mean()
+    roots, status = orc.solve_fixed(co, T=20)
+    ok20 = (matched_errors(roots, true_roots).max(axis=1) < 1e-6).mean()
+    assert 0.85 < ok10 < 0.95 and ok20 > 0.995
