@@ -13,7 +13,7 @@
 //
 // Kernel: one warp per sub-disk, lane q owns angle theta_q; the radial sums
 // u_j(q) = sum_p (w_p r_p^{j+1}) g_pq use real weights (2 FMA per term), then
-// v_j = sum_q u_j(q) e^{-i j theta_q} is a warp butterfly. The 512 samples of a
+// v_j = sum_q u_j(q) e^{-i j theta_q} is a warp reduce-scatter. The 512 samples of a
 // sub-disk (8 KB) are read once, 32 consecutive doubles2 per load.
 #include <cmath>
 
@@ -77,6 +77,31 @@ int l2_nodes_host(int nr, double *r, double *w)
     return 0;
 }
 
+// Sum each of the V values of every lane over the warp (reduce-scatter).
+// Level by level (offsets 16, 8, 4, 2) a lane keeps one half of its values,
+// sends the other half to its partner and adds what it receives; the last
+// level (offset 1) adds the partner's copy of the same value. Afterwards lane
+// L holds the warp sum of value (L >> 1) & (V - 1); V = 16: 16 additions per
+// lane instead of 5 V for V separate butterflies.
+template <int V>
+__device__ __forceinline__ double warp_reduce_scatter(double (&v)[V])
+{
+    const int lane = threadIdx.x & 31;
+    static_assert(V == 16, "four halving levels");
+#pragma unroll
+    for (int lev = 0; lev < 4; ++lev) {
+        const int o = 16 >> lev, half = V >> (lev + 1);
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            double send = upper ? v[i] : v[i + half];
+            double keep = upper ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 __global__ void __launch_bounds__(256) l2_kernel(const double2 *__restrict__ samples, int64_t n, int nr,
                                                  int degree, double2 *coeffs, const L2Tables T)
 {
@@ -104,19 +129,29 @@ __global__ void __launch_bounds__(256) l2_kernel(const double2 *__restrict__ sam
                     ui[j] = fma(T.wr[p][j], v.y, ui[j]);
                 }
         }
+        // angular sums v_j = sum_q u_j(q) e^{-i j theta_q}: this lane's term, then
+        // warp sums, 8 coefficients (16 reals) per reduce-scatter pass
 #pragma unroll
-        for (int j = 0; j <= L2_MAX_DEG; ++j)
-            if (j <= degree) {
-                double c = twr[j], sn = twi[j];
-                double vr = fma(ur[j], c, -ui[j] * sn);
-                double vi = fma(ur[j], sn, ui[j] * c);
+        for (int j0 = 0; j0 <= L2_MAX_DEG; j0 += 8) {
+            if (j0 > degree) break;
+            double val[16];
 #pragma unroll
-                for (int off = 16; off >= 1; off >>= 1) {
-                    vr += __shfl_xor_sync(0xffffffffu, vr, off);
-                    vi += __shfl_xor_sync(0xffffffffu, vi, off);
+            for (int jj = 0; jj < 8; ++jj) {
+                const int j = j0 + jj;
+                double vr = 0.0, vi = 0.0;
+                if (j <= L2_MAX_DEG && j <= degree) {
+                    vr = fma(ur[j], twr[j], -ui[j] * twi[j]);
+                    vi = fma(ur[j], twi[j], ui[j] * twr[j]);
                 }
-                if (lane == j) coeffs[(int64_t)j * n + s] = make_double2(vr, vi);
+                val[2 * jj] = vr;
+                val[2 * jj + 1] = vi;
             }
+            // lane 4 jj holds Re of coefficient j0 + jj, lane 4 jj + 2 its Im
+            double sum = warp_reduce_scatter<16>(val);
+            double im = __shfl_down_sync(0xffffffffu, sum, 2);
+            const int jj = lane >> 2;
+            if ((lane & 3) == 0 && j0 + jj <= degree) coeffs[(int64_t)(j0 + jj) * n + s] = make_double2(sum, im);
+        }
     }
 }
 
