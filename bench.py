@@ -258,8 +258,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed_leg(mode: str):
-        p = api.params(mode)
+    from paper_2507_02164_gb300 import autotune
+    tuned = {m: autotune.tune(m, degrees=[DEGREE]) for m in ("mixed",) + (() if args.no_plain else ("plain",))}
+
+    def timed_leg(mode: str, **overrides):
+        p = autotune.degree_params(tuned[mode], DEGREE, mode)
+        for k, v in overrides.items():
+            setattr(p, k, v)
         k_start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         k_end = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         t0 = torch.cuda.Event(enable_timing=True)
@@ -296,6 +301,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     launches_per_step = 3  # histogram clear, counter clear, fused solve
     polys_total = n * world * args.steps
     value = polys_total / (elapsed_mx * 1e-3)
+
+    # the double-float polish variant on the same batch (not the headline)
+    elapsed_df, kern_df, st_df, clk_df = timed_leg("mixed", polish_mode=api.N.POLISH_DF)
 
     plain = None
     if not args.no_plain:
@@ -343,7 +351,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "warmup": args.warmup, "ms_per_step": elapsed_mx / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic: seeded Littlewood {1,-1,i,-i} degree-6 polynomials (SplitMix64 seed 2), generated on device",
-        "config": workload_config(args),
+        "config": dict(workload_config(args), launch_shapes={m: tuned[m]["degrees"][str(DEGREE)] for m in tuned}),
         "roofline": roofline,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk_mx,
@@ -354,6 +362,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                   "paper_equiv_gflops": value * 41.9e3 / 1e9,
                   "equiv_qr_sweeps_per_s": value * st_mx["sweeps"] / max(1, st_mx["polys"])},
     }
+    g32, g64 = algorithmic_flops(st_df)
+    t_df = kern_df * 1e-3
+    line["mixed_df_polish"] = {
+        "value": polys_total / (elapsed_df * 1e-3), "unit": UNIT, "ms_per_step": elapsed_df / args.steps,
+        "kernel_ms": kern_df, "fp32_frac": g32 / p32 / t_df, "fp64_frac": g64 / p64 / t_df,
+        "status": {k: st_df[k] for k in ("status_ok", "status_not_converged", "status_rejected", "status_degenerate")},
+        "note": "Newton steps in double-float arithmetic on the FP32 pipe, FP64 final residual check",
+        "clocks": clk_df}
     if plain is not None:
         pv = polys_total / (plain["elapsed_ms"] * 1e-3)
         _, g64 = algorithmic_flops(plain["stats"])
@@ -437,9 +453,19 @@ def run_e2e(args, coeffs_dev, win, dev, world):
     ms = D.max_over_ranks(t0.elapsed_time(t1), device=dev)
     h2d = sum(h.numel() * h.element_size() for h in host)
     d2h = hist_h.numel() * hist_h.element_size() + stats_h.numel() * stats_h.element_size()
+    # the copies alone, for reference: host-to-device bandwidth of this machine
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(comp)
+    for c in range(nchunks):
+        m = host[c].shape[1]
+        bufs[c % 2][:(DEGREE + 1) * m].view(DEGREE + 1, m).copy_(host[c], non_blocking=True)
+    c1.record(comp)
+    torch.cuda.synchronize()
+    h2d_gbs = h2d / (c0.elapsed_time(c1) * 1e-3) / 1e9
     return {"value": n * world * args.steps / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": ms / args.steps, "chunks_per_step": nchunks,
-            "gpu_launches_per_step": 2 + nchunks}
+            "gpu_launches_per_step": 2 + nchunks, "h2d_copy_only_gbs": h2d_gbs}
 
 
 UNEVEN_SEED = 3
@@ -492,12 +518,15 @@ def run_uneven(args, rank: int, world: int, local_rank: int):
     stats = api.new_stats(dev)
     p = api.params("mixed")
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    from paper_2507_02164_gb300 import autotune
+    tuned = autotune.tune("mixed", degrees=range(2, 13))
+    tuning = autotune.uneven_tuning(tuned)
 
     def step_body():
         api.hist_clear(hist)
         api.hist_clear(stats)
-        api.roots_uneven(packed, deg, off, ws, mode="mixed", params_=p, window=win, hist=hist, stats=stats,
-                         want_roots=False, want_status=False)
+        api.roots_uneven(packed, deg, off, ws, mode="mixed", params_=p, tuning=tuning, window=win, hist=hist,
+                         stats=stats, want_roots=False, want_status=False)
 
     step_body()  # eager once (loads the library, sizes the grids)
     torch.cuda.synchronize()
@@ -575,7 +604,9 @@ def run_uneven(args, rank: int, world: int, local_rank: int):
                                f"i64 offsets, bin & pack + 12 persistent per-degree solvers, {W_PIX}x{H_PIX} histogram "
                                f"over [-3,3]x[-1.6875,1.6875]", "polys_per_gpu": n,
                    "coefficients": int(packed.numel()), "l2_flush": "inputs larger than L2 (0.94 GB per step)",
-                   "parallelism": f"dp{world}"},
+                   "parallelism": f"dp{world}",
+                   "launch_shapes": {"groups_1_6_7_9_10_12": tuned["groups"], "per_degree": tuned["degrees"],
+                                     "tuning_seconds": tuned["seconds"]}},
         "roofline": {"bound": "alu", "kernel": "whole step (pack + 12 uneven_solve_kernel launches)",
                      "achieved": (f32 + f64 * p32 / p64) / t / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
                      "frac": f32 / p32 / t + f64 / p64 / t, "traffic": None,

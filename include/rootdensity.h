@@ -72,7 +72,17 @@ typedef struct {
                               that fails the residual check after polish_steps (0..16)          */
     int32_t fixed_sweeps;  /* 0: adaptive deflation (tol). T > 0: the paper's fixed schedule
                               (Alg. 2): exactly T sweeps per eigenvalue, no deflation test       */
+    int32_t polish_mode;   /* RD_MIXED: rd_polish                                                */
+    int32_t reserved;      /* must be 0                                                          */
 } rd_params;
+
+/* RD_POLISH_FP64: every Newton step evaluates p(z) by FP64 Horner.
+ * RD_POLISH_DF: the Newton steps evaluate p(z) in double-float arithmetic
+ * (pairs of FP32 numbers with error-free products and sums, about 2^-48
+ * relative precision) on the FP32 pipe, which GB300 runs 64x faster than its
+ * FP64 pipe; the final residual check is still an FP64 Horner evaluation and
+ * a root that fails it still gets polish_extra FP64 Newton steps. */
+typedef enum { RD_POLISH_FP64 = 0, RD_POLISH_DF = 1 } rd_polish;
 
 /* Defaults: plain tol 1e-13, mixed tol 4 * 2^-24, max_iters 40, Wilkinson
  * shift, exc_period 10, 3 polish steps, 5 extra steps, residual 64 d 2^-53,
@@ -110,6 +120,8 @@ typedef struct {
  * Wilkinson shift and deflation test, in the sweep precision. RD_MIXED adds
  * per Newton step 8d + 2 FP64 (p(z)) and 8d + 3 FP32 (p'(z), step size), and
  * per root 8d + 4 FP64 (final residual, binning) and 2d + 4 FP32 (denominator);
+ * with RD_POLISH_DF a Newton step costs 116d + 3 FP32 (double-float Horner:
+ * 108 FP32 operations per coefficient) and a root 8d + 6 FP64;
  * RD_PLAIN_FP64 adds 4 FP64 per root (binning). */
 
 /* Optional per-polynomial tile clip of the full pipeline (Sec. II, domain

@@ -16,6 +16,7 @@ STATUS_OK, STATUS_NOT_CONVERGED, STATUS_REJECTED, STATUS_DEGENERATE = 0, 1, 2, 3
 C64, C128 = 0, 1
 PLAIN_FP64, MIXED = 0, 1
 SHIFT_WILKINSON, SHIFT_RAYLEIGH = 0, 1
+POLISH_FP64, POLISH_DF = 0, 1
 
 
 class Params(ctypes.Structure):
@@ -23,7 +24,8 @@ class Params(ctypes.Structure):
                 ("exc_period", ctypes.c_int32), ("polish_steps", ctypes.c_int32),
                 ("residual_tol", ctypes.c_double), ("collapse_tol", ctypes.c_double),
                 ("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("polish_extra", ctypes.c_int32), ("fixed_sweeps", ctypes.c_int32)]
+                ("polish_extra", ctypes.c_int32), ("fixed_sweeps", ctypes.c_int32),
+                ("polish_mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Window(ctypes.Structure):

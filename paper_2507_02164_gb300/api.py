@@ -62,6 +62,8 @@ def params(mode="mixed", **overrides) -> N.Params:
     for k, v in overrides.items():
         if k == "shift" and isinstance(v, str):
             v = {"wilkinson": N.SHIFT_WILKINSON, "rayleigh": N.SHIFT_RAYLEIGH}[v]
+        if k == "polish_mode" and isinstance(v, str):
+            v = {"fp64": N.POLISH_FP64, "df": N.POLISH_DF}[v]
         setattr(p, k, v)
     return p
 

@@ -94,6 +94,9 @@ int check_params(const rd_params &p)
         return rd_set_error(RD_EINVAL, "params.block must be 0 or a multiple of 32 in [32, 256]");
     if (p.ctas_per_sm < 0 || p.ctas_per_sm > 64) return rd_set_error(RD_EINVAL, "params.ctas_per_sm must be in [0, 64]");
     if (p.polish_extra < 0 || p.polish_extra > 16) return rd_set_error(RD_EINVAL, "params.polish_extra must be in [0, 16]");
+    if (p.polish_mode != RD_POLISH_FP64 && p.polish_mode != RD_POLISH_DF)
+        return rd_set_error(RD_EINVAL, "params.polish_mode must be RD_POLISH_FP64 or RD_POLISH_DF");
+    if (p.reserved != 0) return rd_set_error(RD_EINVAL, "params.reserved must be 0");
     if (p.fixed_sweeps < 0 || p.fixed_sweeps > p.max_iters)
         return rd_set_error(RD_EINVAL, "params.fixed_sweeps must be in [0, max_iters]");
     return RD_OK;
@@ -121,6 +124,7 @@ int build_solve_args(rd_dtype dtype, int degree_for_tol, rd_mode mode, const rd_
     a.polish_steps = p.polish_steps;
     a.polish_extra = p.polish_extra;
     a.fixed_sweeps = p.fixed_sweeps;
+    a.polish_mode = p.polish_mode;
     a.residual_tol = p.residual_tol > 0 ? p.residual_tol : 64.0 * degree_for_tol * std::ldexp(1.0, -53);
     a.collapse_tol = p.collapse_tol;
     a.roots = roots;
@@ -203,6 +207,8 @@ void rd_default_params(rd_mode mode, rd_params *out)
     out->ctas_per_sm = 0;
     out->polish_extra = 5;
     out->fixed_sweeps = 0;
+    out->polish_mode = RD_POLISH_FP64;
+    out->reserved = 0;
 }
 
 int rd_roots_batched(const void *coeffs, rd_dtype dtype, int degree, int64_t n, rd_mode mode, const rd_params *params,

@@ -178,6 +178,61 @@ __device__ __forceinline__ bool finite_bits(double d)
 __device__ __forceinline__ cx<double> f2d(cx<float> a) { return {f2d(a.re), f2d(a.im)}; }
 __device__ __forceinline__ cx<float> d2f(cx<double> a) { return {d2f(a.re), d2f(a.im)}; }
 
+// ---- double-float arithmetic on the FP32 pipe ----------------------------
+// A value is the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi)/2),
+// about 48 significant bits. TwoSum (Knuth) and the FMA-based exact product
+// make the elementary steps error-free; every operation below uses explicit
+// round-to-nearest intrinsics so that no contraction changes them.
+struct dfl {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfl two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+// requires |a| >= |b| (or a = 0)
+__device__ __forceinline__ dfl fast_two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ dfl df_add(dfl a, dfl b)
+{
+    dfl s = two_sum(a.hi, b.hi);
+    dfl t = two_sum(a.lo, b.lo);
+    s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b)
+{
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);  // exact error of the product
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+
+struct dfc {
+    dfl re, im;
+};
+
+// acc * z + a in double-float complex arithmetic (one Horner step)
+__device__ __forceinline__ dfc dfc_fma(dfc acc, dfc z, dfc a)
+{
+    dfl re = df_add(df_add(df_mul(acc.re, z.re), df_neg(df_mul(acc.im, z.im))), a.re);
+    dfl im = df_add(df_add(df_mul(acc.re, z.im), df_mul(acc.im, z.re)), a.im);
+    return {re, im};
+}
+
 // ---- warp helpers --------------------------------------------------------
 
 __device__ __forceinline__ unsigned warp_sum_u32(unsigned v)

@@ -35,6 +35,10 @@
 
 namespace rd {
 
+// Kernel variants: plain FP64 sweeps; FP32 sweeps with the FP64 Newton
+// polish; FP32 sweeps with the double-float Newton polish.
+enum : int { MODE_PLAIN = 0, MODE_MIXED_FP64 = 1, MODE_MIXED_DF = 2 };
+
 struct SolveArgs {
     const void *coeffs;  // [N+1][n]
     int64_t n;
@@ -45,6 +49,7 @@ struct SolveArgs {
     int polish_steps;
     int polish_extra;
     int fixed_sweeps;  // > 0: exactly this many sweeps per eigenvalue, no deflation test
+    int polish_mode;   // rd_polish (selects the kernel variant at launch)
     double residual_tol;
     double collapse_tol;
     double *roots;    // [N][n] c128 or null
@@ -195,10 +200,11 @@ struct PackedMap {
 // One warp solves (and bins) the 32 polynomials base .. base+31 of a
 // coefficient-major batch `coeffs` of n polynomials of degree N. All 32
 // lanes must call it together.
-template <int N, typename T, typename In, bool MIXED, class Map>
+template <int N, typename T, typename In, int MODE, class Map>
 __device__ __forceinline__ void solve_warp(const SolveArgs &A, const void *coeffs, int64_t n, int64_t base,
                                            const Map &map, const CtaStats &S)
 {
+    constexpr bool MIXED = MODE != MODE_PLAIN;
     const int lane = threadIdx.x & 31;
     const T tol = (T)A.tol;
     {
@@ -340,6 +346,20 @@ __device__ __forceinline__ void solve_warp(const SolveArgs &A, const void *coeff
                     af[N] = {1.0f, 0.0f};
                 }
                 // residual_tol <= 0: the default 64 d 2^-53 for this degree
+                // double-float coefficients for MODE_MIXED_DF: hi = the FP32 rounding,
+                // lo = the FP32 rounding of the remainder (zero for complex64 input)
+                dfc adf[MODE == MODE_MIXED_DF ? N + 1 : 1];
+                if constexpr (MODE == MODE_MIXED_DF) {
+#pragma unroll
+                    for (int k = 0; k <= N; ++k) {
+                        if constexpr (std::is_same<In, float2>::value) {
+                            adf[k] = {{af[k].re, 0.0f}, {af[k].im, 0.0f}};
+                        } else {
+                            adf[k] = {{af[k].re, d2f(ad[k].re - f2d(af[k].re))},
+                                      {af[k].im, d2f(ad[k].im - f2d(af[k].im))}};
+                        }
+                    }
+                }
                 const float rtol = A.residual_tol > 0 ? (float)A.residual_tol : (float)(64.0 * N * 0x1p-53);
                 // residual test |p(z)| <= residual_tol * sum_k |a_k|_1 |z|^k (1-norms
                 // |re| + |im| of the coefficients, at most sqrt(2) above the moduli)
@@ -356,24 +376,52 @@ __device__ __forceinline__ void solve_warp(const SolveArgs &A, const void *coeff
                     cx<float> zf = zq[0];
 #pragma unroll
                     for (int k = 0; k + 1 < N; ++k) zq[k] = zq[k + 1];
-                    cx<double> zj = f2d(zf);
-                    // Newton steps: p(z) by FP64 Horner on the original coefficients,
-                    // p'(z) and the step size in FP32 (they only scale the correction)
-                    for (int step = 0; step < A.polish_steps; ++step) {
-                        cx<double> p = ad[N];
+                    cx<double> zj;
+                    if constexpr (MODE == MODE_MIXED_DF) {
+                        // Newton steps with p(z) in double-float arithmetic on the FP32
+                        // pipe (coefficients split into hi + lo floats), z kept as a
+                        // double-float pair; p'(z) and the step size in FP32
+                        dfc zd = {{zf.re, 0.0f}, {zf.im, 0.0f}};
+                        for (int step = 0; step < A.polish_steps; ++step) {
+                            dfc p = adf[N];
 #pragma unroll
-                        for (int k = N - 1; k >= 0; --k) p = cfma(p, zj, ad[k]);
-                        cx<float> pf = af[N], dp = {0.0f, 0.0f};
+                            for (int k = N - 1; k >= 0; --k) p = dfc_fma(p, zd, adf[k]);
+                            cx<float> pf = af[N], dp = {0.0f, 0.0f};
 #pragma unroll
-                        for (int k = N - 1; k >= 0; --k) {
-                            dp = cfma(dp, zf, pf);
-                            pf = cfma(pf, zf, af[k]);
+                            for (int k = N - 1; k >= 0; --k) {
+                                dp = cfma(dp, zf, pf);
+                                pf = cfma(pf, zf, af[k]);
+                            }
+                            cx<float> r = {__fadd_rn(p.re.hi, p.re.lo), __fadd_rn(p.im.hi, p.im.lo)};
+                            cx<float> dz = cdiv(r, dp);
+                            if (!finite_c(dz)) break;
+                            zd.re = df_add(zd.re, dfl{-dz.re, 0.0f});
+                            zd.im = df_add(zd.im, dfl{-dz.im, 0.0f});
+                            zf = {zd.re.hi, zd.im.hi};
+                            newton += 1;
                         }
-                        cx<float> dz = cdiv(d2f(p), dp);
-                        if (!finite_c(dz)) break;
-                        zj = sub(zj, f2d(dz));
-                        zf = sub(zf, dz);
-                        newton += 1;
+                        // the pair hi + lo is exact in FP64
+                        zj = {f2d(zd.re.hi) + f2d(zd.re.lo), f2d(zd.im.hi) + f2d(zd.im.lo)};
+                    } else {
+                        zj = f2d(zf);
+                        // Newton steps: p(z) by FP64 Horner on the original coefficients,
+                        // p'(z) and the step size in FP32 (they only scale the correction)
+                        for (int step = 0; step < A.polish_steps; ++step) {
+                            cx<double> p = ad[N];
+#pragma unroll
+                            for (int k = N - 1; k >= 0; --k) p = cfma(p, zj, ad[k]);
+                            cx<float> pf = af[N], dp = {0.0f, 0.0f};
+#pragma unroll
+                            for (int k = N - 1; k >= 0; --k) {
+                                dp = cfma(dp, zf, pf);
+                                pf = cfma(pf, zf, af[k]);
+                            }
+                            cx<float> dz = cdiv(d2f(p), dp);
+                            if (!finite_c(dz)) break;
+                            zj = sub(zj, f2d(dz));
+                            zf = sub(zf, dz);
+                            newton += 1;
+                        }
                     }
                     // final FP64 residual
                     cx<double> p = ad[N];
@@ -443,8 +491,16 @@ __device__ __forceinline__ void solve_warp(const SolveArgs &A, const void *coeff
             }
             S.add(ST_NEWTON, degenerate ? 0u : newton);
             const unsigned nw = degenerate ? 0u : newton, nr = (degenerate || !polish) ? 0u : (unsigned)N;
-            S.add(ST_F64, (8u * N + 2u) * nw + (8u * N + 4u) * nr);
-            S.add(ST_F32, (8u * N + 3u) * nw + (2u * N + 4u) * nr);
+            if constexpr (MODE == MODE_MIXED_DF) {
+                // double-float Horner: per coefficient 4 products (7 FP32 ops) and
+                // 4 sums (20) = 108 FP32 ops; FP64 only for the hi + lo assembly,
+                // the final residual and the binning
+                S.add(ST_F64, (8u * N + 6u) * nr);
+                S.add(ST_F32, (116u * N + 3u) * nw + (2u * N + 4u) * nr);
+            } else {
+                S.add(ST_F64, (8u * N + 2u) * nw + (8u * N + 4u) * nr);
+                S.add(ST_F32, (8u * N + 3u) * nw + (2u * N + 4u) * nr);
+            }
         }
         if (degenerate) {
 #pragma unroll
@@ -499,8 +555,8 @@ __device__ __forceinline__ void solve_warp(const SolveArgs &A, const void *coeff
 }
 
 // Uniform batch: warps stride over A.n polynomials, 32 at a time.
-template <int N, typename T, typename In, bool MIXED>
-__global__ void __launch_bounds__(256, (MIXED && N <= 6) ? 2 : 1) solve_kernel(SolveArgs A)
+template <int N, typename T, typename In, int MODE>
+__global__ void __launch_bounds__(256, (MODE != MODE_PLAIN && N <= 6) ? 2 : 1) solve_kernel(SolveArgs A)
 {
     const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t warp_id = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -508,7 +564,7 @@ __global__ void __launch_bounds__(256, (MIXED && N <= 6) ? 2 : 1) solve_kernel(S
     const CtaStats S = stats_begin(acc, A.stats);
     const UniformMap map{A.n};
     for (int64_t base = warp_id * 32; base < A.n; base += warps_total * 32)
-        solve_warp<N, T, In, MIXED>(A, A.coeffs, A.n, base, map, S);
+        solve_warp<N, T, In, MODE>(A, A.coeffs, A.n, base, map, S);
     stats_end(S, A.stats);
 }
 

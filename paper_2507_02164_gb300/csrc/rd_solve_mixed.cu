@@ -4,7 +4,11 @@
 namespace rd {
 int launch_solve_mixed(int degree, rd_dtype dt, const SolveArgs &a, int block, int ctas_per_sm, cudaStream_t st)
 {
-    if (dt == RD_C64) return launch_degree<float2, true>(degree, a, block, ctas_per_sm, st);
-    return launch_degree<double2, true>(degree, a, block, ctas_per_sm, st);
+    if (a.polish_mode == RD_POLISH_DF) {
+        if (dt == RD_C64) return launch_degree<float2, MODE_MIXED_DF>(degree, a, block, ctas_per_sm, st);
+        return launch_degree<double2, MODE_MIXED_DF>(degree, a, block, ctas_per_sm, st);
+    }
+    if (dt == RD_C64) return launch_degree<float2, MODE_MIXED_FP64>(degree, a, block, ctas_per_sm, st);
+    return launch_degree<double2, MODE_MIXED_FP64>(degree, a, block, ctas_per_sm, st);
 }
 }  // namespace rd

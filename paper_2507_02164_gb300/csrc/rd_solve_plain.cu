@@ -4,7 +4,7 @@
 namespace rd {
 int launch_solve_plain(int degree, rd_dtype dt, const SolveArgs &a, int block, int ctas_per_sm, cudaStream_t st)
 {
-    if (dt == RD_C64) return launch_degree<float2, false>(degree, a, block, ctas_per_sm, st);
-    return launch_degree<double2, false>(degree, a, block, ctas_per_sm, st);
+    if (dt == RD_C64) return launch_degree<float2, MODE_PLAIN>(degree, a, block, ctas_per_sm, st);
+    return launch_degree<double2, MODE_PLAIN>(degree, a, block, ctas_per_sm, st);
 }
 }  // namespace rd

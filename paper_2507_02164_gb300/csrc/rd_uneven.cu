@@ -183,11 +183,11 @@ __global__ void __launch_bounds__(256) uneven_pack_kernel(UnevenArgs U, const E 
 // Persistent solver for the degree-N bin: each warp takes the next task of
 // the bin's queue (task = 32 consecutive slots) until the queue is empty.
 // One kernel per degree keeps each degree's own register allocation.
-template <int N, typename In, bool MIXED>
-__global__ void __launch_bounds__(256, (MIXED && N <= 6) ? 2 : 1)
+template <int N, typename In, int MODE>
+__global__ void __launch_bounds__(256, (MODE != MODE_PLAIN && N <= 6) ? 2 : 1)
     uneven_solve_kernel(SolveArgs A, UnevenHeader *hdr, const uint32_t *perm, const char *bins, const int64_t *offsets)
 {
-    using T = typename std::conditional<MIXED, float, double>::type;
+    using T = typename std::conditional<MODE != MODE_PLAIN, float, double>::type;
     __shared__ unsigned long long acc[ST_WORDS];
     const CtaStats S = stats_begin(acc, A.stats);
     const int lane = threadIdx.x & 31;
@@ -200,16 +200,16 @@ __global__ void __launch_bounds__(256, (MIXED && N <= 6) ? 2 : 1)
         if (lane == 0) t = atomicAdd(&hdr->head[N], 1u);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= tasks) break;
-        solve_warp<N, T, In, MIXED>(A, base, cnt, (int64_t)t * 32, map, S);
+        solve_warp<N, T, In, MODE>(A, base, cnt, (int64_t)t * 32, map, S);
     }
     stats_end(S, A.stats);
 }
 
-template <int N, typename In, bool MIXED>
+template <int N, typename In, int MODE>
 static int launch_degree_bin(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, int block,
                              int ctas_per_sm, cudaStream_t st)
 {
-    auto kern = uneven_solve_kernel<N, In, MIXED>;
+    auto kern = uneven_solve_kernel<N, In, MODE>;
     int per_sm = ctas_per_sm;
     if (per_sm <= 0) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0) != cudaSuccess || per_sm < 1)
@@ -221,13 +221,13 @@ static int launch_degree_bin(const SolveArgs &a, const UnevenLayout &L, const in
 }
 
 // Degree bins largest first: the most expensive work starts first.
-template <typename In, bool MIXED>
+template <typename In, int MODE>
 static int launch_bins(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, const int *block,
                        const int *cps, cudaStream_t st)
 {
     int rc = 0;
 #define RD_BIN(D, G) \
-    if (!rc) rc = launch_degree_bin<D, In, MIXED>(a, L, offsets, block[G], cps[G], st);
+    if (!rc) rc = launch_degree_bin<D, In, MODE>(a, L, offsets, block[G], cps[G], st);
     RD_BIN(12, 2) RD_BIN(11, 2) RD_BIN(10, 2) RD_BIN(9, 1) RD_BIN(8, 1) RD_BIN(7, 1)
     RD_BIN(6, 0) RD_BIN(5, 0) RD_BIN(4, 0) RD_BIN(3, 0) RD_BIN(2, 0) RD_BIN(1, 0)
 #undef RD_BIN
@@ -262,10 +262,15 @@ int launch_uneven(const SolveArgs &a, rd_dtype dt, const uint8_t *degrees, const
         uneven_pack_kernel<double2><<<(unsigned)ctas, tb, 0, st>>>(U, reinterpret_cast<const double2 *>(a.coeffs),
                                                                    L.hdr, L.perm, reinterpret_cast<double2 *>(L.bins));
     if ((rc = rd_check_launch("uneven_pack_kernel"))) return rc;
-    if (dt == RD_C64) return mixed ? launch_bins<float2, true>(a, L, offsets, block, cps, st)
-                                   : launch_bins<float2, false>(a, L, offsets, block, cps, st);
-    return mixed ? launch_bins<double2, true>(a, L, offsets, block, cps, st)
-                 : launch_bins<double2, false>(a, L, offsets, block, cps, st);
+    const int mode = !mixed ? MODE_PLAIN : (a.polish_mode == RD_POLISH_DF ? MODE_MIXED_DF : MODE_MIXED_FP64);
+    if (dt == RD_C64) {
+        if (mode == MODE_PLAIN) return launch_bins<float2, MODE_PLAIN>(a, L, offsets, block, cps, st);
+        if (mode == MODE_MIXED_DF) return launch_bins<float2, MODE_MIXED_DF>(a, L, offsets, block, cps, st);
+        return launch_bins<float2, MODE_MIXED_FP64>(a, L, offsets, block, cps, st);
+    }
+    if (mode == MODE_PLAIN) return launch_bins<double2, MODE_PLAIN>(a, L, offsets, block, cps, st);
+    if (mode == MODE_MIXED_DF) return launch_bins<double2, MODE_MIXED_DF>(a, L, offsets, block, cps, st);
+    return launch_bins<double2, MODE_MIXED_FP64>(a, L, offsets, block, cps, st);
 }
 
 }  // namespace rd

@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported_and_bound():
 
 
 def test_struct_sizes_match_header_layout():
-    assert ctypes.sizeof(N.Params) == 56
+    assert ctypes.sizeof(N.Params) == 64
     assert ctypes.sizeof(N.Window) == 32
     assert ctypes.sizeof(N.Clip) == 64
     assert N.STATS_WORDS == 14
@@ -48,7 +48,7 @@ def test_default_params():
     assert p.tol == 1e-13 and p.max_iters == 40 and p.shift == N.SHIFT_WILKINSON
     q = N.default_params(N.MIXED)
     assert q.tol == 4 * 2.0 ** -24 and q.polish_steps == 3 and q.collapse_tol == 1e-9
-    assert q.polish_extra == 5 and q.fixed_sweeps == 0
+    assert q.polish_extra == 5 and q.fixed_sweeps == 0 and q.polish_mode == N.POLISH_FP64 and q.reserved == 0
 
 
 @pytest.mark.parametrize("nr", [1, 2, 7, 16, 32])

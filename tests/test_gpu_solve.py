@@ -232,3 +232,28 @@ def test_paper_fixed_schedule_fp32_matches_oracle_fixed_schedule(dev, orc):
     err = matched_errors(roots[converged], ref[converged])
     kappa = orc.root_condition(co32[converged], ref[converged])
     assert (err <= 1e-5 * np.maximum(1.0, kappa)).mean() > 0.99
+
+
+# ------------------------------------------------ double-float polish variant
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_double_float_polish_matches_oracle(dev, orc, dtype):
+    """RD_POLISH_DF: Newton steps in double-float arithmetic, FP64 final check;
+    same 1e-9 bar as the FP64 polish, on the unit-disk and Littlewood batches."""
+    co, true_roots = WL.unit_disk_roots(1, 65536)
+    if dtype == torch.complex64:
+        co = co.astype(np.complex64).astype(np.complex128)
+    roots, status, hist, st = _solve(to_soa(co, dev, dtype), "mixed", WIN1, polish_mode="df")
+    ref, _, _, _ = orc.solve(co, tol=1e-13)
+    assert np.all((status == 0) | (status == 2)) and (status == 2).mean() <= MAX_REJECTED
+    ok = status == 0
+    compare_roots(roots[ok], ref[ok], co[ok], orc, MIXED_TOL, KAPPA_MIXED)
+    h_ref, _ = orc.hist(roots, WIN1.tuple(), W, H)
+    assert np.array_equal(hist_np(hist), h_ref)
+    idx = np.arange(1 << 16, dtype=np.uint64) * np.uint64(1024)
+    cl = WL.littlewood(2, idx)
+    roots, status, _, _ = _solve(to_soa(cl, dev, torch.complex64), "mixed", polish_mode="df")
+    ref, _, _, _ = orc.solve(cl.astype(np.complex128))
+    ok = status == 0
+    assert ok.mean() >= 1 - MAX_REJECTED
+    compare_roots(roots[ok], ref[ok], cl[ok].astype(np.complex128), orc, MIXED_TOL, KAPPA_MIXED)
