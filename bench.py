@@ -444,11 +444,12 @@ def run_e2e(args, coeffs_dev, win, dev, world):
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(comp)
-    for _ in range(args.steps):
-        step()
-    t1.record(comp)
-    torch.cuda.synchronize()
+    with ClockSampler(dev.index or 0) as clk:
+        t0.record(comp)
+        for _ in range(args.steps):
+            step()
+        t1.record(comp)
+        torch.cuda.synchronize()
     from paper_2507_02164_gb300 import dist as D
     ms = D.max_over_ranks(t0.elapsed_time(t1), device=dev)
     h2d = sum(h.numel() * h.element_size() for h in host)
@@ -465,7 +466,7 @@ def run_e2e(args, coeffs_dev, win, dev, world):
     h2d_gbs = h2d / (c0.elapsed_time(c1) * 1e-3) / 1e9
     return {"value": n * world * args.steps / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": ms / args.steps, "chunks_per_step": nchunks,
-            "gpu_launches_per_step": 2 + nchunks, "h2d_copy_only_gbs": h2d_gbs}
+            "gpu_launches_per_step": 2 + nchunks, "h2d_copy_only_gbs": h2d_gbs, "clocks": clk.summary()}
 
 
 UNEVEN_SEED = 3

@@ -146,3 +146,22 @@ def test_soft_density_loss_gradients_on_1024_polynomials(dev, orc):
         assert rel.max() <= 1e-6, (i, rel.max())
         checked += 1
     assert checked > 900
+
+
+def test_full_size_adjoint_sampled(dev, orc):
+    """2^20 degree-6 polynomials (complex128): forward mixed roots, adjoint of
+    L = sum |z|^2; 4096 sampled polynomials match the oracle's adjoint of the
+    same roots to 1e-12."""
+    n = 1 << 20
+    co = WL.gaussian(4, n, 6)
+    coeffs = to_soa(co, dev)
+    roots, status = api.roots_batched(coeffs, mode="mixed")
+    grad = api.roots_backward(coeffs, roots, 2.0 * roots)
+    torch.cuda.synchronize()
+    idx = np.linspace(0, n - 1, 4096).astype(np.int64)
+    z = roots.cpu().numpy().T[idx]
+    g_ref, st = orc.roots_backward(co[idx], z, 2.0 * z)
+    g = grad.cpu().numpy().T[idx]
+    ok = st == 0
+    scale = np.maximum(np.abs(g_ref).max(axis=1, keepdims=True), 1e-300)
+    assert (np.abs(g - g_ref)[ok] / scale[ok]).max() <= 1e-12

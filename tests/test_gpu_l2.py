@@ -88,3 +88,42 @@ def test_full_pipeline_block_of_tiles(dev, orc):
     keep_mask = t == np.repeat(tile_idx, 6)
     step = np.abs(fz / fp)[keep_mask]
     assert np.all(step < 1e-6), step.max()
+
+
+def test_full_pipeline_all_tiles(dev, orc):
+    """All 129,600 sub-disks of the 480 x 270 grid, as bench.py times them:
+    the fused histogram equals the oracle's clip + binning of the GPU roots
+    bit for bit, the L2 coefficients of a sample of 2,000 sub-disks match the
+    oracle's, and every kept root is a zero of f (one Newton step on f moves
+    it by less than 1e-6)."""
+    win = (-4.0, 4.0, -2.25, 2.25)
+    centres, rho, _, _ = WL.tiles(*win, 480, 270)
+    c = torch.from_numpy(centres).to(dev)
+    w = api.l2_sample_points(16, 32, dev)
+    samples = WL.f_sin_cube(c[:, None] + rho * w[None, :]).contiguous()
+    coeffs = api.l2_approx(samples, 16, 32, 6)
+    hist = api.new_hist(1920, 1080, dev)
+    roots = torch.empty((6, c.numel()), dtype=torch.complex128, device=dev)
+    stats = api.new_stats(dev)
+    clip = api.make_clip(c, rho, 480, 270, api.Window(*win))
+    api.roots_density(coeffs, api.Window(*win), hist, mode="mixed", clip=clip, roots=roots, stats=stats)
+    torch.cuda.synchronize()
+    z = orc.affine(roots_poly_major(roots), centres, rho)
+    h_ref, oow, dropped = orc.hist_tiled(z, np.arange(c.numel()), 480, 270, win)
+    assert np.array_equal(hist_np(hist), h_ref)
+    st = api.stats_dict(stats)
+    assert st["clipped"] == dropped and st["binned"] == int(h_ref.sum())
+    idx = np.linspace(0, c.numel() - 1, 2000).astype(np.int64)
+    ref = orc.l2_approx(samples.cpu().numpy()[idx])
+    # |sin(z^3)| reaches ~1e41 at the window corners: compare relative to each
+    # sub-disk's largest coefficient
+    scale = np.abs(ref).max(axis=1, keepdims=True)
+    assert (np.abs(coeffs.cpu().numpy().T[idx] - ref) / scale).max() <= 1e-13
+    zz = z.reshape(-1)
+    tx = np.floor((zz.real + 4.0) * 60).astype(np.int64)
+    ty = np.floor((2.25 - zz.imag) * 60).astype(np.int64)
+    own = (tx == np.repeat(np.arange(c.numel()), 6) % 480) & (ty == np.repeat(np.arange(c.numel()), 6) // 480)
+    k = zz[own & np.isfinite(zz)]
+    assert k.size == st["binned"]
+    step = np.abs(WL.f_sin_cube(k) / (3 * k ** 2 * np.cos(k ** 3) + 0.5))
+    assert np.all(step < 1e-6), step.max()

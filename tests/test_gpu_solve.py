@@ -257,3 +257,47 @@ def test_double_float_polish_matches_oracle(dev, orc, dtype):
     ok = status == 0
     assert ok.mean() >= 1 - MAX_REJECTED
     compare_roots(roots[ok], ref[ok], cl[ok].astype(np.complex128), orc, MIXED_TOL, KAPPA_MIXED)
+
+
+# ------------------------------------- full size, in the benchmark's launch shape
+
+def test_full_littlewood_batch_sampled(dev, orc):
+    """The 2^26-polynomial Littlewood batch exactly as bench.py times it (fused
+    roots + histogram, autotuned launch shape, mixed), with the roots stored:
+    every counter adds up, the fused histogram equals the standalone binning
+    of the stored roots, and 2^16 polynomials spread over the batch match the
+    oracle at the 1e-9 bar (mixed) and, for the plain FP64 path on the same
+    sample, at 1e-11."""
+    from paper_2507_02164_gb300 import autotune
+    n = 1 << 26
+    coeffs = WL.littlewood_soa_torch(2, 0, n, dev)
+    tuned = autotune.tune("mixed", degrees=[6])
+    p = autotune.degree_params(tuned, 6, "mixed")
+    hist = api.new_hist(W, H, dev)
+    stats = api.new_stats(dev)
+    roots = torch.empty((6, n), dtype=torch.complex128, device=dev)
+    status = torch.empty(n, dtype=torch.uint8, device=dev)
+    api.roots_density(coeffs, WIN2, hist, mode="mixed", params_=p, roots=roots, status=status, stats=stats)
+    torch.cuda.synchronize()
+    st = api.stats_dict(stats)
+    assert st["polys"] == n and st["binned"] + st["out_of_window"] == 6 * n
+    h = hist_np(hist)
+    assert int(h.sum(dtype=np.int64)) == st["binned"]
+    h2 = api.new_hist(W, H, dev)
+    api.density_accumulate(roots.reshape(-1), WIN2, h2)
+    torch.cuda.synchronize()
+    assert np.array_equal(hist_np(h2), h)
+    s = status.cpu().numpy()
+    assert np.all((s == 0) | (s == 2)) and (s == 2).mean() <= MAX_REJECTED
+    idx = np.arange(1 << 16, dtype=np.int64) * 1024 + 511
+    sample = torch.from_numpy(idx).to(dev)
+    r_s = roots[:, sample].cpu().numpy().T
+    co = coeffs[:, sample].cpu().numpy().T.astype(np.complex128)
+    ref, ref_st, _, _ = orc.solve(co)
+    ok = (s[idx] == 0) & (ref_st == 0)
+    compare_roots(r_s[ok], ref[ok], co[ok], orc, MIXED_TOL, KAPPA_MIXED)
+    pr, ps = api.roots_batched(coeffs[:, sample].contiguous(), mode="plain")
+    torch.cuda.synchronize()
+    pr = pr.cpu().numpy().T
+    okp = (ps.cpu().numpy() == 0) & (ref_st == 0)
+    compare_roots(pr[okp], ref[okp], co[okp], orc, PLAIN_TOL, KAPPA_PLAIN)
