@@ -261,8 +261,14 @@ int rd_l2_nodes(int nr, double *r, double *w);
  * <g, h> = integral g conj(h) dA, whose Gram matrix is diagonal:
  * a_j = (j+1)/pi <g, w^j>. coeffs: device rd_c128, coefficient-major
  * [degree+1][n] (ready for rd_roots_*). nt must be 32; nr <= 32; degree <= 12. */
-int rd_l2_approx(const double *samples, int64_t n, int nr, int nt, int degree, double *coeffs,
+int rd_l2_approx(const double *samples, int64_t n, int nr, int nt, int degree, int precision, double *coeffs,
                  void *stream);
+/* precision: RD_L2_FP64 sums in FP64 (the FP64 pipe bounds the kernel);
+ * RD_L2_DF sums in double-float arithmetic on the FP32 pipe (about 2^-48
+ * relative per term, ~1e-14 on the coefficients relative to the largest of a
+ * sub-disk), after scaling each sub-disk's samples by a power of two. */
+#define RD_L2_FP64 0
+#define RD_L2_DF 1
 
 #ifdef __cplusplus
 }

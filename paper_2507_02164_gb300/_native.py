@@ -17,6 +17,7 @@ C64, C128 = 0, 1
 PLAIN_FP64, MIXED = 0, 1
 SHIFT_WILKINSON, SHIFT_RAYLEIGH = 0, 1
 POLISH_FP64, POLISH_DF = 0, 1
+L2_FP64, L2_DF = 0, 1
 
 
 class Params(ctypes.Structure):
@@ -67,7 +68,7 @@ SIGNATURES = {
     "rd_roots_uneven_static": (I32, [P, I32, P, P, I64, I64, I32, ctypes.POINTER(Params),
                                      ctypes.POINTER(UnevenTuning), ctypes.POINTER(Window), I32, I32, P, P, P, P, P]),
     "rd_l2_nodes": (I32, [I32, P, P]),
-    "rd_l2_approx": (I32, [P, I64, I32, I32, I32, P, P]),
+    "rd_l2_approx": (I32, [P, I64, I32, I32, I32, I32, P, P]),
 }
 
 _lock = threading.Lock()

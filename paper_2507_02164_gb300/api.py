@@ -221,15 +221,18 @@ def l2_sample_points(nr: int = 16, nt: int = 32, device="cuda") -> torch.Tensor:
     return (rr[:, None] * torch.exp(1j * th)[None, :]).reshape(-1)
 
 
-def l2_approx(samples: torch.Tensor, nr: int = 16, nt: int = 32, degree: int = 6, coeffs=None, stream=None):
-    """samples [n, nr*nt] complex128 -> coeffs [degree+1, n] complex128 (local variable w)."""
+def l2_approx(samples: torch.Tensor, nr: int = 16, nt: int = 32, degree: int = 6, coeffs=None, stream=None,
+              precision: str = "fp64"):
+    """samples [n, nr*nt] complex128 -> coeffs [degree+1, n] complex128 (local variable w).
+    precision "fp64" (FP64 sums) or "df" (double-float sums on the FP32 pipe)."""
     _check_cuda("samples", samples, torch.complex128)
     n = samples.shape[0]
     if samples.shape[1] != nr * nt:
         raise ValueError("samples must have shape [n, nr*nt]")
     if coeffs is None:
         coeffs = torch.empty((degree + 1, n), dtype=torch.complex128, device=samples.device)
-    N.call("rd_l2_approx", _ptr(samples), n, nr, nt, degree, _ptr(coeffs), _stream(stream))
+    N.call("rd_l2_approx", _ptr(samples), n, nr, nt, degree, {"fp64": N.L2_FP64, "df": N.L2_DF}[precision],
+           _ptr(coeffs), _stream(stream))
     return coeffs
 
 

@@ -22,7 +22,8 @@ int l2_nodes_host(int nr, double *r, double *w);
 size_t uneven_workspace_bytes(int64_t n, int64_t n_coeffs, rd_dtype dt);
 int launch_uneven(const SolveArgs &a, rd_dtype dt, const uint8_t *degrees, const int64_t *offsets, int64_t n,
                   int64_t n_coeffs, bool mixed, void *ws, const int *block, const int *cps, cudaStream_t st);
-int launch_l2(const double *samples, int64_t n, int nr, int degree, double *coeffs, cudaStream_t st);
+int launch_l2(const double *samples, int64_t n, int nr, int degree, double *coeffs, int precision,
+              cudaStream_t st);
 }  // namespace rd
 
 static thread_local char g_err[512] = "";
@@ -317,8 +318,10 @@ int rd_l2_nodes(int nr, double *r, double *w)
     return rd::l2_nodes_host(nr, r, w);
 }
 
-int rd_l2_approx(const double *samples, int64_t n, int nr, int nt, int degree, double *coeffs, void *stream)
+int rd_l2_approx(const double *samples, int64_t n, int nr, int nt, int degree, int precision, double *coeffs,
+                 void *stream)
 {
+    if (precision != RD_L2_FP64 && precision != RD_L2_DF) return rd_set_error(RD_EINVAL, "precision must be RD_L2_FP64 or RD_L2_DF");
     if (nt != 32) return rd_set_error(RD_EUNSUPPORTED, "nt must be 32 (one angle per lane)");
     if (nr < 1 || nr > 32) return rd_set_error(RD_EINVAL, "nr must be in 1..32");
     if (degree < 0 || degree > 12) return rd_set_error(RD_EINVAL, "degree must be in 0..12");
@@ -326,7 +329,7 @@ int rd_l2_approx(const double *samples, int64_t n, int nr, int nt, int degree, d
     if (n == 0) return RD_OK;
     if (!samples || !aligned(samples, 16) || !coeffs || !aligned(coeffs, 16))
         return rd_set_error(RD_EINVAL, "samples / coeffs null or misaligned");
-    return rd::launch_l2(samples, n, nr, degree, coeffs, reinterpret_cast<cudaStream_t>(stream));
+    return rd::launch_l2(samples, n, nr, degree, coeffs, precision, reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

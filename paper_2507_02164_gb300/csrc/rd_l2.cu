@@ -155,8 +155,164 @@ __global__ void __launch_bounds__(256) l2_kernel(const double2 *__restrict__ sam
     }
 }
 
-int launch_l2(const double *samples, int64_t n, int nr, int degree, double *coeffs, cudaStream_t st)
+// ---- double-float variant on the FP32 pipe --------------------------------
+// Same sums, each term a double-float (hi + lo floats): GB300 runs FP32 64x
+// faster than FP64. Samples are first scaled by a power of two per sub-disk
+// (the largest exponent of its 512 samples becomes 0; sin(z^3) reaches 1e41,
+// beyond FP32) and split into hi + lo floats with integer operations, then
+// the scale is applied back to the FP64 coefficients exactly.
+
+struct L2TablesDF {
+    float whi[L2_MAX_NR][L2_MAX_DEG + 1], wlo[L2_MAX_NR][L2_MAX_DEG + 1];
+    float thi[L2_MAX_DEG + 1][L2_NT][2], tlo[L2_MAX_DEG + 1][L2_NT][2];
+};
+
+// Split d * 2^-shift into hi + lo floats (|d * 2^-shift| <= 2): hi = d's
+// significand rounded to 24 bits, lo = the rest rounded to 24 bits (relative
+// error 2^-48). Magnitudes below the FP32 normal range become zero.
+__device__ __forceinline__ dfl split_scaled(double d, int shift)
 {
+    unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    int E = (int)((b >> 52) & 0x7ff);
+    unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);  // 53-bit significand
+    unsigned long long H = (M + (1ull << 28)) >> 29;                 // rounded to 24 bits (may be 2^24)
+    long long r = (long long)M - (long long)(H << 29);               // |r| <= 2^28, exact remainder
+    int e = E - 1023 - shift;                                         // unbiased exponent after scaling
+    // hi = H * 2^(e - 23): float bits, the carry of H = 2^24 moves into the exponent
+    unsigned hib = sign | (unsigned)((e + 127) << 23) + (unsigned)(H - (1ull << 23));
+    float hi = (e + 127 > 0 && E != 0) ? __uint_as_float(hib) : 0.0f;
+    // lo = r * 2^(e - 52)
+    float lo = __int2float_rn((int)r);
+    int le = e - 52 + 127;
+    lo = (le > 0 && E != 0) ? lo * __uint_as_float((unsigned)le << 23) : 0.0f;
+    lo = sign ? -lo : lo;
+    if (E == 0x7ff) return {__int_as_float(0x7fc00000), 0.0f};  // inf or NaN sample: NaN coefficients
+    return {hi, lo};
+}
+
+__global__ void __launch_bounds__(256) l2_kernel_df(const double2 *__restrict__ samples, int64_t n, int nr,
+                                                    int degree, double2 *coeffs, const L2TablesDF T)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+    dfl twr[L2_MAX_DEG + 1], twi[L2_MAX_DEG + 1];
+#pragma unroll
+    for (int j = 0; j <= L2_MAX_DEG; ++j) {
+        twr[j] = {T.thi[j][lane][0], T.tlo[j][lane][0]};
+        twi[j] = {T.thi[j][lane][1], T.tlo[j][lane][1]};
+    }
+    for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n; s += warps_total) {
+        const double2 *g = samples + s * (int64_t)nr * L2_NT;
+        // per sub-disk scale: the largest biased exponent of its samples
+        unsigned emax = 0;
+        for (int p = 0; p < nr; ++p) {
+            double2 v = __ldg(g + p * L2_NT + lane);
+            unsigned ex = ((unsigned)__double2hiint(v.x) >> 20) & 0x7ffu;
+            unsigned ey = ((unsigned)__double2hiint(v.y) >> 20) & 0x7ffu;
+            emax = max(emax, max(ex, ey));
+        }
+        emax = __reduce_max_sync(0xffffffffu, emax);
+        const int shift = (int)emax - 1023;
+        dfl ur[L2_MAX_DEG + 1], ui[L2_MAX_DEG + 1];
+#pragma unroll
+        for (int j = 0; j <= L2_MAX_DEG; ++j) ur[j] = ui[j] = dfl{0.0f, 0.0f};
+        for (int p = 0; p < nr; ++p) {
+            double2 v = __ldg(g + p * L2_NT + lane);
+            dfl gx = split_scaled(v.x, shift), gy = split_scaled(v.y, shift);
+#pragma unroll
+            for (int j = 0; j <= L2_MAX_DEG; ++j)
+                if (j <= degree) {
+                    const float wh = T.whi[p][j], wl = T.wlo[p][j];
+                    // exact product hi and its error, then TwoSum into the accumulator
+                    float ph = __fmul_rn(wh, gx.hi);
+                    float pe = __fmaf_rn(wh, gx.hi, -ph);
+                    pe = __fmaf_rn(wh, gx.lo, pe);
+                    pe = __fmaf_rn(wl, gx.hi, pe);
+                    dfl t = two_sum(ur[j].hi, ph);
+                    ur[j] = {t.hi, __fadd_rn(ur[j].lo, __fadd_rn(t.lo, pe))};
+                    ph = __fmul_rn(wh, gy.hi);
+                    pe = __fmaf_rn(wh, gy.hi, -ph);
+                    pe = __fmaf_rn(wh, gy.lo, pe);
+                    pe = __fmaf_rn(wl, gy.hi, pe);
+                    t = two_sum(ui[j].hi, ph);
+                    ui[j] = {t.hi, __fadd_rn(ui[j].lo, __fadd_rn(t.lo, pe))};
+                }
+        }
+#pragma unroll
+        for (int j0 = 0; j0 <= L2_MAX_DEG; j0 += 8) {
+            if (j0 > degree) break;
+            dfl val[16];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                const int j = j0 + jj;
+                dfl vr = {0.0f, 0.0f}, vi = {0.0f, 0.0f};
+                if (j <= L2_MAX_DEG && j <= degree) {
+                    dfl a = fast_two_sum(ur[j].hi, ur[j].lo), b = fast_two_sum(ui[j].hi, ui[j].lo);
+                    vr = df_add(df_mul(a, twr[j]), df_neg(df_mul(b, twi[j])));
+                    vi = df_add(df_mul(a, twi[j]), df_mul(b, twr[j]));
+                }
+                val[2 * jj] = vr;
+                val[2 * jj + 1] = vi;
+            }
+            // double-float reduce-scatter (see warp_reduce_scatter)
+#pragma unroll
+            for (int lev = 0; lev < 4; ++lev) {
+                const int o = 16 >> lev, half = 16 >> (lev + 1);
+                const bool upper = (lane & o) != 0;
+#pragma unroll
+                for (int i = 0; i < half; ++i) {
+                    dfl send = upper ? val[i] : val[i + half];
+                    dfl keep = upper ? val[i + half] : val[i];
+                    dfl got = {__shfl_xor_sync(0xffffffffu, send.hi, o), __shfl_xor_sync(0xffffffffu, send.lo, o)};
+                    val[i] = df_add(keep, got);
+                }
+            }
+            dfl got = {__shfl_xor_sync(0xffffffffu, val[0].hi, 1), __shfl_xor_sync(0xffffffffu, val[0].lo, 1)};
+            dfl sum = df_add(val[0], got);
+            // back to FP64 and to the sub-disk's scale (a power of two: exact)
+            double d = (f2d(sum.hi) + f2d(sum.lo)) * __longlong_as_double((long long)(shift + 1023) << 52);
+            double im = __shfl_down_sync(0xffffffffu, d, 2);
+            const int jj = lane >> 2;
+            if ((lane & 3) == 0 && j0 + jj <= degree) coeffs[(int64_t)(j0 + jj) * n + s] = make_double2(d, im);
+        }
+    }
+}
+
+int launch_l2(const double *samples, int64_t n, int nr, int degree, double *coeffs, int precision,
+              cudaStream_t st)
+{
+    if (precision == 1) {
+        L2TablesDF T;
+        double r[L2_MAX_NR], w[L2_MAX_NR];
+        l2_nodes_host(nr, r, w);
+        const double pi = 3.14159265358979323846;
+        for (int p = 0; p < L2_MAX_NR; ++p)
+            for (int j = 0; j <= L2_MAX_DEG; ++j) {
+                double v = 0.0;
+                if (p < nr && j <= degree) v = w[p] * std::pow(r[p], j + 1) * (2.0 * pi / L2_NT) * (j + 1) / pi;
+                T.whi[p][j] = (float)v;
+                T.wlo[p][j] = (float)(v - (double)T.whi[p][j]);
+            }
+        for (int j = 0; j <= L2_MAX_DEG; ++j)
+            for (int q = 0; q < L2_NT; ++q) {
+                int t = (j * q) % L2_NT;
+                double ang = 2.0 * pi * t / L2_NT;
+                double c = std::cos(ang), sn = -std::sin(ang);
+                T.thi[j][q][0] = (float)c;
+                T.tlo[j][q][0] = (float)(c - (double)T.thi[j][q][0]);
+                T.thi[j][q][1] = (float)sn;
+                T.tlo[j][q][1] = (float)(sn - (double)T.thi[j][q][1]);
+            }
+        const int block = 256;
+        int64_t ctas = (n + 7) / 8;
+        int64_t cap = (int64_t)rd_sm_count_cached() * 8;
+        if (ctas > cap) ctas = cap;
+        if (ctas < 1) ctas = 1;
+        l2_kernel_df<<<(unsigned)ctas, block, 0, st>>>(reinterpret_cast<const double2 *>(samples), n, nr, degree,
+                                                       reinterpret_cast<double2 *>(coeffs), T);
+        return rd_check_launch("l2_kernel_df");
+    }
     L2Tables T;
     double r[L2_MAX_NR], w[L2_MAX_NR];
     l2_nodes_host(nr, r, w);

@@ -112,9 +112,11 @@ def test_argument_validation_without_gpu():
     rc, _ = _err(L.rd_density_accumulate(ctypes.c_void_p(64), 4, nanw, 16, 16, ctypes.c_void_p(64), null, null))
     assert rc == N.RD_EINVAL
     # l2: nt must be 32, nr in 1..32
-    rc, _ = _err(L.rd_l2_approx(ctypes.c_void_p(64), 4, 16, 16, 6, ctypes.c_void_p(64), null))
+    rc, _ = _err(L.rd_l2_approx(ctypes.c_void_p(64), 4, 16, 16, 6, 0, ctypes.c_void_p(64), null))
     assert rc == N.RD_EUNSUPPORTED
-    rc, _ = _err(L.rd_l2_approx(ctypes.c_void_p(64), 4, 40, 32, 6, ctypes.c_void_p(64), null))
+    rc, _ = _err(L.rd_l2_approx(ctypes.c_void_p(64), 4, 40, 32, 6, 0, ctypes.c_void_p(64), null))
+    assert rc == N.RD_EINVAL
+    rc, _ = _err(L.rd_l2_approx(ctypes.c_void_p(64), 4, 16, 32, 6, 7, ctypes.c_void_p(64), null))
     assert rc == N.RD_EINVAL
     # backward: bad degree / null
     rc, _ = _err(L.rd_roots_backward(null, N.C128, 0, 4, null, null, null, null, null))

@@ -127,3 +127,34 @@ def test_full_pipeline_all_tiles(dev, orc):
     assert k.size == st["binned"]
     step = np.abs(WL.f_sin_cube(k) / (3 * k ** 2 * np.cos(k ** 3) + 0.5))
     assert np.all(step < 1e-6), step.max()
+
+
+# ---------------------------------------------- double-float L2 variant
+
+def test_l2_double_float_matches_oracle(dev, orc):
+    """RD_L2_DF on random samples of widely varying scale (each sub-disk
+    scaled by up to 2^+-120): within 1e-13 of the oracle relative to each
+    sub-disk's largest coefficient; the worked example within 1e-13."""
+    g = np.random.default_rng(4)
+    n = 3000 + 7
+    s = g.standard_normal((n, 512)) + 1j * g.standard_normal((n, 512))
+    s *= 2.0 ** g.integers(-120, 120, size=(n, 1))
+    got = api.l2_approx(torch.from_numpy(s).to(dev), 16, 32, 6, precision="df").cpu().numpy().T
+    ref = orc.l2_approx(s)
+    scale = np.abs(ref).max(axis=1, keepdims=True)
+    assert (np.abs(got - ref) / scale).max() <= 1e-13
+    w = api.l2_sample_points(16, 32, dev)
+    a = api.l2_approx((1.0 / (1.0 - 0.3 * w))[None, :].contiguous(), 16, 32, 6, precision="df").cpu().numpy()[:, 0]
+    assert np.abs(a - 0.3 ** np.arange(7)).max() <= 1e-13
+
+
+def test_l2_double_float_on_the_full_tile_grid(dev, orc):
+    win = (-4.0, 4.0, -2.25, 2.25)
+    centres, rho, _, _ = WL.tiles(*win, 480, 270)
+    c = torch.from_numpy(centres).to(dev)
+    w = api.l2_sample_points(16, 32, dev)
+    samples = WL.f_sin_cube(c[:, None] + rho * w[None, :]).contiguous()
+    df = api.l2_approx(samples, 16, 32, 6, precision="df").cpu().numpy().T
+    fp = api.l2_approx(samples, 16, 32, 6, precision="fp64").cpu().numpy().T
+    scale = np.abs(fp).max(axis=1, keepdims=True)
+    assert (np.abs(df - fp) / scale).max() <= 1e-13
