@@ -619,7 +619,8 @@ def run_uneven(args, rank: int, world: int, local_rank: int):
                                f"over [-3,3]x[-1.6875,1.6875]", "polys_per_gpu": n,
                    "coefficients": int(packed.numel()), "l2_flush": "inputs larger than L2 (0.94 GB per step)",
                    "parallelism": f"dp{world}",
-                   "launch_shapes": {"groups_1_6_7_9_10_12": tuned["groups"], "per_degree": tuned["degrees"],
+                   "launch_shapes": {"per_degree": {d: {k: e[k] for k in ("lanes", "block", "ctas_per_sm", "ms")}
+                                                      for d, e in tuned["degrees"].items()},
                                      "tuning_seconds": tuned["seconds"]}},
         "roofline": {"bound": "alu", "kernel": "whole step (pack + 12 uneven_solve_kernel launches)",
                      "achieved": (f32 + f64 * p32 / p64) / t / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
@@ -727,7 +728,9 @@ def run_pipeline(args, rank, world, local_rank):
     """The full pipeline: f(z) = sin(z^3) + 0.5 z on [-4,4]x[-2.25,2.25] in
     480 x 270 tiles; samples at the 16 x 32 nodes of every sub-disk are made
     on the device by torch outside the timed step; a step is L2
-    approximation + fused mixed roots, tile clip and histogram."""
+    approximation + fused mixed roots, tile clip and histogram. Beside it:
+    the one-launch path (rd_field_density, f evaluated inside the kernel) and
+    the split path's sampling time."""
     import torch
 
     from paper_2507_02164_gb300 import api, build, workloads as WL
@@ -759,6 +762,31 @@ def run_pipeline(args, rank, world, local_rank):
             api.roots_density(coeffs, win, hist, mode="mixed", clip=clip, stats=stats)
             e[2].record(stream)
         return step
+
+    # the split path's producer: f at every node by torch (not in the timed
+    # step; the evaluation above warmed torch's kernels)
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev_s[0].record(stream)
+    samples = WL.f_sin_cube(c[:, None] + rho * w[None, :]).contiguous()
+    ev_s[1].record(stream)
+    torch.cuda.synchronize()
+    sampling_ms = ev_s[0].elapsed_time(ev_s[1])
+
+    # the one-launch path (rd_field_density): f, L2, roots, clip and histogram
+    # in one kernel, no sample array
+    spec = api.field_spec(win, 480, 270, radius=rho)
+    e_f = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def fused_step():
+        api.hist_clear(hist)
+        api.hist_clear(stats)
+        e_f[0].record(stream)
+        api.field_density(spec, win, hist, mode="mixed", stats=stats)
+        e_f[1].record(stream)
+
+    ms_fused, clk_fused = _timed(fused_step, args, dev, world, local_rank)
+    fused_kernel_ms = e_f[0].elapsed_time(e_f[1])
+    st_fused = api.stats_dict(stats)
 
     # the FP64 L2 sums (RD_L2_FP64), for reference
     ms_fp64, _ = _timed(make_step("fp64"), args, dev, world, local_rank)
@@ -792,6 +820,15 @@ def run_pipeline(args, rank, world, local_rank):
         "l2_fp64": {"value": n * world * args.steps / (ms_fp64 * 1e-3), "ms_per_step": ms_fp64 / args.steps,
                     "l2_approx_ms": l2_fp64_ms, "fp64_tflops": l2_flops / (l2_fp64_ms * 1e-3) / 1e12,
                     "fp64_frac": l2_flops / (l2_fp64_ms * 1e-3) / p64},
+        "fused": {"value": n * world * args.steps / (ms_fused * 1e-3), "unit": "sub-disks/s",
+                  "ms_per_step": ms_fused / args.steps, "field_kernel_ms": fused_kernel_ms,
+                  "samples_per_s": n * 512 / (fused_kernel_ms * 1e-3), "kept_roots": st_fused["binned"],
+                  "note": "rd_field_density: f evaluated in FP64 at the 16x32 nodes inside the kernel, L2, roots, "
+                          "clip and histogram in one launch; no 1.06 GB sample array",
+                  "clocks": clk_fused},
+        "split_end_to_end": {"sampling_ms": sampling_ms, "l2_plus_roots_ms": ms / args.steps,
+                             "value": n / ((sampling_ms + ms / args.steps) * 1e-3),
+                             "note": "torch evaluates f at every node into a 1.06 GB array, then the timed step"},
         "kept_roots": st["binned"], "clipped": st["clipped"],
         "status": {k: st[k] for k in ("status_ok", "status_not_converged", "status_rejected", "status_degenerate")},
         "gpu_launches": 4 * args.steps, "clocks": clk,

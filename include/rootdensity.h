@@ -73,7 +73,10 @@ typedef struct {
     int32_t fixed_sweeps;  /* 0: adaptive deflation (tol). T > 0: the paper's fixed schedule
                               (Alg. 2): exactly T sweeps per eigenvalue, no deflation test       */
     int32_t polish_mode;   /* RD_MIXED: rd_polish                                                */
-    int32_t reserved;      /* must be 0                                                          */
+    int32_t lanes;         /* lanes per polynomial: 0 = chosen per degree and mode; 1 = one
+                              thread holds the whole matrix; 2 = two lanes share it (columns
+                              split by parity, rotations exchanged by warp shuffles; degree
+                              >= 2 and RD_POLISH_FP64 only, degree 1 always runs one lane)   */
 } rd_params;
 
 /* RD_POLISH_FP64: every Newton step evaluates p(z) by FP64 Horner.
@@ -186,8 +189,8 @@ int rd_hist_clear(uint32_t *hist, int64_t words, void *stream);
  * the same way without the leading coefficient: root j of polynomial i is
  * roots[offsets[i] - i + j] (rd_c128). The call bins the batch by degree
  * into the workspace, then solves every degree bin with a persistent kernel
- * that takes 32-polynomial tasks from the bin's atomic queue, binning roots
- * into hist when it is given.
+ * that takes 32-polynomial tasks (16 with two lanes per polynomial) from the
+ * bin's atomic queue, binning roots into hist when it is given.
  * A polynomial whose offsets do not hold degree+1 coefficients inside the
  * array, or whose degree is outside 1..12, gets RD_STATUS_DEGENERATE (NaN
  * roots when its offsets are consistent; nothing written otherwise).
@@ -195,12 +198,16 @@ int rd_hist_clear(uint32_t *hist, int64_t words, void *stream);
  *             dtype) bytes, 256-byte aligned; overwritten; must not be shared
  *             by two calls in flight at once
  *   window    host pointer; NULL with hist NULL = no binning
- *   tuning    host pointer or NULL (params.block / ctas_per_sm for all groups)
+ *   tuning    host pointer or NULL (params.block / ctas_per_sm / lanes for every
+ *             degree); see rd_uneven_tuning
  * n < 2^32. Only enqueues kernels on `stream` (16 launches), so the whole
  * call can be captured in a CUDA graph. */
 typedef struct {
-    int32_t block[3];        /* threads per CTA for the degree-1..6, 7..9, 10..12 kernels (0 = default) */
-    int32_t ctas_per_sm[3];  /* resident CTAs per SM for each group (0 = occupancy maximum)     */
+    /* Launch shape of each degree bin's solve kernel, indexed by the degree
+     * (entries 1..12; entries 0 and 13..15 are ignored). 0 = the default.   */
+    int32_t block[16];        /* threads per CTA, a multiple of 32 in [32, 256]                  */
+    int32_t ctas_per_sm[16];  /* resident CTAs per SM (0 = the occupancy maximum)                 */
+    int32_t lanes[16];        /* lanes per polynomial, 1 or 2 (0 = params.lanes)                  */
 } rd_uneven_tuning;
 
 size_t rd_uneven_workspace_bytes(int64_t n, int64_t n_coeffs, rd_dtype dtype);
@@ -269,6 +276,46 @@ int rd_l2_approx(const double *samples, int64_t n, int nr, int nt, int degree, i
  * sub-disk), after scaling each sub-disk's samples by a power of two. */
 #define RD_L2_FP64 0
 #define RD_L2_DF 1
+
+/* ---- the whole path for an analytic f, one launch -----------------------------
+ * Sec. II: the region is covered by sub-disks; on each, f is approximated by a
+ * polynomial g (Sec. II-A, least squares on the disk, a_j = (j+1)/pi <g, w^j>
+ * in the local variable w, z = c + rho w), the roots of g are found (Sec.
+ * II-B/II-C) and a root is counted in the tile whose sub-disk produced it
+ * (each zero of f once). rd_field_density does all of it in one kernel: it
+ * evaluates f in FP64 at the 16 x 32 polar nodes of every tile's sub-disk
+ * (the rd_l2_nodes radii, theta_q = 2 pi q / 32), forms the coefficients with
+ * double-float sums (as RD_L2_DF), solves them (rd_roots_density, `mode`),
+ * keeps the roots that fall in their own tile and bins them. No sample array
+ * is read or written.
+ * Tiles: nx x ny over spec->tiles, tile t = iy * nx + ix from the top-left
+ * corner, centre (xmin + (ix + 1/2) w, ymax - (iy + 1/2) h), w = (xmax - xmin)
+ * / nx, h = (ymax - ymin) / ny, each product and sum rounded once.
+ *   f         RD_F_SIN_CUBE: f(z) = sin(z^3) + z/2; RD_F_POLY: f(z) = sum_k
+ *             poly[k] z^k, k <= poly_degree <= 12
+ *   spec      host pointer; nr must be 16 and degree 6
+ *   coeffs    device rd_c128 [degree+1][nx*ny] (local variable w) or NULL
+ *   roots     device rd_c128 [degree][nx*ny] (local variable w) or NULL
+ *   status    device uint8 [nx*ny] or NULL
+ *   hist      device uint32 [H][W] over window (accumulated, never cleared);
+ *             required
+ * params: as rd_roots_density; lanes must be 0 or 1 and polish_mode
+ * RD_POLISH_FP64. Errors: RD_EINVAL for a bad spec, window or pointer,
+ * RD_EUNSUPPORTED for another nr or degree. */
+typedef enum { RD_F_SIN_CUBE = 0, RD_F_POLY = 1 } rd_field;
+typedef struct {
+    rd_window tiles;        /* the tiled region                                     */
+    int32_t nx, ny;         /* tile grid, nx * ny < 2^31                            */
+    double radius;          /* sub-disk radius; <= 0: half the tile diagonal        */
+    int32_t nr;             /* radial nodes: 16                                     */
+    int32_t degree;         /* degree of g: 6                                       */
+    int32_t poly_degree;    /* RD_F_POLY: degree of f, 0..12                        */
+    int32_t reserved;       /* must be 0                                            */
+    double poly[26];        /* RD_F_POLY: c_0 .. c_12 as (re, im) pairs             */
+} rd_field_spec;
+int rd_field_density(rd_field f, const rd_field_spec *spec, rd_mode mode, const rd_params *params,
+                     rd_window window, int W, int H, uint32_t *hist, double *coeffs, double *roots,
+                     uint8_t *status, rd_stats *stats, void *stream);
 
 #ifdef __cplusplus
 }

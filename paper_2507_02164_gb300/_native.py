@@ -26,7 +26,7 @@ class Params(ctypes.Structure):
                 ("residual_tol", ctypes.c_double), ("collapse_tol", ctypes.c_double),
                 ("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("polish_extra", ctypes.c_int32), ("fixed_sweeps", ctypes.c_int32),
-                ("polish_mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("polish_mode", ctypes.c_int32), ("lanes", ctypes.c_int32)]
 
 
 class Window(ctypes.Structure):
@@ -40,8 +40,17 @@ class Clip(ctypes.Structure):
 
 
 class UnevenTuning(ctypes.Structure):
-    _fields_ = [("block", ctypes.c_int32 * 3), ("ctas_per_sm", ctypes.c_int32 * 3)]
+    # indexed by degree (1..12 used)
+    _fields_ = [("block", ctypes.c_int32 * 16), ("ctas_per_sm", ctypes.c_int32 * 16), ("lanes", ctypes.c_int32 * 16)]
 
+
+class FieldSpec(ctypes.Structure):
+    _fields_ = [("tiles", Window), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("radius", ctypes.c_double),
+                ("nr", ctypes.c_int32), ("degree", ctypes.c_int32), ("poly_degree", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("poly", ctypes.c_double * 26)]
+
+
+F_SIN_CUBE, F_POLY = 0, 1
 
 STATS_FIELDS = ("polys", "status_ok", "status_not_converged", "status_rejected", "status_degenerate",
                 "sweeps", "pair_updates", "rotations", "newton_steps", "binned", "out_of_window", "clipped",
@@ -69,6 +78,8 @@ SIGNATURES = {
                                      ctypes.POINTER(UnevenTuning), ctypes.POINTER(Window), I32, I32, P, P, P, P, P]),
     "rd_l2_nodes": (I32, [I32, P, P]),
     "rd_l2_approx": (I32, [P, I64, I32, I32, I32, I32, P, P]),
+    "rd_field_density": (I32, [I32, ctypes.POINTER(FieldSpec), I32, ctypes.POINTER(Params), Window, I32, I32, P, P,
+                               P, P, P, P]),
 }
 
 _lock = threading.Lock()

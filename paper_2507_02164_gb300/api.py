@@ -156,11 +156,14 @@ def new_uneven_workspace(n: int, n_coeffs: int, dtype=torch.complex64, device="c
     return torch.empty(uneven_workspace_bytes(n, n_coeffs, dtype), dtype=torch.uint8, device=device)
 
 
-def uneven_tuning(block=(0, 0, 0), ctas_per_sm=(0, 0, 0)) -> N.UnevenTuning:
+def uneven_tuning(block=None, ctas_per_sm=None, lanes=None) -> N.UnevenTuning:
+    """rd_uneven_tuning from {degree: value} dicts (missing degrees: defaults)."""
     t = N.UnevenTuning()
-    for g in range(3):
-        t.block[g] = int(block[g])
-        t.ctas_per_sm[g] = int(ctas_per_sm[g])
+    for arr, vals in ((t.block, block), (t.ctas_per_sm, ctas_per_sm), (t.lanes, lanes)):
+        for d, v in (vals or {}).items():
+            if not 1 <= int(d) <= 12:
+                raise ValueError(f"tuning degree {d} outside 1..12")
+            arr[int(d)] = int(v)
     return t
 
 
@@ -259,3 +262,38 @@ class RootsFn(torch.autograd.Function):
 def roots(coeffs: torch.Tensor, mode="mixed"):
     """Differentiable roots: (roots [d, n] complex128, status [n] uint8)."""
     return RootsFn.apply(coeffs, mode)
+
+
+def field_spec(tiles: Window, nx: int, ny: int, radius: float = 0.0, poly=None, degree: int = 6,
+               nr: int = 16) -> N.FieldSpec:
+    """rd_field_spec: nx x ny tiles over `tiles`; `poly` (c_0..c_k, k <= 12) for
+    f = RD_F_POLY; radius <= 0 means half the tile diagonal."""
+    sp = N.FieldSpec()
+    sp.tiles = tiles.c()
+    sp.nx, sp.ny, sp.radius, sp.nr, sp.degree = nx, ny, float(radius), nr, degree
+    if poly is not None:
+        c = [complex(v) for v in poly]
+        if not 1 <= len(c) <= 13:
+            raise ValueError("poly needs 1..13 coefficients")
+        sp.poly_degree = len(c) - 1
+        for k, v in enumerate(c):
+            sp.poly[2 * k], sp.poly[2 * k + 1] = v.real, v.imag
+    return sp
+
+
+def field_density(spec: N.FieldSpec, window: Window, hist: torch.Tensor, f: str = "sin_cube", mode="mixed",
+                  params_=None, coeffs=None, roots=None, status=None, stats=None, stream=None):
+    """The whole path for f in one launch: f at the 16 x 32 nodes of every
+    tile's sub-disk, L2 coefficients, roots, own-tile clip, histogram
+    (accumulated into hist [H, W]). Optional outputs: coeffs [7, nx*ny],
+    roots [6, nx*ny] (complex128, local variable w), status [nx*ny] uint8."""
+    _check_cuda("hist", hist)
+    for name, t in (("coeffs", coeffs), ("roots", roots)):
+        if t is not None:
+            _check_cuda(name, t, torch.complex128)
+    H, W = hist.shape
+    func = {"sin_cube": N.F_SIN_CUBE, "poly": N.F_POLY}[f]
+    p = params_ if params_ is not None else params(mode)
+    N.call("rd_field_density", func, ctypes.byref(spec), _mode(mode), ctypes.byref(p), window.c(), W, H,
+           _ptr(hist), _ptr(coeffs), _ptr(roots), _ptr(status), _ptr(stats), _stream(stream))
+    return hist

@@ -1,13 +1,13 @@
 """Launch-shape autotuner for the solve kernels.
 
-For each degree the candidates are a threads-per-CTA size (64, 128, 256) and
-a number of resident CTAs per SM (the occupancy maximum, or fewer). Each
-candidate solves a probe batch of complex-Gaussian polynomials through the C
-ABI (rd_roots_density, the fused path the benchmarks time) and is timed with
-CUDA events; the fastest wins. The uneven-degree path takes one shape per
-degree group (1-6, 7-9, 10-12): the candidate with the smallest summed time
-over the group's degrees. Results are cached per GPU, mode and storage type in
-a JSON file, so a process tunes once.
+For each degree the candidates are the lanes per polynomial (one thread per
+matrix, or two lanes sharing it; degree >= 2), a threads-per-CTA size (64,
+128, 256) and a number of resident CTAs per SM (the occupancy maximum, or
+fewer). Each candidate solves a probe batch of complex-Gaussian polynomials
+through the C ABI (rd_roots_density, the fused path the benchmarks time) and
+is timed with CUDA events; the fastest wins. The uneven-degree path launches
+one kernel per degree bin and takes each degree's own winner. Results are
+cached per GPU, mode and storage type in a JSON file, so a process tunes once.
 """
 from __future__ import annotations
 
@@ -20,7 +20,7 @@ import torch
 from . import api, workloads as WL
 
 BLOCKS = (64, 128, 256)
-GROUPS = ((1, 6), (7, 9), (10, 12))
+CACHE_FORMAT = 2  # table rows [lanes, block, ctas_per_sm, ms]
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "rootdensity_tuning.json")
 
 
@@ -36,11 +36,15 @@ def _probe(degree: int, n: int, dtype, device):
     return torch.from_numpy(np.ascontiguousarray(co.T)).to(device=device, dtype=dtype)
 
 
-def time_shape(coeffs, mode: str, block: int, cps: int, reps: int = 3) -> float:
+def lane_candidates(degree: int):
+    return (1, 2) if degree >= 2 else (1,)
+
+
+def time_shape(coeffs, mode: str, block: int, cps: int, reps: int = 3, lanes: int = 1) -> float:
     """Median milliseconds of one fused solve + binning of `coeffs` with the given shape."""
     hist = api.new_hist(1920, 1080, coeffs.device)
     win = api.Window(-3.0, 3.0, -1.6875, 1.6875)
-    p = api.params(mode, block=block, ctas_per_sm=cps)
+    p = api.params(mode, block=block, ctas_per_sm=cps, lanes=lanes)
     api.roots_density(coeffs, win, hist, mode=mode, params_=p)  # warm-up (and launch check)
     times = []
     for _ in range(reps):
@@ -56,33 +60,22 @@ def time_shape(coeffs, mode: str, block: int, cps: int, reps: int = 3) -> float:
 
 
 def tune_degree(degree: int, mode: str = "mixed", dtype=torch.complex64, n: int = 1 << 18, device="cuda"):
-    """{(block, cps): ms} for one degree, and the best shape."""
+    """{(lanes, block, cps): ms} for one degree, and the best shape."""
     coeffs = _probe(degree, n, dtype, device)
     res = {}
-    for block in BLOCKS:
-        for cps in _occupancy_candidates(block):
-            try:
-                res[(block, cps)] = time_shape(coeffs, mode, block, cps)
-            except api.N.RootDensityError:
-                continue  # shape not launchable (registers)
-    best = min(res, key=res.get)
-    return res, best
+    for lanes in lane_candidates(degree):
+        for block in BLOCKS:
+            for cps in _occupancy_candidates(block):
+                try:
+                    res[(lanes, block, cps)] = time_shape(coeffs, mode, block, cps, lanes=lanes)
+                except api.N.RootDensityError:
+                    continue  # shape not launchable (registers)
+    return res, best_shape(res)
 
 
-def choose_groups(tables: dict) -> list:
-    """Per degree group, the shape with the least summed time over the group's
-    tuned degrees among the shapes every one of them could launch; [0, 0]
-    (library defaults) for a group without tuned degrees."""
-    groups = []
-    for lo, hi in GROUPS:
-        ds = [d for d in tables if lo <= d <= hi]
-        shapes = set.intersection(*(set(tables[d]) for d in ds)) if ds else set()
-        if shapes:
-            best = min(sorted(shapes), key=lambda sh: sum(tables[d][sh] for d in ds))
-            groups.append([best[0], best[1]])
-        else:
-            groups.append([0, 0])
-    return groups
+def best_shape(table: dict):
+    """The fastest (lanes, block, cps) of a table; ties go to the smaller tuple."""
+    return min(sorted(table), key=lambda sh: table[sh])
 
 
 def _key(mode: str, dtype) -> str:
@@ -102,9 +95,9 @@ def tune(mode: str = "mixed", dtype=torch.complex64, degrees=range(1, 13), n: in
          cache_path: str | None = DEFAULT_CACHE, force: bool = False) -> dict:
     """Tune every requested degree; degrees already in the cache (same GPU,
     mode, storage type and probe size) are not re-measured. Returns
-    {"degrees": {d: {"block", "ctas_per_sm", "ms", "table"}}, "groups":
-    [[block, cps] x 3], "seconds": time spent measuring}."""
-    key = f"{_key(mode, dtype)}|n={n}"
+    {"degrees": {d: {"lanes", "block", "ctas_per_sm", "ms", "table"}},
+    "seconds": time spent measuring, "probe_polys": n}."""
+    key = f"{_key(mode, dtype)}|n={n}|v{CACHE_FORMAT}"
     cache = load(cache_path) if cache_path else {}
     entry = cache.get(key, {}) if not force else {}
     t0 = time.perf_counter()
@@ -112,8 +105,8 @@ def tune(mode: str = "mixed", dtype=torch.complex64, degrees=range(1, 13), n: in
         if str(d) in entry:
             continue
         res, best = tune_degree(d, mode, dtype, n)
-        entry[str(d)] = {"block": best[0], "ctas_per_sm": best[1], "ms": res[best],
-                         "table": [[b, c, t] for (b, c), t in sorted(res.items())]}
+        entry[str(d)] = {"lanes": best[0], "block": best[1], "ctas_per_sm": best[2], "ms": res[best],
+                         "table": [[la, b, c, t] for (la, b, c), t in sorted(res.items())]}
     spent = time.perf_counter() - t0
     if cache_path:
         cache[key] = entry
@@ -122,18 +115,19 @@ def tune(mode: str = "mixed", dtype=torch.complex64, degrees=range(1, 13), n: in
         with open(tmp, "w") as f:
             json.dump(cache, f, indent=1)
         os.replace(tmp, cache_path)
-    tables = {int(d): {(b, c): t for b, c, t in entry[str(d)]["table"]} for d in degrees}
     per_deg = {str(d): entry[str(d)] for d in degrees}
-    return {"degrees": per_deg, "groups": choose_groups(tables), "seconds": spent, "probe_polys": n}
+    return {"degrees": per_deg, "seconds": spent, "probe_polys": n}
 
 
 def uneven_tuning(result: dict):
-    """rd_uneven_tuning from a tune() result."""
-    g = result["groups"]
-    return api.uneven_tuning(block=[x[0] for x in g], ctas_per_sm=[x[1] for x in g])
+    """rd_uneven_tuning (per degree) from a tune() result."""
+    deg = result["degrees"]
+    return api.uneven_tuning(block={int(d): e["block"] for d, e in deg.items()},
+                             ctas_per_sm={int(d): e["ctas_per_sm"] for d, e in deg.items()},
+                             lanes={int(d): e["lanes"] for d, e in deg.items()})
 
 
 def degree_params(result: dict, degree: int, mode: str = "mixed"):
     """rd_params for a uniform batch of `degree` from a tune() result."""
     e = result["degrees"][str(degree)]
-    return api.params(mode, block=e["block"], ctas_per_sm=e["ctas_per_sm"])
+    return api.params(mode, block=e["block"], ctas_per_sm=e["ctas_per_sm"], lanes=e["lanes"])

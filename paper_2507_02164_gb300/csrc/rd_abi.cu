@@ -13,6 +13,8 @@
 namespace rd {
 int launch_solve_mixed(int degree, rd_dtype dt, const SolveArgs &a, int block, int ctas_per_sm, cudaStream_t st);
 int launch_solve_plain(int degree, rd_dtype dt, const SolveArgs &a, int block, int ctas_per_sm, cudaStream_t st);
+int launch_solve2(int degree, rd_dtype dt, bool mixed, const SolveArgs &a, int block, int ctas_per_sm, cudaStream_t st);
+int lanes_for(int degree, bool mixed, int polish_mode, int requested);
 int launch_density(const double *roots, int64_t n, const Binner &bin, uint32_t *hist, rd_stats *stats,
                    cudaStream_t st);
 int launch_clear(uint32_t *p, int64_t words, cudaStream_t st);
@@ -21,9 +23,12 @@ int launch_backward(int degree, rd_dtype dt, const void *coeffs, const double *r
 int l2_nodes_host(int nr, double *r, double *w);
 size_t uneven_workspace_bytes(int64_t n, int64_t n_coeffs, rd_dtype dt);
 int launch_uneven(const SolveArgs &a, rd_dtype dt, const uint8_t *degrees, const int64_t *offsets, int64_t n,
-                  int64_t n_coeffs, bool mixed, void *ws, const int *block, const int *cps, cudaStream_t st);
+                  int64_t n_coeffs, bool mixed, void *ws, const int *block, const int *cps, const int *lanes,
+                  cudaStream_t st);
 int launch_l2(const double *samples, int64_t n, int nr, int degree, double *coeffs, int precision,
               cudaStream_t st);
+int launch_field(const SolveArgs &a, const rd_field_spec &spec, int func, double rho, bool mixed, double *coeffs,
+                 int ctas_per_sm, cudaStream_t st);
 }  // namespace rd
 
 static thread_local char g_err[512] = "";
@@ -97,7 +102,9 @@ int check_params(const rd_params &p)
     if (p.polish_extra < 0 || p.polish_extra > 16) return rd_set_error(RD_EINVAL, "params.polish_extra must be in [0, 16]");
     if (p.polish_mode != RD_POLISH_FP64 && p.polish_mode != RD_POLISH_DF)
         return rd_set_error(RD_EINVAL, "params.polish_mode must be RD_POLISH_FP64 or RD_POLISH_DF");
-    if (p.reserved != 0) return rd_set_error(RD_EINVAL, "params.reserved must be 0");
+    if (p.lanes < 0 || p.lanes > 2) return rd_set_error(RD_EINVAL, "params.lanes must be 0, 1 or 2");
+    if (p.lanes == 2 && p.polish_mode != RD_POLISH_FP64)
+        return rd_set_error(RD_EINVAL, "params.lanes = 2 needs polish_mode RD_POLISH_FP64");
     if (p.fixed_sweeps < 0 || p.fixed_sweeps > p.max_iters)
         return rd_set_error(RD_EINVAL, "params.fixed_sweeps must be in [0, max_iters]");
     return RD_OK;
@@ -173,6 +180,8 @@ int solve_common(const void *coeffs, rd_dtype dtype, int degree, int64_t n, rd_m
     if (n == 0) return RD_OK;
     int block = p.block ? p.block : 128;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (rd::lanes_for(degree, mode == RD_MIXED, p.polish_mode, p.lanes) == 2)
+        return rd::launch_solve2(degree, dtype, mode == RD_MIXED, a, block, p.ctas_per_sm, st);
     if (mode == RD_MIXED) return rd::launch_solve_mixed(degree, dtype, a, block, p.ctas_per_sm, st);
     return rd::launch_solve_plain(degree, dtype, a, block, p.ctas_per_sm, st);
 }
@@ -209,7 +218,7 @@ void rd_default_params(rd_mode mode, rd_params *out)
     out->polish_extra = 5;
     out->fixed_sweeps = 0;
     out->polish_mode = RD_POLISH_FP64;
-    out->reserved = 0;
+    out->lanes = 0;
 }
 
 int rd_roots_batched(const void *coeffs, rd_dtype dtype, int degree, int64_t n, rd_mode mode, const rd_params *params,
@@ -276,22 +285,28 @@ int rd_roots_uneven(const void *coeffs, rd_dtype dtype, const uint8_t *degrees, 
     if (!ws || !aligned(ws, 256)) return rd_set_error(RD_EINVAL, "workspace null or not 256-byte aligned");
     size_t need = rd::uneven_workspace_bytes(n, n_coeffs, dtype);
     if (ws_bytes < need) return rd_set_error(RD_EINVAL, "workspace too small: %zu < %zu bytes", ws_bytes, need);
-    int block[3], cps[3];
-    for (int g = 0; g < 3; ++g) {
-        block[g] = p.block ? p.block : 128;
-        cps[g] = p.ctas_per_sm;
-        if (tuning) {
-            if (tuning->block[g] != 0 && (tuning->block[g] < 32 || tuning->block[g] > 256 || tuning->block[g] % 32))
-                return rd_set_error(RD_EINVAL, "tuning.block[%d] must be 0 or a multiple of 32 in [32, 256]", g);
-            if (tuning->ctas_per_sm[g] < 0 || tuning->ctas_per_sm[g] > 64)
-                return rd_set_error(RD_EINVAL, "tuning.ctas_per_sm[%d] must be in [0, 64]", g);
-            if (tuning->block[g]) block[g] = tuning->block[g];
-            if (tuning->ctas_per_sm[g]) cps[g] = tuning->ctas_per_sm[g];
+    int block[16], cps[16], lanes[16];
+    for (int d = 0; d < 16; ++d) {
+        block[d] = p.block ? p.block : 128;
+        cps[d] = p.ctas_per_sm;
+        lanes[d] = p.lanes;
+        if (tuning && d >= 1 && d <= 12) {
+            if (tuning->block[d] != 0 && (tuning->block[d] < 32 || tuning->block[d] > 256 || tuning->block[d] % 32))
+                return rd_set_error(RD_EINVAL, "tuning.block[%d] must be 0 or a multiple of 32 in [32, 256]", d);
+            if (tuning->ctas_per_sm[d] < 0 || tuning->ctas_per_sm[d] > 64)
+                return rd_set_error(RD_EINVAL, "tuning.ctas_per_sm[%d] must be in [0, 64]", d);
+            if (tuning->lanes[d] < 0 || tuning->lanes[d] > 2)
+                return rd_set_error(RD_EINVAL, "tuning.lanes[%d] must be 0, 1 or 2", d);
+            if (tuning->lanes[d] == 2 && mode == RD_MIXED && p.polish_mode != RD_POLISH_FP64)
+                return rd_set_error(RD_EINVAL, "tuning.lanes[%d] = 2 needs polish_mode RD_POLISH_FP64", d);
+            if (tuning->block[d]) block[d] = tuning->block[d];
+            if (tuning->ctas_per_sm[d]) cps[d] = tuning->ctas_per_sm[d];
+            if (tuning->lanes[d]) lanes[d] = tuning->lanes[d];
         }
     }
     a.coeffs = coeffs;
     a.n = n;
-    return rd::launch_uneven(a, dtype, degrees, offsets, n, n_coeffs, mode == RD_MIXED, ws, block, cps,
+    return rd::launch_uneven(a, dtype, degrees, offsets, n, n_coeffs, mode == RD_MIXED, ws, block, cps, lanes,
                              reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -330,6 +345,44 @@ int rd_l2_approx(const double *samples, int64_t n, int nr, int nt, int degree, i
     if (!samples || !aligned(samples, 16) || !coeffs || !aligned(coeffs, 16))
         return rd_set_error(RD_EINVAL, "samples / coeffs null or misaligned");
     return rd::launch_l2(samples, n, nr, degree, coeffs, precision, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int rd_field_density(rd_field f, const rd_field_spec *spec, rd_mode mode, const rd_params *params,
+                     rd_window window, int W, int H, uint32_t *hist, double *coeffs, double *roots,
+                     uint8_t *status, rd_stats *stats, void *stream)
+{
+    if (f != RD_F_SIN_CUBE && f != RD_F_POLY) return rd_set_error(RD_EINVAL, "f must be RD_F_SIN_CUBE or RD_F_POLY");
+    if (!spec) return rd_set_error(RD_EINVAL, "spec is null");
+    const rd_field_spec &sp = *spec;
+    if (!window_ok(sp.tiles)) return rd_set_error(RD_EINVAL, "spec.tiles must be finite with xmin < xmax, ymin < ymax");
+    if (sp.nx < 1 || sp.ny < 1 || (int64_t)sp.nx * sp.ny >= ((int64_t)1 << 31))
+        return rd_set_error(RD_EINVAL, "spec.nx, spec.ny must be >= 1 with nx * ny < 2^31");
+    if (sp.nr != 16) return rd_set_error(RD_EUNSUPPORTED, "spec.nr must be 16");
+    if (sp.degree != 6) return rd_set_error(RD_EUNSUPPORTED, "spec.degree must be 6");
+    if (sp.reserved != 0) return rd_set_error(RD_EINVAL, "spec.reserved must be 0");
+    if (f == RD_F_POLY) {
+        if (sp.poly_degree < 0 || sp.poly_degree > 12) return rd_set_error(RD_EINVAL, "spec.poly_degree must be in 0..12");
+        for (int k = 0; k < 26; ++k)
+            if (!std::isfinite(sp.poly[k])) return rd_set_error(RD_EINVAL, "spec.poly must be finite");
+    }
+    if (!std::isfinite(sp.radius)) return rd_set_error(RD_EINVAL, "spec.radius must be finite");
+    const double tw = (sp.tiles.xmax - sp.tiles.xmin) / sp.nx, th = (sp.tiles.ymax - sp.tiles.ymin) / sp.ny;
+    const double rho = sp.radius > 0 ? sp.radius : 0.5 * std::hypot(tw, th);
+    if (!hist) return rd_set_error(RD_EINVAL, "hist is required");
+    if (coeffs && !aligned(coeffs, 16)) return rd_set_error(RD_EINVAL, "coeffs misaligned (16 B)");
+    rd::SolveArgs a;
+    rd_params p;
+    int rc = build_solve_args(RD_C128, sp.degree, mode, params, nullptr, &window, W, H, hist, roots, status, stats, a, p);
+    if (rc) return rc;
+    if (p.lanes == 2) return rd_set_error(RD_EINVAL, "params.lanes must be 0 or 1 here");
+    if (mode == RD_MIXED && p.polish_mode != RD_POLISH_FP64)
+        return rd_set_error(RD_EINVAL, "params.polish_mode must be RD_POLISH_FP64 here");
+    a.n = (int64_t)sp.nx * sp.ny;
+    a.clip_on = 1;
+    a.radius = rho;
+    a.tiles = make_binner(sp.tiles, sp.nx, sp.ny);
+    return rd::launch_field(a, sp, (int)f, rho, mode == RD_MIXED, coeffs, p.ctas_per_sm,
+                            reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

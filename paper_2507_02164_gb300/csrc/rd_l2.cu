@@ -167,30 +167,6 @@ struct L2TablesDF {
     float thi[L2_MAX_DEG + 1][L2_NT][2], tlo[L2_MAX_DEG + 1][L2_NT][2];
 };
 
-// Split d * 2^-shift into hi + lo floats (|d * 2^-shift| <= 2): hi = d's
-// significand rounded to 24 bits, lo = the rest rounded to 24 bits (relative
-// error 2^-48). Magnitudes below the FP32 normal range become zero.
-__device__ __forceinline__ dfl split_scaled(double d, int shift)
-{
-    unsigned long long b = (unsigned long long)__double_as_longlong(d);
-    unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-    int E = (int)((b >> 52) & 0x7ff);
-    unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);  // 53-bit significand
-    unsigned long long H = (M + (1ull << 28)) >> 29;                 // rounded to 24 bits (may be 2^24)
-    long long r = (long long)M - (long long)(H << 29);               // |r| <= 2^28, exact remainder
-    int e = E - 1023 - shift;                                         // unbiased exponent after scaling
-    // hi = H * 2^(e - 23): float bits, the carry of H = 2^24 moves into the exponent
-    unsigned hib = sign | (unsigned)((e + 127) << 23) + (unsigned)(H - (1ull << 23));
-    float hi = (e + 127 > 0 && E != 0) ? __uint_as_float(hib) : 0.0f;
-    // lo = r * 2^(e - 52)
-    float lo = __int2float_rn((int)r);
-    int le = e - 52 + 127;
-    lo = (le > 0 && E != 0) ? lo * __uint_as_float((unsigned)le << 23) : 0.0f;
-    lo = sign ? -lo : lo;
-    if (E == 0x7ff) return {__int_as_float(0x7fc00000), 0.0f};  // inf or NaN sample: NaN coefficients
-    return {hi, lo};
-}
-
 __global__ void __launch_bounds__(256) l2_kernel_df(const double2 *__restrict__ samples, int64_t n, int nr,
                                                     int degree, double2 *coeffs, const L2TablesDF T)
 {

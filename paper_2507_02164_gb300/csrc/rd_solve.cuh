@@ -95,6 +95,23 @@ struct InLoad<double2> {
     }
 };
 
+// Complex128 coefficients staged in shared memory by the kernel itself
+// (plain loads: the read-only path does not serve shared memory).
+struct SharedC128 {};
+template <>
+struct InLoad<SharedC128> {
+    __device__ static cx<double> ld(const void *p, int64_t idx)
+    {
+        double2 v = reinterpret_cast<const double2 *>(p)[idx];
+        return {v.x, v.y};
+    }
+    __device__ static cx<float> ldf(const void *p, int64_t idx)
+    {
+        double2 v = reinterpret_cast<const double2 *>(p)[idx];
+        return {(float)v.x, (float)v.y};
+    }
+};
+
 template <typename T>
 __device__ __forceinline__ bool finite_c(cx<T> z) { return isfinite(z.re) && isfinite(z.im); }
 
@@ -181,16 +198,26 @@ __device__ __forceinline__ cx<T> wilkinson(cx<T> a, cx<T> b, cx<T> c, cx<T> d)
     return sub(d, cdiv(bc, den));
 }
 
-// Where the results of local polynomial i of a solved batch go.
+// Where the results of local polynomial i of a solved batch go, and (for
+// the tile clip) the centre and tile of polynomial p, read from the caller's
+// arrays (A.centres, A.tile_index; no tile_index: tile p).
+struct ClipFromArrays {
+    __device__ static cx<double> centre(const SolveArgs &A, int64_t p)
+    {
+        double2 c = __ldg(reinterpret_cast<const double2 *>(A.centres) + p);
+        return {c.x, c.y};
+    }
+    __device__ static int64_t tile(const SolveArgs &A, int64_t p) { return A.tile_index ? __ldg(A.tile_index + p) : p; }
+};
 // Uniform batch: polynomial i itself, root j at j*n + i (coefficient-major).
-struct UniformMap {
+struct UniformMap : ClipFromArrays {
     int64_t n;
     __device__ int64_t poly(int64_t i) const { return i; }
     __device__ int64_t root(int64_t p, int j) const { return (int64_t)j * n + p; }
 };
 // Degree bin of a packed uneven batch: local slot i is polynomial perm[i];
 // its roots are packed like its coefficients without the leading one.
-struct PackedMap {
+struct PackedMap : ClipFromArrays {
     const uint32_t *perm;
     const int64_t *offsets;
     __device__ int64_t poly(int64_t i) const { return (int64_t)__ldg(perm + i); }
@@ -517,9 +544,8 @@ __device__ __forceinline__ void solve_warp(const SolveArgs &A, const void *coeff
         cx<double> cen = {0.0, 0.0};
         int64_t my_tile = pid;
         if (A.hist && A.clip_on && valid) {
-            double2 c = __ldg(reinterpret_cast<const double2 *>(A.centres) + pid);
-            cen = {c.x, c.y};
-            if (A.tile_index) my_tile = __ldg(A.tile_index + pid);
+            cen = map.centre(A, pid);
+            my_tile = map.tile(A, pid);
         }
         unsigned n_clipped = 0, n_binned = 0, n_oow = 0;
         double2 *R = reinterpret_cast<double2 *>(A.roots);
@@ -562,7 +588,7 @@ __global__ void __launch_bounds__(256, (MODE != MODE_PLAIN && N <= 6) ? 2 : 1) s
     const int64_t warp_id = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     __shared__ unsigned long long acc[ST_WORDS];
     const CtaStats S = stats_begin(acc, A.stats);
-    const UniformMap map{A.n};
+    const UniformMap map{{}, A.n};
     for (int64_t base = warp_id * 32; base < A.n; base += warps_total * 32)
         solve_warp<N, T, In, MODE>(A, A.coeffs, A.n, base, map, S);
     stats_end(S, A.stats);

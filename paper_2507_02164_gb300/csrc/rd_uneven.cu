@@ -14,7 +14,7 @@
 // no synchronisation): clear header -> count -> scan -> pack -> one
 // persistent solve kernel per degree, largest degree first, each with its
 // own register allocation and its own task queue.
-#include "rd_solve.cuh"
+#include "rd_solve2.cuh"
 
 namespace rd {
 
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256, (MODE != MODE_PLAIN && N <= 6) ? 2 : 1)
     const int lane = threadIdx.x & 31;
     const int64_t cnt = hdr->count[N];
     const unsigned tasks = (unsigned)((cnt + 31) / 32);
-    const PackedMap map{perm + hdr->poly_base[N], offsets};
+    const PackedMap map{{}, perm + hdr->poly_base[N], offsets};
     const void *base = bins + (size_t)hdr->coef_base[N] * sizeof(In);
     for (;;) {
         unsigned t = 0;
@@ -205,11 +205,35 @@ __global__ void __launch_bounds__(256, (MODE != MODE_PLAIN && N <= 6) ? 2 : 1)
     stats_end(S, A.stats);
 }
 
+// The same with two lanes per polynomial (rd_solve2.cuh): tasks of 16 slots.
 template <int N, typename In, int MODE>
-static int launch_degree_bin(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, int block,
-                             int ctas_per_sm, cudaStream_t st)
+__global__ void __maxnreg__(two_lane_regs(N, MODE))
+    uneven_solve2_kernel(SolveArgs A, UnevenHeader *hdr, const uint32_t *perm, const char *bins, const int64_t *offsets)
 {
-    auto kern = uneven_solve_kernel<N, In, MODE>;
+    using T = typename std::conditional<MODE != MODE_PLAIN, float, double>::type;
+    __shared__ unsigned long long acc[ST_WORDS];
+    const CtaStats S = stats_begin(acc, A.stats);
+    const int lane = threadIdx.x & 31;
+    const int64_t cnt = hdr->count[N];
+    const unsigned tasks = (unsigned)((cnt + 15) / 16);
+    const PackedMap map{{}, perm + hdr->poly_base[N], offsets};
+    const void *base = bins + (size_t)hdr->coef_base[N] * sizeof(In);
+    for (;;) {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(&hdr->head[N], 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= tasks) break;
+        solve_warp2<N, T, In, MODE>(A, base, cnt, (int64_t)t * 16, map, S);
+    }
+    stats_end(S, A.stats);
+}
+
+int lanes_for(int degree, bool mixed, int polish_mode, int requested);
+
+template <typename K>
+static int launch_persistent(K kern, const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, int block,
+                             int ctas_per_sm, cudaStream_t st, const char *what)
+{
     int per_sm = ctas_per_sm;
     if (per_sm <= 0) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0) != cudaSuccess || per_sm < 1)
@@ -217,19 +241,32 @@ static int launch_degree_bin(const SolveArgs &a, const UnevenLayout &L, const in
     }
     int grid = per_sm * rd_sm_count_cached();
     kern<<<grid, block, 0, st>>>(a, L.hdr, L.perm, L.bins, offsets);
-    return rd_check_launch("uneven_solve_kernel");
+    return rd_check_launch(what);
+}
+
+template <int N, typename In, int MODE>
+static int launch_degree_bin(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, int block,
+                             int ctas_per_sm, int lanes, cudaStream_t st)
+{
+    if constexpr (N >= 2 && MODE != MODE_MIXED_DF) {
+        if (lanes_for(N, MODE != MODE_PLAIN, a.polish_mode, lanes) == 2)
+            return launch_persistent(uneven_solve2_kernel<N, In, MODE>, a, L, offsets, block, ctas_per_sm, st,
+                                     "uneven_solve2_kernel");
+    }
+    return launch_persistent(uneven_solve_kernel<N, In, MODE>, a, L, offsets, block, ctas_per_sm, st,
+                             "uneven_solve_kernel");
 }
 
 // Degree bins largest first: the most expensive work starts first.
 template <typename In, int MODE>
 static int launch_bins(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, const int *block,
-                       const int *cps, cudaStream_t st)
+                       const int *cps, const int *lanes, cudaStream_t st)
 {
     int rc = 0;
-#define RD_BIN(D, G) \
-    if (!rc) rc = launch_degree_bin<D, In, MODE>(a, L, offsets, block[G], cps[G], st);
-    RD_BIN(12, 2) RD_BIN(11, 2) RD_BIN(10, 2) RD_BIN(9, 1) RD_BIN(8, 1) RD_BIN(7, 1)
-    RD_BIN(6, 0) RD_BIN(5, 0) RD_BIN(4, 0) RD_BIN(3, 0) RD_BIN(2, 0) RD_BIN(1, 0)
+#define RD_BIN(D) \
+    if (!rc) rc = launch_degree_bin<D, In, MODE>(a, L, offsets, block[D], cps[D], lanes[D], st);
+    RD_BIN(12) RD_BIN(11) RD_BIN(10) RD_BIN(9) RD_BIN(8) RD_BIN(7)
+    RD_BIN(6) RD_BIN(5) RD_BIN(4) RD_BIN(3) RD_BIN(2) RD_BIN(1)
 #undef RD_BIN
     return rc;
 }
@@ -240,7 +277,8 @@ size_t uneven_workspace_bytes(int64_t n, int64_t n_coeffs, rd_dtype dt)
 }
 
 int launch_uneven(const SolveArgs &a, rd_dtype dt, const uint8_t *degrees, const int64_t *offsets, int64_t n,
-                  int64_t n_coeffs, bool mixed, void *ws, const int *block, const int *cps, cudaStream_t st)
+                  int64_t n_coeffs, bool mixed, void *ws, const int *block, const int *cps, const int *lanes,
+                  cudaStream_t st)
 {
     UnevenLayout L = uneven_layout(ws, n);
     UnevenArgs U{degrees, offsets, n, n_coeffs};
@@ -264,13 +302,13 @@ int launch_uneven(const SolveArgs &a, rd_dtype dt, const uint8_t *degrees, const
     if ((rc = rd_check_launch("uneven_pack_kernel"))) return rc;
     const int mode = !mixed ? MODE_PLAIN : (a.polish_mode == RD_POLISH_DF ? MODE_MIXED_DF : MODE_MIXED_FP64);
     if (dt == RD_C64) {
-        if (mode == MODE_PLAIN) return launch_bins<float2, MODE_PLAIN>(a, L, offsets, block, cps, st);
-        if (mode == MODE_MIXED_DF) return launch_bins<float2, MODE_MIXED_DF>(a, L, offsets, block, cps, st);
-        return launch_bins<float2, MODE_MIXED_FP64>(a, L, offsets, block, cps, st);
+        if (mode == MODE_PLAIN) return launch_bins<float2, MODE_PLAIN>(a, L, offsets, block, cps, lanes, st);
+        if (mode == MODE_MIXED_DF) return launch_bins<float2, MODE_MIXED_DF>(a, L, offsets, block, cps, lanes, st);
+        return launch_bins<float2, MODE_MIXED_FP64>(a, L, offsets, block, cps, lanes, st);
     }
-    if (mode == MODE_PLAIN) return launch_bins<double2, MODE_PLAIN>(a, L, offsets, block, cps, st);
-    if (mode == MODE_MIXED_DF) return launch_bins<double2, MODE_MIXED_DF>(a, L, offsets, block, cps, st);
-    return launch_bins<double2, MODE_MIXED_FP64>(a, L, offsets, block, cps, st);
+    if (mode == MODE_PLAIN) return launch_bins<double2, MODE_PLAIN>(a, L, offsets, block, cps, lanes, st);
+    if (mode == MODE_MIXED_DF) return launch_bins<double2, MODE_MIXED_DF>(a, L, offsets, block, cps, lanes, st);
+    return launch_bins<double2, MODE_MIXED_FP64>(a, L, offsets, block, cps, lanes, st);
 }
 
 }  // namespace rd

@@ -40,6 +40,8 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(N.Params) == 64
     assert ctypes.sizeof(N.Window) == 32
     assert ctypes.sizeof(N.Clip) == 64
+    assert ctypes.sizeof(N.UnevenTuning) == 3 * 16 * 4
+    assert ctypes.sizeof(N.FieldSpec) == 32 + 8 + 8 + 16 + 26 * 8
     assert N.STATS_WORDS == 14
 
 
@@ -48,7 +50,7 @@ def test_default_params():
     assert p.tol == 1e-13 and p.max_iters == 40 and p.shift == N.SHIFT_WILKINSON
     q = N.default_params(N.MIXED)
     assert q.tol == 4 * 2.0 ** -24 and q.polish_steps == 3 and q.collapse_tol == 1e-9
-    assert q.polish_extra == 5 and q.fixed_sweeps == 0 and q.polish_mode == N.POLISH_FP64 and q.reserved == 0
+    assert q.polish_extra == 5 and q.fixed_sweeps == 0 and q.polish_mode == N.POLISH_FP64 and q.lanes == 0
 
 
 @pytest.mark.parametrize("nr", [1, 2, 7, 16, 32])
@@ -126,6 +128,60 @@ def test_argument_validation_without_gpu():
     assert L.rd_hist_clear(null, 0, null) == 0
     rc, _ = _err(L.rd_hist_clear(null, 5, null))
     assert rc == N.RD_EINVAL
+    # lanes per polynomial: 0, 1 or 2; two lanes only with the FP64 polish
+    bad = N.default_params(N.MIXED)
+    bad.lanes = 3
+    rc, msg = _err(L.rd_roots_batched(ctypes.c_void_p(64), N.C64, 6, 5, N.MIXED, ctypes.byref(bad), null, null,
+                                      null, null))
+    assert rc == N.RD_EINVAL and "lanes" in msg
+    bad.lanes, bad.polish_mode = 2, N.POLISH_DF
+    rc, msg = _err(L.rd_roots_batched(ctypes.c_void_p(64), N.C64, 6, 5, N.MIXED, ctypes.byref(bad), null, null,
+                                      null, null))
+    assert rc == N.RD_EINVAL and "lanes" in msg
+
+
+def test_field_density_argument_validation_without_gpu():
+    L = N.load()
+    null = ctypes.c_void_p(0)
+    p = N.default_params(N.MIXED)
+    w = N.Window(-1.0, 1.0, -1.0, 1.0)
+
+    def spec(**kw):
+        s = N.FieldSpec()
+        s.tiles = N.Window(-1.0, 1.0, -1.0, 1.0)
+        s.nx, s.ny, s.nr, s.degree = 8, 8, 16, 6
+        for k, v in kw.items():
+            setattr(s, k, v)
+        return s
+
+    def call(f, sp, params=p, hist=ctypes.c_void_p(64)):
+        return _err(L.rd_field_density(f, ctypes.byref(sp) if sp is not None else None, N.MIXED,
+                                       ctypes.byref(params), w, 16, 16, hist, null, null, null, null, null))
+
+    rc, msg = call(7, spec())
+    assert rc == N.RD_EINVAL and "RD_F_" in msg
+    rc, msg = call(N.F_SIN_CUBE, None)
+    assert rc == N.RD_EINVAL and "spec" in msg
+    rc, msg = call(N.F_SIN_CUBE, spec(nx=0))
+    assert rc == N.RD_EINVAL and "nx" in msg
+    rc, msg = call(N.F_SIN_CUBE, spec(tiles=N.Window(1.0, -1.0, -1.0, 1.0)))
+    assert rc == N.RD_EINVAL and "tiles" in msg
+    rc, msg = call(N.F_SIN_CUBE, spec(nr=8))
+    assert rc == N.RD_EUNSUPPORTED and "nr" in msg
+    rc, msg = call(N.F_SIN_CUBE, spec(degree=4))
+    assert rc == N.RD_EUNSUPPORTED and "degree" in msg
+    rc, msg = call(N.F_POLY, spec(poly_degree=13))
+    assert rc == N.RD_EINVAL and "poly_degree" in msg
+    sp = spec(poly_degree=2)
+    sp.poly[3] = float("inf")
+    rc, msg = call(N.F_POLY, sp)
+    assert rc == N.RD_EINVAL and "poly" in msg
+    rc, msg = call(N.F_SIN_CUBE, spec(), hist=null)
+    assert rc == N.RD_EINVAL and "hist" in msg
+    two = N.default_params(N.MIXED)
+    two.lanes = 2
+    rc, msg = call(N.F_SIN_CUBE, spec(), params=two)
+    assert rc == N.RD_EINVAL and "lanes" in msg
 
 
 def test_python_binding_raises_on_error():

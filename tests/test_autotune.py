@@ -4,22 +4,25 @@ import pytest
 from paper_2507_02164_gb300 import autotune
 
 
-def test_choose_groups_sums_over_each_group():
-    tables = {
-        2: {(64, 0): 1.0, (128, 0): 2.0},
-        6: {(64, 0): 5.0, (128, 0): 3.5},
-        8: {(128, 0): 7.0, (256, 1): 6.0},
-        12: {(256, 1): 9.0, (128, 0): 9.5},
-    }
-    g = autotune.choose_groups(tables)
-    # group 1-6: (64, 0) sums 1 + 5 = 6.0, (128, 0) sums 2 + 3.5 = 5.5 -> (128, 0)
-    assert g[0] == [128, 0]
-    assert g[1] == [256, 1]
-    assert g[2] == [256, 1]
+def test_best_shape_takes_the_fastest_with_a_stable_tie_break():
+    table = {(1, 128, 0): 2.0, (2, 64, 0): 1.5, (2, 256, 1): 1.5, (1, 64, 2): 3.0}
+    assert autotune.best_shape(table) == (2, 64, 0)
 
 
-def test_choose_groups_without_degrees_gives_defaults():
-    assert autotune.choose_groups({3: {(64, 2): 1.0}}) == [[64, 2], [0, 0], [0, 0]]
+def test_lane_candidates():
+    assert autotune.lane_candidates(1) == (1,)
+    assert autotune.lane_candidates(2) == (1, 2) and autotune.lane_candidates(12) == (1, 2)
+
+
+def test_uneven_tuning_is_per_degree():
+    res = {"degrees": {"3": {"lanes": 1, "block": 64, "ctas_per_sm": 2},
+                       "12": {"lanes": 2, "block": 128, "ctas_per_sm": 0}}}
+    t = autotune.uneven_tuning(res)
+    assert list(t.block)[3] == 64 and list(t.block)[12] == 128 and list(t.lanes)[12] == 2
+    assert list(t.ctas_per_sm)[3] == 2 and list(t.lanes)[3] == 1
+    assert sum(t.block) == 64 + 128  # other degrees left at the defaults
+    with pytest.raises(ValueError):
+        autotune.api.uneven_tuning(block={13: 64})
 
 
 @pytest.mark.gpu
@@ -34,4 +37,5 @@ def test_tune_two_degrees_on_gpu(tmp_path):
     more = autotune.tune("mixed", degrees=(3, 6, 9), n=1 << 14, cache_path=str(tmp_path / "t.json"))
     assert more["degrees"]["3"] == res["degrees"]["3"] and "9" in more["degrees"]
     again = autotune.tune("mixed", degrees=(3, 6, 9), n=1 << 14, cache_path=str(tmp_path / "t.json"))
-    assert again["degrees"] == more["degrees"] and again["groups"] == more["groups"]
+    assert again["degrees"] == more["degrees"]
+    assert {e["lanes"] for e in again["degrees"].values()} <= {1, 2}

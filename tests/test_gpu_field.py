@@ -1,0 +1,165 @@
+"""GPU parity of the one-launch path rd_field_density (f at the quadrature
+nodes -> L2 coefficients -> roots -> own-tile clip -> histogram).
+
+Pins: (1) a polynomial f of degree 6 is reproduced exactly by the L2 step
+(quadrature exactness), so g(w) = f(c + rho w) and the kept roots are exactly
+the zeros of f, each counted once; its coefficients are the Taylor
+coefficients rho^j f^(j)(c) / j!. (2) For f = sin(z^3) + z/2, the
+coefficients equal the oracle's L2 approximation of the same samples, the
+roots the oracle's roots of them, and the histogram the oracle's clip and
+binning of the GPU roots bit for bit; every kept root is a zero of f.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2507_02164_gb300 import api, workloads as WL
+from tests.gpu_common import compare_roots, hist_np, require_gpu, roots_poly_major
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return require_gpu()
+
+
+def _run(dev, spec, win, W, H, f="sin_cube", mode="mixed", **kw):
+    n = spec.nx * spec.ny
+    hist = api.new_hist(W, H, dev)
+    coeffs = torch.empty((7, n), dtype=torch.complex128, device=dev)
+    roots = torch.empty((6, n), dtype=torch.complex128, device=dev)
+    status = torch.empty(n, dtype=torch.uint8, device=dev)
+    stats = api.new_stats(dev)
+    api.field_density(spec, win, hist, f=f, mode=mode, params_=api.params(mode, **kw), coeffs=coeffs,
+                      roots=roots, status=status, stats=stats)
+    torch.cuda.synchronize()
+    return (hist_np(hist), coeffs.cpu().numpy().T, roots_poly_major(roots), status.cpu().numpy(),
+            api.stats_dict(stats))
+
+
+@pytest.mark.parametrize("mode", ["mixed", "plain"])
+def test_polynomial_field_finds_each_zero_once(dev, orc, mode):
+    """f = prod (z - z_k), 6 seeded zeros inside a 41 x 23 tile grid (ragged
+    over 32-tile groups), each at least 1e-3 from every tile and pixel edge."""
+    tiles = api.Window(-2.05, 2.05, -1.15, 1.15)
+    nx, ny = 41, 23
+    W, H = 410, 230  # 10 x 10 pixels per tile
+    g = np.random.default_rng(17)
+    zs = []
+    while len(zs) < 6:
+        # cell centres of the pixel grid, jittered by at most 0.3 pixel
+        ix, iy = g.integers(0, W), g.integers(0, H)
+        x = tiles.xmin + (ix + 0.5 + g.uniform(-0.3, 0.3)) * 0.01
+        y = tiles.ymax - (iy + 0.5 + g.uniform(-0.3, 0.3)) * 0.01
+        if all(abs(complex(x, y) - z) > 0.05 for z in zs):
+            zs.append(complex(x, y))
+    zs = np.array(zs)
+    poly = np.polynomial.polynomial.polyfromroots(zs)  # c_0 .. c_6, monic
+    centres, rho, _, _ = WL.tiles(tiles.xmin, tiles.xmax, tiles.ymin, tiles.ymax, nx, ny)
+    spec = api.field_spec(tiles, nx, ny, radius=rho, poly=poly)
+    h, co, r, st_, st = _run(dev, spec, tiles, W, H, f="poly", mode=mode)
+    # each zero counted exactly once, in its own pixel
+    h_true, oow = orc.hist(zs, tiles.tuple(), W, H)
+    assert oow == 0 and np.array_equal(h, h_true)
+    assert st["binned"] == 6 and st["polys"] == nx * ny
+    assert np.all(st_ == 0) or (st_ != 0).sum() <= 2
+    # coefficients: rho^j f^(j)(c) / j!, the exact expansion of f(c + rho w)
+    taylor = np.zeros((nx * ny, 7), complex)
+    for t, c in enumerate(centres):
+        shifted = np.polynomial.polynomial.polyval(c, np.polynomial.polynomial.polyder(poly, 0))
+        taylor[t, 0] = shifted
+        for j in range(1, 7):
+            taylor[t, j] = np.polynomial.polynomial.polyval(c, np.polynomial.polynomial.polyder(poly, j)) \
+                / math.factorial(j) * rho ** j
+    scale = np.abs(taylor).max(axis=1, keepdims=True)
+    assert (np.abs(co - taylor) / scale).max() <= 1e-12
+    # the kept roots, mapped back, are the zeros
+    z = orc.affine(r, centres, rho)
+    tx = np.floor((z.real - tiles.xmin) / (4.1 / nx)).astype(np.int64)
+    ty = np.floor((tiles.ymax - z.imag) / (2.3 / ny)).astype(np.int64)
+    own = (tx == (np.arange(nx * ny) % nx)[:, None]) & (ty == (np.arange(nx * ny) // nx)[:, None])
+    kept = np.sort_complex(z[own])
+    assert kept.size == 6
+    assert np.abs(kept - np.sort_complex(zs)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("mode", ["mixed", "plain"])
+def test_sin_cube_field_matches_oracle(dev, orc, mode):
+    """f = sin(z^3) + z/2 on a 97 x 53 grid over [-4,4] x [-2.25,2.25]."""
+    tiles = api.Window(-4.0, 4.0, -2.25, 2.25)
+    nx, ny = 97, 53
+    W, H = 1920, 1080
+    centres, rho, _, _ = WL.tiles(-4.0, 4.0, -2.25, 2.25, nx, ny)
+    spec = api.field_spec(tiles, nx, ny, radius=rho)
+    h, co, r, st_, st = _run(dev, spec, tiles, W, H, mode=mode)
+    samples = WL.f_sin_cube(centres[:, None] + rho * orc.l2_nodes(16, 32)[None, :])
+    co_ref = orc.l2_approx(samples)
+    scale = np.abs(co_ref).max(axis=1, keepdims=True)
+    assert (np.abs(co - co_ref) / scale).max() <= 1e-12
+    # roots against the oracle's roots of its own coefficients
+    r_ref, ref_st, _, _ = orc.solve(co_ref)
+    ok = (st_ == 0) & (ref_st == 0)
+    assert ok.mean() > 0.98, np.bincount(st_, minlength=4)
+    tol, kcap = (1e-9, 1e3) if mode == "mixed" else (1e-11, 100.0)
+    compare_roots(r[ok], r_ref[ok], co_ref[ok], orc, tol, kcap)
+    # histogram: the oracle's clip + binning of the GPU roots, bit for bit
+    z = orc.affine(r, centres, rho)
+    h_ref, oow, dropped = orc.hist_tiled(z, np.arange(nx * ny), nx, ny, tiles.tuple(), W, H)
+    assert np.array_equal(h, h_ref)
+    assert st["clipped"] == dropped and st["binned"] == int(h_ref.sum()) and st["polys"] == nx * ny
+    assert st["binned"] >= 20
+
+
+def test_full_grid_fused_equals_split_path(dev, orc):
+    """The 480 x 270 grid the benchmark renders: the fused histogram is the
+    oracle's clip + binning of the fused roots bit for bit, close to the split
+    path's (samples array -> rd_l2_approx -> rd_roots_density), and every kept
+    root is a zero of f (one Newton step on f moves it by < 1e-6)."""
+    win_t = (-4.0, 4.0, -2.25, 2.25)
+    tiles = api.Window(*win_t)
+    centres, rho, _, _ = WL.tiles(*win_t, 480, 270)
+    spec = api.field_spec(tiles, 480, 270, radius=rho)
+    h, co, r, st_, st = _run(dev, spec, tiles, 1920, 1080)
+    z = orc.affine(r, centres, rho)
+    h_ref, _, dropped = orc.hist_tiled(z, np.arange(centres.size), 480, 270, win_t)
+    assert np.array_equal(h, h_ref) and st["clipped"] == dropped
+    # the split path on the same tiles
+    c = torch.from_numpy(centres).to(dev)
+    w = api.l2_sample_points(16, 32, dev)
+    samples = WL.f_sin_cube(c[:, None] + rho * w[None, :]).contiguous()
+    coeffs = api.l2_approx(samples, 16, 32, 6, precision="df")
+    hist2 = api.new_hist(1920, 1080, dev)
+    api.roots_density(coeffs, tiles, hist2, mode="mixed", clip=api.make_clip(c, rho, 480, 270, tiles))
+    torch.cuda.synchronize()
+    h2 = hist_np(hist2)
+    scale = np.abs(co).max(axis=1, keepdims=True)
+    assert (np.abs(co - coeffs.cpu().numpy().T) / scale).max() <= 1e-12
+    assert np.abs(h.astype(np.int64) - h2).sum() <= 4 and abs(int(h.sum()) - int(h2.sum())) <= 2
+    zz = z.reshape(-1)
+    t = np.arange(centres.size)
+    tx = np.floor((zz.real + 4.0) * 60).astype(np.int64)
+    ty = np.floor((2.25 - zz.imag) * 60).astype(np.int64)
+    own = (tx == np.repeat(t % 480, 6)) & (ty == np.repeat(t // 480, 6))
+    k = zz[own & np.isfinite(zz)]
+    assert k.size == st["binned"] > 1000
+    step = np.abs(WL.f_sin_cube(k) / (3 * k ** 2 * np.cos(k ** 3) + 0.5))
+    assert np.all(step < 1e-6), step.max()
+
+
+def test_field_argument_errors(dev):
+    tiles = api.Window(-1.0, 1.0, -1.0, 1.0)
+    hist = api.new_hist(64, 64, dev)
+    for kw, msg in (({"nr": 8}, "nr"), ({"degree": 5}, "degree")):
+        spec = api.field_spec(tiles, 4, 4, **kw)
+        with pytest.raises(api.N.RootDensityError, match=msg):
+            api.field_density(spec, tiles, hist)
+    spec = api.field_spec(tiles, 4, 4)
+    with pytest.raises(api.N.RootDensityError, match="lanes"):
+        api.field_density(spec, tiles, hist, params_=api.params("mixed", lanes=2))
+    with pytest.raises(api.N.RootDensityError, match="polish_mode"):
+        api.field_density(spec, tiles, hist, params_=api.params("mixed", polish_mode="df"))

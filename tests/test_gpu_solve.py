@@ -109,12 +109,13 @@ def test_littlewood_subsample_matches_oracle(dev, orc, mode, tol, kcap):
 @pytest.mark.parametrize("degree", list(range(1, 13)))
 @pytest.mark.parametrize("mode", ["mixed", "plain"])
 @pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
-def test_every_degree_matches_oracle(dev, orc, degree, mode, dtype):
+@pytest.mark.parametrize("lanes", [1, 2])
+def test_every_degree_matches_oracle(dev, orc, degree, mode, dtype, lanes):
     n = 1000 + 37  # several warps and a ragged tail
     co = WL.gaussian(100 + degree, n, degree)
     if dtype == torch.complex64:
         co = co.astype(np.complex64).astype(np.complex128)  # the stored values
-    roots, status, _, st = _solve(to_soa(co, dev, dtype), mode)
+    roots, status, _, st = _solve(to_soa(co, dev, dtype), mode, lanes=lanes)
     ref, ref_status, _, _ = orc.solve(co, tol=1e-13)
     good = (status == 0) & (ref_status == 0)
     assert good.mean() > 0.99, np.bincount(status, minlength=4)
