@@ -427,8 +427,10 @@ __device__ __forceinline__ void solve_warp2(const SolveArgs &A, const void *coef
     } else {
         S.add(ST_F64, degenerate ? 0u : 4u * (unsigned)nmine);
     }
-    // the pair agrees on REJECTED
-    reject = reject || __shfl_xor_sync(0xffffffffu, reject ? 1 : 0, 1) != 0;
+    // the pair agrees on REJECTED (the shuffle runs in every lane: a
+    // short-circuit here would leave lanes out of a full-mask collective)
+    const int partner_reject = __shfl_xor_sync(0xffffffffu, reject ? 1 : 0, 1);
+    reject = reject || partner_reject != 0;
     if (reject && st == RD_STATUS_OK && !degenerate) st = RD_STATUS_REJECTED;
     if (degenerate) {
 #pragma unroll
