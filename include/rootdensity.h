@@ -277,6 +277,27 @@ int rd_l2_approx(const double *samples, int64_t n, int nr, int nt, int degree, i
 #define RD_L2_FP64 0
 #define RD_L2_DF 1
 
+/* ---- soft root density (the differentiation workload's loss) ------------------
+ * Not in the paper, which counts roots into pixels (Sec. III): a loss needs an
+ * image that moves smoothly with the roots. Pixel (iy, ix) of the W x H image
+ * has its centre at x = xmin + (ix + 1/2) px, y = ymax - (iy + 1/2) py
+ * (px = (xmax - xmin)/W, py = (ymax - ymin)/H, row 0 at ymax, as the
+ * histogram). rd_splat adds, for every root z_j,
+ *   img[iy*W + ix] += scale * max(0, exp(-r^2 / (2 sigma^2)) - exp(-9/2)),
+ * r the distance from z_j to the pixel centre in pixel units (zero beyond
+ * 3 sigma); a non-finite root adds nothing. FP64 atomic adds: repeated calls
+ * agree to rounding, not bit for bit.
+ *   roots       device rd_c128 [n]
+ *   img         device double [H][W], accumulated (the caller zeroes it)
+ *   0 < sigma <= 2 (the stencil is at most 13 x 13 pixels); W, H >= 1.
+ * rd_splat_backward writes grad_roots[j] = dL/dRe z_j + i dL/dIm z_j (PyTorch's
+ * gradient convention) of a loss L(img), given grad_img = dL/dimg (device
+ * double [H][W]); grad_roots: device rd_c128 [n], overwritten. */
+int rd_splat(const double *roots, int64_t n, rd_window window, int W, int H, double sigma, double scale,
+             double *img, void *stream);
+int rd_splat_backward(const double *roots, int64_t n, rd_window window, int W, int H, double sigma, double scale,
+                      const double *grad_img, double *grad_roots, void *stream);
+
 /* ---- the whole path for an analytic f, one launch -----------------------------
  * Sec. II: the region is covered by sub-disks; on each, f is approximated by a
  * polynomial g (Sec. II-A, least squares on the disk, a_j = (j+1)/pi <g, w^j>

@@ -71,6 +71,8 @@ def lib() -> ctypes.CDLL:
                 "or_l2_approx": (i32, [P, i64, i32, i32, i32, P, P, i32]),
                 "or_roots_backward": (None, [P, i64, i32, P, P, P, P]),
                 "or_root_condition": (None, [P, i64, i32, P, P]),
+                "or_splat": (None, [P, i64, f64, f64, f64, f64, i32, i32, f64, f64, P]),
+                "or_splat_grad": (None, [P, i64, f64, f64, f64, f64, i32, i32, f64, f64, P, P]),
                 "or_max_threads": (i32, []),
             }
             for name, (res, args) in sig.items():
@@ -240,6 +242,27 @@ def root_condition(coeffs, roots) -> np.ndarray:
     kappa = np.zeros((n, K - 1))
     lib().or_root_condition(_p(a), n, K - 1, _p(z), _p(kappa))
     return kappa
+
+
+def splat(roots, window, W: int = 256, H: int = 144, sigma: float = 1.5, scale: float = 1.0) -> np.ndarray:
+    """Soft root density image [H, W] (float64) of the complex roots (any shape)."""
+    z = _c128(roots).reshape(-1)
+    img = np.zeros((H, W), np.float64)
+    xmin, xmax, ymin, ymax = window
+    lib().or_splat(_p(z), z.size, xmin, xmax, ymin, ymax, W, H, sigma, scale, _p(img))
+    return img
+
+
+def splat_grad(roots, G, window, W: int = 256, H: int = 144, sigma: float = 1.5, scale: float = 1.0) -> np.ndarray:
+    """dL/dRe z + i dL/dIm z for every root (shape of roots) given G = dL/dimg [H, W]."""
+    z = _c128(roots)
+    flat = z.reshape(-1)
+    g = np.ascontiguousarray(G, dtype=np.float64)
+    assert g.shape == (H, W)
+    out = np.zeros(flat.size, np.complex128)
+    xmin, xmax, ymin, ymax = window
+    lib().or_splat_grad(_p(flat), flat.size, xmin, xmax, ymin, ymax, W, H, sigma, scale, _p(g), _p(out))
+    return out.reshape(z.shape)
 
 
 def max_threads() -> int:

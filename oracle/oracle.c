@@ -499,6 +499,82 @@ void or_roots_backward(const double *coef, int64_t n, int d, const double *roots
     }
 }
 
+/* ------------------------------------------------- soft root density (C4) */
+
+/* The differentiable stand-in for the histogram used by the differentiation
+ * workload (not in the paper): W x H pixel centres over the window, pixel
+ * (iy, ix) at x = xmin + (ix + 1/2) px, y = ymax - (iy + 1/2) py with
+ * px = (xmax - xmin)/W, py = (ymax - ymin)/H. A root at (x, y), in pixel
+ * units u = (x - xmin)/px, v = (ymax - y)/py, adds
+ *   w = max(0, exp(-r^2 / (2 sigma^2)) - exp(-9/2)),  r^2 = du^2 + dv^2,
+ *   du = u - (ix + 1/2), dv = v - (iy + 1/2),
+ * times `scale` to pixel (iy, ix); w reaches 0 at r = 3 sigma, so only the
+ * pixels whose centres lie within 3 sigma in both axes are visited. A root
+ * with a non-finite coordinate adds nothing. */
+static int splat_box(double u, double sigma, int n_pix, int *lo, int *hi)
+{
+    if (!isfinite(u)) return 0;
+    double a = ceil(u - 0.5 - 3.0 * sigma), b = floor(u - 0.5 + 3.0 * sigma);
+    if (a < 0.0) a = 0.0;
+    if (b > n_pix - 1.0) b = n_pix - 1.0;
+    if (a > b) return 0;
+    *lo = (int)a;
+    *hi = (int)b;
+    return 1;
+}
+
+void or_splat(const double *roots, int64_t n, double xmin, double xmax, double ymin, double ymax, int W, int H,
+              double sigma, double scale, double *img)
+{
+    const double px = (xmax - xmin) / W, py = (ymax - ymin) / H;
+    const double cut = exp(-4.5);
+    for (int64_t j = 0; j < n; ++j) {
+        const double u = (roots[2 * j] - xmin) / px;
+        const double v = (ymax - roots[2 * j + 1]) / py;
+        int x0, x1, y0, y1;
+        if (!splat_box(u, sigma, W, &x0, &x1) || !splat_box(v, sigma, H, &y0, &y1)) continue;
+        for (int iy = y0; iy <= y1; ++iy)
+            for (int ix = x0; ix <= x1; ++ix) {
+                const double du = u - (ix + 0.5);
+                const double dv = v - (iy + 0.5);
+                const double w = exp(-(du * du + dv * dv) / (2.0 * sigma * sigma)) - cut;
+                if (w > 0.0) img[(size_t)iy * W + ix] += scale * w;
+            }
+    }
+}
+
+/* Gradient of L(img) with respect to every root: given G = dL/dimg,
+ *   dL/du = scale sum_pix G dw/du,  dw/du = -(du / sigma^2) exp(-r^2/(2 sigma^2))
+ * where w > 0 (0 elsewhere), likewise for v; then x = xmin + px u and
+ * y = ymax - py v give grad[2j] = dL/dx = (dL/du) / px and
+ * grad[2j+1] = dL/dy = -(dL/dv) / py (PyTorch's convention for a complex
+ * root: dL/dRe + i dL/dIm). */
+void or_splat_grad(const double *roots, int64_t n, double xmin, double xmax, double ymin, double ymax, int W,
+                   int H, double sigma, double scale, const double *G, double *grad)
+{
+    const double px = (xmax - xmin) / W, py = (ymax - ymin) / H;
+    const double cut = exp(-4.5);
+    for (int64_t j = 0; j < n; ++j) {
+        const double u = (roots[2 * j] - xmin) / px, v = (ymax - roots[2 * j + 1]) / py;
+        double gu = 0.0, gv = 0.0;
+        int x0, x1, y0, y1;
+        if (splat_box(u, sigma, W, &x0, &x1) && splat_box(v, sigma, H, &y0, &y1)) {
+            for (int iy = y0; iy <= y1; ++iy)
+                for (int ix = x0; ix <= x1; ++ix) {
+                    const double du = u - (ix + 0.5), dv = v - (iy + 0.5);
+                    const double e = exp(-(du * du + dv * dv) / (2.0 * sigma * sigma));
+                    if (e - cut > 0.0) {
+                        const double g = G[(size_t)iy * W + ix];
+                        gu += g * (-du / (sigma * sigma)) * e;
+                        gv += g * (-dv / (sigma * sigma)) * e;
+                    }
+                }
+        }
+        grad[2 * j] = scale * gu / px;
+        grad[2 * j + 1] = -scale * gv / py;
+    }
+}
+
 void or_root_condition(const double *coef, int64_t n, int d, const double *roots, double *kappa)
 {
     for (int64_t i = 0; i < n; ++i) {

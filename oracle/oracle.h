@@ -94,6 +94,16 @@ void or_roots_backward(const double *coef, int64_t n, int d, const double *roots
 /* Condition number of each root: sum_k |a_k||z|^k / (max(1,|z|) |p'(z)|). */
 void or_root_condition(const double *coef, int64_t n, int d, const double *roots, double *kappa);
 
+/* Soft root density (differentiation workload): img[iy*W + ix] += scale *
+ * max(0, exp(-r^2/(2 sigma^2)) - exp(-9/2)) for every root, r the distance in
+ * pixels from the root to the centre of pixel (iy, ix) (row 0 at ymax). */
+void or_splat(const double *roots, int64_t n, double xmin, double xmax, double ymin, double ymax, int W, int H,
+              double sigma, double scale, double *img);
+
+/* dL/dRe z_j, dL/dIm z_j (interleaved) of L(img) for every root, given G = dL/dimg. */
+void or_splat_grad(const double *roots, int64_t n, double xmin, double xmax, double ymin, double ymax, int W,
+                   int H, double sigma, double scale, const double *G, double *grad);
+
 /* Number of OpenMP threads the batch calls use by default. */
 int or_max_threads(void);
 

@@ -78,6 +78,8 @@ SIGNATURES = {
                                      ctypes.POINTER(UnevenTuning), ctypes.POINTER(Window), I32, I32, P, P, P, P, P]),
     "rd_l2_nodes": (I32, [I32, P, P]),
     "rd_l2_approx": (I32, [P, I64, I32, I32, I32, I32, P, P]),
+    "rd_splat": (I32, [P, I64, Window, I32, I32, F64, F64, P, P]),
+    "rd_splat_backward": (I32, [P, I64, Window, I32, I32, F64, F64, P, P, P]),
     "rd_field_density": (I32, [I32, ctypes.POINTER(FieldSpec), I32, ctypes.POINTER(Params), Window, I32, I32, P, P,
                                P, P, P, P]),
 }

@@ -29,6 +29,10 @@ int launch_l2(const double *samples, int64_t n, int nr, int degree, double *coef
               cudaStream_t st);
 int launch_field(const SolveArgs &a, const rd_field_spec &spec, int func, double rho, bool mixed, double *coeffs,
                  int ctas_per_sm, cudaStream_t st);
+int launch_splat(const double *roots, int64_t n, const rd_window &w, int W, int H, double sigma, double scale,
+                 double *img, cudaStream_t st);
+int launch_splat_backward(const double *roots, int64_t n, const rd_window &w, int W, int H, double sigma,
+                          double scale, const double *G, double *grad, cudaStream_t st);
 }  // namespace rd
 
 static thread_local char g_err[512] = "";
@@ -345,6 +349,42 @@ int rd_l2_approx(const double *samples, int64_t n, int nr, int nt, int degree, i
     if (!samples || !aligned(samples, 16) || !coeffs || !aligned(coeffs, 16))
         return rd_set_error(RD_EINVAL, "samples / coeffs null or misaligned");
     return rd::launch_l2(samples, n, nr, degree, coeffs, precision, reinterpret_cast<cudaStream_t>(stream));
+}
+
+namespace {
+int check_splat(const double *roots, int64_t n, const rd_window &window, int W, int H, double sigma, double scale)
+{
+    if (n < 0) return rd_set_error(RD_EINVAL, "n < 0");
+    if (n > 0 && (!roots || !aligned(roots, 16))) return rd_set_error(RD_EINVAL, "roots null or misaligned (16 B)");
+    if (!window_ok(window)) return rd_set_error(RD_EINVAL, "window must be finite with xmin < xmax, ymin < ymax");
+    if (W < 1 || H < 1 || (int64_t)W * H > ((int64_t)1 << 31)) return rd_set_error(RD_EINVAL, "bad image size %d x %d", W, H);
+    if (!(sigma > 0.0 && sigma <= 2.0)) return rd_set_error(RD_EINVAL, "sigma must be in (0, 2]");
+    if (!std::isfinite(scale)) return rd_set_error(RD_EINVAL, "scale must be finite");
+    return RD_OK;
+}
+}  // namespace
+
+int rd_splat(const double *roots, int64_t n, rd_window window, int W, int H, double sigma, double scale, double *img,
+             void *stream)
+{
+    int rc = check_splat(roots, n, window, W, H, sigma, scale);
+    if (rc) return rc;
+    if (!img || !aligned(img, 8)) return rd_set_error(RD_EINVAL, "img null or misaligned");
+    if (n == 0) return RD_OK;
+    return rd::launch_splat(roots, n, window, W, H, sigma, scale, img, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int rd_splat_backward(const double *roots, int64_t n, rd_window window, int W, int H, double sigma, double scale,
+                      const double *grad_img, double *grad_roots, void *stream)
+{
+    int rc = check_splat(roots, n, window, W, H, sigma, scale);
+    if (rc) return rc;
+    if (!grad_img || !aligned(grad_img, 8)) return rd_set_error(RD_EINVAL, "grad_img null or misaligned");
+    if (n > 0 && (!grad_roots || !aligned(grad_roots, 16)))
+        return rd_set_error(RD_EINVAL, "grad_roots null or misaligned (16 B)");
+    if (n == 0) return RD_OK;
+    return rd::launch_splat_backward(roots, n, window, W, H, sigma, scale, grad_img, grad_roots,
+                                     reinterpret_cast<cudaStream_t>(stream));
 }
 
 int rd_field_density(rd_field f, const rd_field_spec *spec, rd_mode mode, const rd_params *params,

@@ -94,13 +94,15 @@ def test_soft_density_loss_gradients_on_1024_polynomials(dev, orc):
     degree-6 polynomials and T the splat of a second seeded batch (2^16
     polynomials). The gradient through RootsFn (GPU solve + adjoint kernel)
     equals the oracle's implicit gradient to 1e-12 and central finite
-    differences (h = 1e-6, FP64, oracle re-solves rematched) to 1e-6 for
-    every polynomial whose roots are separated by more than 1e-2."""
+    differences (h = 1e-6, FP64, oracle re-solves and the oracle's image,
+    rematched) to 1e-6 for every polynomial whose roots are separated by
+    more than 1e-2. The image and its pull-back run in the CUDA splat
+    kernels."""
     from paper_2507_02164_gb300 import splat as SP
     n = 1024
     co = WL.gaussian(4, n, 6)
     tgt, _, _, _ = orc.solve(WL.gaussian(5, 1 << 16, 6))
-    T = SP.splat(torch.from_numpy(tgt))
+    T = torch.from_numpy(orc.splat(tgt, SP.WINDOW, scale=1.0 / tgt.size))
     coeffs_t = to_soa(co, dev).requires_grad_(True)
     roots_t, status = api.roots(coeffs_t, "plain")
     L = SP.loss(roots_t, T.to(dev))
@@ -115,13 +117,12 @@ def test_soft_density_loss_gradients_on_1024_polynomials(dev, orc):
     assert (np.abs(grad - g_or) / scale).max() <= 1e-12
     # finite differences of the loss change caused by one polynomial
     N_roots = 6 * n
-    D0 = SP.splat(torch.from_numpy(z0), n_norm=N_roots).numpy()
+    D0 = orc.splat(z0, SP.WINDOW, scale=1.0 / N_roots)
     R0 = D0 - T.numpy()
 
     def dloss(i, zi_new):
         zi_old = z0[i]
-        dD = (SP.splat(torch.from_numpy(zi_new), n_norm=N_roots) -
-              SP.splat(torch.from_numpy(zi_old), n_norm=N_roots)).numpy()
+        dD = orc.splat(zi_new, SP.WINDOW, scale=1.0 / N_roots) - orc.splat(zi_old, SP.WINDOW, scale=1.0 / N_roots)
         return float((np.abs(zi_new) ** 2).sum() - (np.abs(zi_old) ** 2).sum() + (dD * (2 * R0 + dD)).sum())
 
     h = 1e-6

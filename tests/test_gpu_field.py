@@ -6,8 +6,9 @@ Pins: (1) a polynomial f of degree 6 is reproduced exactly by the L2 step
 the zeros of f, each counted once; its coefficients are the Taylor
 coefficients rho^j f^(j)(c) / j!. (2) For f = sin(z^3) + z/2, the
 coefficients equal the oracle's L2 approximation of the same samples, the
-roots the oracle's roots of them, and the histogram the oracle's clip and
-binning of the GPU roots bit for bit; every kept root is a zero of f.
+roots kept in their own tiles the oracle's kept roots of its coefficients,
+and the histogram the oracle's clip and binning of the GPU roots bit for
+bit; every kept root is a zero of f.
 """
 from __future__ import annotations
 
@@ -18,7 +19,7 @@ import pytest
 import torch
 
 from paper_2507_02164_gb300 import api, workloads as WL
-from tests.gpu_common import compare_roots, hist_np, require_gpu, roots_poly_major
+from tests.gpu_common import hist_np, require_gpu, roots_poly_major
 
 pytestmark = pytest.mark.gpu
 
@@ -88,6 +89,18 @@ def test_polynomial_field_finds_each_zero_once(dev, orc, mode):
     assert np.abs(kept - np.sort_complex(zs)).max() <= 1e-12
 
 
+def _kept(z, tiles, nx, ny):
+    """Roots z [tiles, d] (mapped to the plane) that lie in their own tile."""
+    tw = (tiles.xmax - tiles.xmin) / nx
+    th = (tiles.ymax - tiles.ymin) / ny
+    with np.errstate(invalid="ignore"):
+        tx = np.floor((z.real - tiles.xmin) / tw)
+        ty = np.floor((tiles.ymax - z.imag) / th)
+    t = np.arange(z.shape[0])[:, None]
+    own = (tx == t % nx) & (ty == t // nx)
+    return z[own & np.isfinite(z)]
+
+
 @pytest.mark.parametrize("mode", ["mixed", "plain"])
 def test_sin_cube_field_matches_oracle(dev, orc, mode):
     """f = sin(z^3) + z/2 on a 97 x 53 grid over [-4,4] x [-2.25,2.25]."""
@@ -101,18 +114,22 @@ def test_sin_cube_field_matches_oracle(dev, orc, mode):
     co_ref = orc.l2_approx(samples)
     scale = np.abs(co_ref).max(axis=1, keepdims=True)
     assert (np.abs(co - co_ref) / scale).max() <= 1e-12
-    # roots against the oracle's roots of its own coefficients
+    # the roots that count, those inside their own tile, against the oracle's
+    # kept roots of its own coefficients (the far roots of a degree-6 fit are
+    # set by its smallest coefficients and are not compared)
     r_ref, ref_st, _, _ = orc.solve(co_ref)
-    ok = (st_ == 0) & (ref_st == 0)
-    assert ok.mean() > 0.98, np.bincount(st_, minlength=4)
-    tol, kcap = (1e-9, 1e3) if mode == "mixed" else (1e-11, 100.0)
-    compare_roots(r[ok], r_ref[ok], co_ref[ok], orc, tol, kcap)
-    # histogram: the oracle's clip + binning of the GPU roots, bit for bit
+    assert (st_ == 0).mean() > 0.98, np.bincount(st_, minlength=4)
     z = orc.affine(r, centres, rho)
+    z_ref = orc.affine(r_ref, centres, rho)
+    k_gpu, k_ref = _kept(z, tiles, nx, ny), _kept(z_ref, tiles, nx, ny)
+    assert abs(k_gpu.size - k_ref.size) <= 2 and k_gpu.size >= 20
+    near = np.abs(k_gpu[:, None] - k_ref[None, :]).min(axis=1)
+    assert (near <= 1e-9).sum() >= k_gpu.size - 2, np.sort(near)[-4:]
+    # histogram: the oracle's clip + binning of the GPU roots, bit for bit
     h_ref, oow, dropped = orc.hist_tiled(z, np.arange(nx * ny), nx, ny, tiles.tuple(), W, H)
     assert np.array_equal(h, h_ref)
     assert st["clipped"] == dropped and st["binned"] == int(h_ref.sum()) and st["polys"] == nx * ny
-    assert st["binned"] >= 20
+    assert st["binned"] == k_gpu.size
 
 
 def test_full_grid_fused_equals_split_path(dev, orc):

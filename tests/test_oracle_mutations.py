@@ -39,6 +39,16 @@ MUTANTS = {
     "adjoint_not_conjugated": ("g[k] += conj(-zk / dp) * gz;", "g[k] += (-zk / dp) * gz;"),
     "adjoint_derivative_index": ("dp = dp * z + (double)k * ld(a + 2 * k);",
                                  "dp = dp * z + (double)(k - 1) * ld(a + 2 * k);"),
+    "splat_pixel_corner": ("const double du = u - (ix + 0.5);", "const double du = u - ix;"),
+    "splat_sigma_factor": ("const double w = exp(-(du * du + dv * dv) / (2.0 * sigma * sigma)) - cut;",
+                           "const double w = exp(-(du * du + dv * dv) / (sigma * sigma)) - cut;"),
+    "splat_no_cut": ("const double w = exp(-(du * du + dv * dv) / (2.0 * sigma * sigma)) - cut;",
+                     "const double w = exp(-(du * du + dv * dv) / (2.0 * sigma * sigma));"),
+    "splat_rows_flipped": ("const double v = (ymax - roots[2 * j + 1]) / py;",
+                           "const double v = (roots[2 * j + 1] - ymin) / py;"),
+    "splat_grad_sign": ("gv += g * (-dv / (sigma * sigma)) * e;", "gv += g * (dv / (sigma * sigma)) * e;"),
+    "splat_grad_scale": ("grad[2 * j] = scale * gu / px;", "grad[2 * j] = scale * gu * px;"),
+    "splat_grad_y_orientation": ("grad[2 * j + 1] = -scale * gv / py;", "grad[2 * j + 1] = scale * gv / py;"),
 }
 
 

@@ -507,3 +507,68 @@ def test_fixed_schedule_with_paper_settings_mostly_converges(orc):
     roots, status = orc.solve_fixed(co, T=20)
     ok20 = (matched_errors(roots, true_roots).max(axis=1) < 1e-6).mean()
     assert 0.85 < ok10 < 0.95 and ok20 > 0.995
+
+
+# --------------------------------- soft root density (differentiation workload)
+
+SPLAT_WIN = (-2.0, 2.0, -1.125, 1.125)  # 256 x 144 pixels of 1/64
+
+
+def test_splat_mass_averaged_over_subpixel_offsets_is_the_integral(orc):
+    """Averaged over a 16 x 16 grid of sub-pixel positions, the image mass of
+    one root equals the integral of the truncated bump over the plane
+    (Poisson summation): pi sigma^2 (2 - 11 e^{-9/2}) for the cut at 3 sigma."""
+    px = 4.0 / 256
+    tot = [orc.splat(np.array([(a + 0.5) / 16 * px + 1j * (b + 0.5) / 16 * px]), SPLAT_WIN).sum()
+           for a in range(16) for b in range(16)]
+    exact = math.pi * 1.5 ** 2 * (2.0 - 11.0 * math.exp(-4.5))
+    assert abs(np.mean(tot) / exact - 1.0) <= 3e-6
+
+
+def test_splat_of_a_root_at_a_pixel_centre_is_symmetric_and_peaks_there(orc):
+    """A root at the centre of pixel (iy, ix) (dyadic coordinates, exact in
+    pixel units): the image is symmetric under x and y reflection about that
+    pixel, peaks at 1 - e^{-9/2} there, and that pixel is the one the
+    histogram's binning (row 0 at ymax) assigns to the root."""
+    ix, iy = 100, 40
+    z = complex(-2.0 + (ix + 0.5) / 64, 1.125 - (iy + 0.5) / 64)
+    img = orc.splat(np.array([z]), SPLAT_WIN)
+    assert np.unravel_index(np.argmax(img), img.shape) == (iy, ix)
+    assert img[iy, ix] == 1.0 - math.exp(-4.5)
+    box = img[iy - 6:iy + 7, ix - 6:ix + 7]
+    assert np.array_equal(box, box[::-1, :]) and np.array_equal(box, box[:, ::-1])
+    assert np.array_equal(box, box.T)
+    rest = img.copy()
+    rest[iy - 6:iy + 7, ix - 6:ix + 7] = 0.0
+    assert not rest.any()  # nothing beyond 6 pixels
+    h, _ = orc.hist(np.array([z]), SPLAT_WIN, 256, 144)
+    assert h[iy, ix] == 1
+
+
+def test_splat_moves_with_the_root(orc):
+    """Shifting a root by exactly one pixel (dyadic steps) shifts its image by
+    one pixel, bit for bit; a NaN root or one 10 pixels outside adds nothing."""
+    z = complex(0.25 + 3.0 / 1024, -0.5 + 5.0 / 1024)
+    a = orc.splat(np.array([z]), SPLAT_WIN)
+    b = orc.splat(np.array([z + 1.0 / 64]), SPLAT_WIN)
+    c = orc.splat(np.array([z - 1j / 64]), SPLAT_WIN)
+    assert np.array_equal(a[:, :-1], b[:, 1:]) and np.array_equal(a[:-1, :], c[1:, :])
+    far = orc.splat(np.array([complex(np.nan, 0.0), 2.0 + 10.0 / 64 + 0j]), SPLAT_WIN)
+    assert not far.any()
+
+
+def test_splat_gradient_is_the_derivative_of_the_image(orc):
+    """dL/dRe z, dL/dIm z of L = sum G * img against central differences of
+    the oracle's own image (h = 1e-7), for 50 roots and a random G."""
+    g = rng(91)
+    z = g.uniform(-1.9, 1.9, 50) + 1j * g.uniform(-1.0, 1.0, 50)
+    G = g.standard_normal((144, 256))
+    grad = orc.splat_grad(z, G, SPLAT_WIN, scale=0.5)
+    h = 1e-7
+    for j in range(z.size):
+        fd = 0j
+        for unit in (1.0, 1j):
+            lp = (G * orc.splat(np.array([z[j] + h * unit]), SPLAT_WIN, scale=0.5)).sum()
+            lm = (G * orc.splat(np.array([z[j] - h * unit]), SPLAT_WIN, scale=0.5)).sum()
+            fd += unit * (lp - lm) / (2 * h)
+        assert abs(fd - grad[j]) <= 1e-6 * max(1.0, abs(grad[j])), (j, fd, grad[j])
