@@ -841,7 +841,8 @@ ADJOINT_METRIC = "deg-6 polys/s through forward roots + implicit-differentiation
 def run_adjoint(args, rank, world, local_rank):
     """2^20 complex-Gaussian degree-6 polynomials (seed 4): forward roots
     (mixed) and the adjoint for L = sum |z|^2 (grad_z = 2 z), timed
-    separately, for complex128 and complex64 coefficients."""
+    separately, for complex128 and complex64 coefficients; and the whole
+    soft-density loss step (roots, image, loss, pull-back, adjoint)."""
     import numpy as np
     import torch
 
@@ -849,10 +850,14 @@ def run_adjoint(args, rank, world, local_rank):
     build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    from paper_2507_02164_gb300 import splat as SP
     n = 1 << 20
     co = WL.gaussian(4, n, 6)
     out = {}
     stream = torch.cuda.current_stream()
+    # target image: the splat of a second seeded batch (2^16 polynomials)
+    tgt_co = torch.from_numpy(np.ascontiguousarray(WL.gaussian(5, 1 << 16, 6).T)).to(dev)
+    target = SP.splat(api.roots_batched(tgt_co, mode="mixed")[0])
     for name, dt in (("c128", torch.complex128), ("c64", torch.complex64)):
         coeffs = torch.from_numpy(np.ascontiguousarray(co.T)).to(dev).to(dt)
         roots = torch.empty((6, n), dtype=torch.complex128, device=dev)
@@ -870,6 +875,20 @@ def run_adjoint(args, rank, world, local_rank):
         out[name] = {"ms_per_step": ms / args.steps, "forward_ms": ev[0].elapsed_time(ev[1]),
                      "backward_ms": ev[1].elapsed_time(ev[2]), "value": n * args.steps / (ms * 1e-3),
                      "clocks": clk}
+
+        # the whole differentiation step through autograd: roots, soft-density
+        # image, loss, the image's pull-back (CUDA splat kernels) and the adjoint
+        co_g = coeffs.clone().requires_grad_(True)
+
+        def loss_step():
+            co_g.grad = None
+            z, _ = api.roots(co_g, "mixed")
+            L = SP.loss(z, target)
+            L.backward()
+
+        ms_l, _ = _timed(loss_step, args, dev, world, local_rank)
+        out[name]["loss_step_ms"] = ms_l / args.steps
+        out[name]["loss_step_value"] = n * args.steps / (ms_l * 1e-3)
     if rank != 0:
         return
     print(json.dumps({
@@ -877,7 +896,9 @@ def run_adjoint(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": out["c128"]["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 (c128) / f32 (c64)",
         "data": "synthetic: seeded complex-Gaussian degree-6 polynomials (SplitMix64 seed 4)",
-        "config": {"workload": "2^20 deg-6, forward mixed roots + adjoint of L = sum |z|^2",
+        "config": {"workload": "2^20 deg-6, forward mixed roots + adjoint of L = sum |z|^2; loss_step: "
+                               "L = sum |z|^2 + sum (D - T)^2 with D the 256x144 soft-density image "
+                               "(sigma 1.5 px) of the roots, forward and backward through autograd",
                    "l2_flush": "none (inputs 112 MB c128, 56 MB c64)", "parallelism": f"dp{world}"},
         "c128": out["c128"], "c64": out["c64"], "gpu_launches": 2 * args.steps, "clocks": out["c128"]["clocks"],
     }), flush=True)

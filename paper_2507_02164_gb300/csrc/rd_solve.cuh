@@ -115,6 +115,29 @@ struct InLoad<SharedC128> {
 template <typename T>
 __device__ __forceinline__ bool finite_c(cx<T> z) { return isfinite(z.re) && isfinite(z.im); }
 
+// Multiply complex128 coefficients by the power of two that brings the
+// largest exponent among them to 0 (clamped to 2^+-1000): exact, and it
+// changes neither the roots, nor the Newton iterates, nor the relative
+// residual test, but keeps the FP32 copies used for p'(z) and the residual
+// bound finite when coefficients lie beyond the FP32 range (an L2 fit of
+// sin(z^3) reaches 1e41). The exponents are read from the bits (integer ops).
+template <int K>
+__device__ __forceinline__ void scale_pow2(cx<double> (&a)[K])
+{
+    unsigned emax = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const unsigned er = ((unsigned)__double2hiint(a[k].re) >> 20) & 0x7ffu;
+        const unsigned ei = ((unsigned)__double2hiint(a[k].im) >> 20) & 0x7ffu;
+        emax = max(emax, max(er, ei));
+    }
+    int sh = (int)emax - 1023;
+    sh = sh > 1000 ? 1000 : (sh < -1000 ? -1000 : sh);
+    const double f = __longlong_as_double((long long)(1023 - sh) << 52);  // 2^-sh
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] = {a[k].re * f, a[k].im * f};
+}
+
 // One shifted QR sweep of size M (warp-uniform) on h; this lane's rotations
 // r >= m are the identity and its diagonal is shifted only for i < m.
 template <int N, typename T>
@@ -360,8 +383,12 @@ __device__ __forceinline__ void solve_warp(const SolveArgs &A, const void *coeff
                             ad[k] = f2d(af[k]);
                         } else {
                             ad[k] = InLoad<In>::ld(coeffs, (int64_t)k * n + i);
-                            af[k] = d2f(ad[k]);
                         }
+                    }
+                    if constexpr (!std::is_same<In, float2>::value) {
+                        scale_pow2(ad);
+#pragma unroll
+                        for (int k = 0; k <= N; ++k) af[k] = d2f(ad[k]);
                     }
                 } else {
 #pragma unroll

@@ -293,8 +293,12 @@ __device__ __forceinline__ void solve_warp2(const SolveArgs &A, const void *coef
                         ad[k] = f2d(af[k]);
                     } else {
                         ad[k] = InLoad<In>::ld(coeffs, (int64_t)k * n + i);
-                        af[k] = d2f(ad[k]);
                     }
+                }
+                if constexpr (!std::is_same<In, float2>::value) {
+                    scale_pow2(ad);  // FP32 copies finite beyond the FP32 range
+#pragma unroll
+                    for (int k = 0; k <= N; ++k) af[k] = d2f(ad[k]);
                 }
             } else {
 #pragma unroll

@@ -89,16 +89,19 @@ def test_polynomial_field_finds_each_zero_once(dev, orc, mode):
     assert np.abs(kept - np.sort_complex(zs)).max() <= 1e-12
 
 
-def _kept(z, tiles, nx, ny):
-    """Roots z [tiles, d] (mapped to the plane) that lie in their own tile."""
+def _kept(z, tiles, nx, ny, with_tiles=False):
+    """Roots z [tiles, d] (mapped to the plane) that lie in their own tile
+    (and, with_tiles, the tile of each)."""
     tw = (tiles.xmax - tiles.xmin) / nx
     th = (tiles.ymax - tiles.ymin) / ny
     with np.errstate(invalid="ignore"):
         tx = np.floor((z.real - tiles.xmin) / tw)
         ty = np.floor((tiles.ymax - z.imag) / th)
     t = np.arange(z.shape[0])[:, None]
-    own = (tx == t % nx) & (ty == t // nx)
-    return z[own & np.isfinite(z)]
+    own = (tx == t % nx) & (ty == t // nx) & np.isfinite(z)
+    if with_tiles:
+        return z[own], np.nonzero(own)[0]
+    return z[own]
 
 
 @pytest.mark.parametrize("mode", ["mixed", "plain"])
@@ -121,10 +124,22 @@ def test_sin_cube_field_matches_oracle(dev, orc, mode):
     assert (st_ == 0).mean() > 0.98, np.bincount(st_, minlength=4)
     z = orc.affine(r, centres, rho)
     z_ref = orc.affine(r_ref, centres, rho)
-    k_gpu, k_ref = _kept(z, tiles, nx, ny), _kept(z_ref, tiles, nx, ny)
+    k_gpu, t_gpu = _kept(z, tiles, nx, ny, with_tiles=True)
+    k_ref = _kept(z_ref, tiles, nx, ny)
     assert abs(k_gpu.size - k_ref.size) <= 2 and k_gpu.size >= 20
-    near = np.abs(k_gpu[:, None] - k_ref[None, :]).min(axis=1)
-    assert (near <= 1e-9).sum() >= k_gpu.size - 2, np.sort(near)[-4:]
+    # the two coefficient sets differ by delta (<= 1e-12 of a tile's largest
+    # coefficient, asserted above), which moves a root w of g by about
+    # delta * kappa_n, kappa_n = max|a| sum_k |w|^k / |g'(w)|: near the window
+    # corners |f| spans orders of magnitude over one sub-disk and kappa_n is large
+    delta = (np.abs(co - co_ref) / scale).max(axis=1)
+    w = (k_gpu - centres[t_gpu]) / rho
+    a = co_ref[t_gpu]
+    dg = sum(k * a[:, k] * w ** (k - 1) for k in range(1, 7))
+    kappa_n = scale[t_gpu, 0] * sum(np.abs(w) ** k for k in range(7)) / np.abs(dg)
+    near = np.abs(k_gpu[:, None] - k_ref[None, :]).min(axis=1) / rho
+    bound = 100 * np.maximum(delta[t_gpu], 1e-16) * kappa_n + 1e-12
+    assert (near <= bound).sum() >= k_gpu.size - 2, (near / bound).max()
+    assert (near <= 1e-9).mean() > 0.8
     # histogram: the oracle's clip + binning of the GPU roots, bit for bit
     h_ref, oow, dropped = orc.hist_tiled(z, np.arange(nx * ny), nx, ny, tiles.tuple(), W, H)
     assert np.array_equal(h, h_ref)
