@@ -73,10 +73,11 @@ typedef struct {
     int32_t fixed_sweeps;  /* 0: adaptive deflation (tol). T > 0: the paper's fixed schedule
                               (Alg. 2): exactly T sweeps per eigenvalue, no deflation test       */
     int32_t polish_mode;   /* RD_MIXED: rd_polish                                                */
-    int32_t lanes;         /* lanes per polynomial: 0 = chosen per degree and mode; 1 = one
-                              thread holds the whole matrix; 2 = two lanes share it (columns
-                              split by parity, rotations exchanged by warp shuffles; degree
-                              >= 2 and RD_POLISH_FP64 only, degree 1 always runs one lane)   */
+    int32_t lanes;         /* lanes per polynomial: 0 or 1 = one thread holds the whole matrix;
+                              2 = two lanes share it (columns split by parity, rotations
+                              exchanged by warp shuffles; degree >= 2 and RD_POLISH_FP64
+                              only, degree 1 always runs one lane). Two lanes measured
+                              slower on GB300 at degrees 6..12; the autotuner times both   */
 } rd_params;
 
 /* RD_POLISH_FP64: every Newton step evaluates p(z) by FP64 Horner.
@@ -289,7 +290,8 @@ int rd_l2_approx(const double *samples, int64_t n, int nr, int nt, int degree, i
  * agree to rounding, not bit for bit.
  *   roots       device rd_c128 [n]
  *   img         device double [H][W], accumulated (the caller zeroes it)
- *   0 < sigma <= 2 (the stencil is at most 13 x 13 pixels); W, H >= 1.
+ *   0 < sigma <= 2 (the stencil is at most 13 x 13 pixels); scale >= 0;
+ *   W, H >= 1.
  * rd_splat_backward writes grad_roots[j] = dL/dRe z_j + i dL/dIm z_j (PyTorch's
  * gradient convention) of a loss L(img), given grad_img = dL/dimg (device
  * double [H][W]); grad_roots: device rd_c128 [n], overwritten. */

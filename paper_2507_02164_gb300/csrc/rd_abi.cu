@@ -359,7 +359,7 @@ int check_splat(const double *roots, int64_t n, const rd_window &window, int W, 
     if (!window_ok(window)) return rd_set_error(RD_EINVAL, "window must be finite with xmin < xmax, ymin < ymax");
     if (W < 1 || H < 1 || (int64_t)W * H > ((int64_t)1 << 31)) return rd_set_error(RD_EINVAL, "bad image size %d x %d", W, H);
     if (!(sigma > 0.0 && sigma <= 2.0)) return rd_set_error(RD_EINVAL, "sigma must be in (0, 2]");
-    if (!std::isfinite(scale)) return rd_set_error(RD_EINVAL, "scale must be finite");
+    if (!(scale >= 0.0) || !std::isfinite(scale)) return rd_set_error(RD_EINVAL, "scale must be finite and >= 0");
     return RD_OK;
 }
 }  // namespace

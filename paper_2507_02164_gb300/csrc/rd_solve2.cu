@@ -6,16 +6,20 @@
 
 namespace rd {
 
-// Lanes per polynomial for params.lanes = 0. Two lanes halve the registers a
-// thread needs for the matrix, so the larger degrees run without spills and
-// with more resident warps; below the thresholds one thread per polynomial
-// is faster (no shuffles, the same registers for twice the polynomials).
+// Lanes per polynomial: params.lanes when set, else one. Measured on GB300
+// (2^20 complex-Gaussian polynomials per degree, best launch shape of each):
+// two lanes take 1.14-1.43x the time of one at degrees 6..12 with FP32 sweeps
+// and 1.33-1.69x with FP64 sweeps. The pair halves the registers per thread
+// but not the FP64-pipe work per polynomial: both lanes form every Givens
+// rotation (a warp instruction costs the pipe the same for any active mask),
+// and the shuffles and selects add issue slots. The autotuner still times
+// both layouts per degree.
 int lanes_for(int degree, bool mixed, int polish_mode, int requested)
 {
+    (void)mixed;
+    (void)polish_mode;
     if (degree < 2) return 1;
-    if (requested == 1 || requested == 2) return requested;
-    if (mixed && polish_mode != RD_POLISH_FP64) return 1;
-    return degree >= (mixed ? 9 : 7) ? 2 : 1;
+    return requested == 2 ? 2 : 1;
 }
 
 template <int N, typename In, int MODE>

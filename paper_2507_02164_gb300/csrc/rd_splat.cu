@@ -36,7 +36,7 @@ constexpr int SPLAT_K = 13;  // stencil width for sigma <= 2
 struct SplatGeom {
     double xmin, ymax, px, py;
     int W, H;
-    double sigma, inv_2s2, inv_s2, step, cut, scale;
+    double sigma, inv_2s2, inv_s2, step, cut, scale, cut_s;  // cut_s = cut * scale
 };
 
 // First pixel index and the count along one axis (<= SPLAT_K), and the 13
@@ -76,14 +76,18 @@ __global__ void __launch_bounds__(256) splat_kernel(const double2 *__restrict__ 
         const int nx = splat_axis(g, u, g.W, x0, ex, dx0);
         const int ny = nx ? splat_axis(g, v, g.H, y0, ey, dy0) : 0;
         if (!ny) continue;
+        // scale * (e(du) e(dv) - cut) = e(du) (scale e(dv)) - scale cut: one FMA
+        // per pixel; w > 0 is read off the sign and magnitude bits (an
+        // integer compare: FP64 compares issue to the FP64 pipe)
 #pragma unroll
         for (int ky = 0; ky < SPLAT_K; ++ky) {
             if (ky >= ny) break;
             double *row = img + (size_t)(y0 + ky) * g.W + x0;
+            const double eys = ey[ky] * g.scale;
 #pragma unroll
             for (int kx = 0; kx < SPLAT_K; ++kx) {
-                const double w = fma(ex[kx], ey[ky], -g.cut);
-                if (kx < nx && w > 0.0) atomicAdd(row + kx, g.scale * w);
+                const double w = fma(ex[kx], eys, -g.cut_s);
+                if (kx < nx && __double_as_longlong(w) > 0) atomicAdd(row + kx, w);
             }
         }
     }
@@ -102,6 +106,10 @@ __global__ void __launch_bounds__(256) splat_backward_kernel(const double2 *__re
         const int ny = nx ? splat_axis(g, v, g.H, y0, ey, dy0) : 0;
         double gu = 0.0, gv = 0.0;
         if (ny) {
+            double dx[SPLAT_K];  // du of each column
+#pragma unroll
+            for (int kx = 0; kx < SPLAT_K; ++kx) dx[kx] = dx0 - kx;
+            const long long cut_bits = __double_as_longlong(g.cut);
 #pragma unroll
             for (int ky = 0; ky < SPLAT_K; ++ky) {
                 if (ky >= ny) break;
@@ -111,9 +119,10 @@ __global__ void __launch_bounds__(256) splat_backward_kernel(const double2 *__re
 #pragma unroll
                 for (int kx = 0; kx < SPLAT_K; ++kx) {
                     const double e = ex[kx] * ey[ky];
-                    if (kx < nx && e > g.cut) {
+                    // e > cut for positive doubles, on the bits (integer pipe)
+                    if (kx < nx && __double_as_longlong(e) > cut_bits) {
                         const double ge = __ldg(row + kx) * e;
-                        su = fma(ge, dx0 - kx, su);
+                        su = fma(ge, dx[kx], su);
                         sv += ge;
                     }
                 }
@@ -142,6 +151,7 @@ static SplatGeom splat_geom(const rd_window &w, int W, int H, double sigma, doub
     g.step = std::exp(-1.0 / (sigma * sigma));
     g.cut = std::exp(-4.5);
     g.scale = scale;
+    g.cut_s = g.cut * scale;
     return g;
 }
 

@@ -38,6 +38,8 @@ def test_splat_argument_validation_without_gpu():
     assert rc == N.RD_EINVAL and "roots" in msg
     rc, msg = err(L.rd_splat(fake, 4, w, 256, 144, 1.5, 1.0, null, null))
     assert rc == N.RD_EINVAL and "img" in msg
+    rc, msg = err(L.rd_splat(fake, 4, w, 256, 144, 1.5, -1.0, fake, null))
+    assert rc == N.RD_EINVAL and "scale" in msg
     rc, msg = err(L.rd_splat(fake, -1, w, 256, 144, 1.5, 1.0, fake, null))
     assert rc == N.RD_EINVAL
     assert L.rd_splat(null, 0, w, 256, 144, 1.5, 1.0, fake, null) == 0  # nothing to do
