@@ -787,6 +787,7 @@ def run_pipeline(args, rank, world, local_rank):
     ms_fused, clk_fused = _timed(fused_step, args, dev, world, local_rank)
     fused_kernel_ms = e_f[0].elapsed_time(e_f[1])
     st_fused = api.stats_dict(stats)
+    frames = render_frames(api, torch, dev, stream)
 
     # the FP64 L2 sums (RD_L2_FP64), for reference
     ms_fp64, _ = _timed(make_step("fp64"), args, dev, world, local_rank)
@@ -826,6 +827,7 @@ def run_pipeline(args, rank, world, local_rank):
                   "note": "rd_field_density: f evaluated in FP64 at the 16x32 nodes inside the kernel, L2, roots, "
                           "clip and histogram in one launch; no 1.06 GB sample array",
                   "clocks": clk_fused},
+        "frames": frames,
         "split_end_to_end": {"sampling_ms": sampling_ms, "l2_plus_roots_ms": ms / args.steps,
                              "value": n / ((sampling_ms + ms / args.steps) * 1e-3),
                              "note": "torch evaluates f at every node into a 1.06 GB array, then the timed step"},
@@ -833,6 +835,52 @@ def run_pipeline(args, rank, world, local_rank):
         "status": {k: st[k] for k in ("status_ok", "status_not_converged", "status_rejected", "status_degenerate")},
         "gpu_launches": 4 * args.steps, "clocks": clk,
     }), flush=True)
+
+
+def render_frames(api, torch, dev, stream, n_frames=60):
+    """A zoom sequence of 1920x1080 root-density frames of sin(z^3) + z/2,
+    each from 480x270 sub-disks with the one-launch path; frame f is copied
+    to pinned host memory on a second stream while frame f+1 renders (two
+    device and two host buffers): the headless counterpart of the paper's
+    60 Hz display. Returns frames/s over the whole sequence, copies included."""
+    import time
+    copy_stream = torch.cuda.Stream(device=dev)
+    hists = [api.new_hist(W_PIX, H_PIX, dev) for _ in range(2)]
+    host = [torch.empty((H_PIX, W_PIX), dtype=torch.int32, pin_memory=True) for _ in range(2)]
+    rendered = [torch.cuda.Event() for _ in range(2)]
+    copied = [torch.cuda.Event() for _ in range(2)]
+    target, zoom = complex(1.2, 0.4), 0.97
+
+    def window(f):
+        s = zoom ** f
+        return api.Window(target.real - 4.0 * s, target.real + 4.0 * s, target.imag - 2.25 * s,
+                          target.imag + 2.25 * s)
+
+    def render(f):
+        b = f % 2
+        stream.wait_event(copied[b])  # the copy of frame f-2 out of this buffer is done
+        api.hist_clear(hists[b])
+        w = window(f)
+        api.field_density(api.field_spec(w, 480, 270), w, hists[b], mode="mixed")
+        rendered[b].record(stream)
+        copy_stream.wait_event(rendered[b])
+        with torch.cuda.stream(copy_stream):
+            host[b].copy_(hists[b], non_blocking=True)
+        copied[b].record(copy_stream)
+
+    for f in range(3):
+        render(f)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for f in range(n_frames):
+        render(f)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    return {"frames": n_frames, "fps": n_frames / sec, "ms_per_frame": 1e3 * sec / n_frames,
+            "d2h_bytes_per_frame": W_PIX * H_PIX * 4, "sub_disks_per_frame": 480 * 270,
+            "zoom": f"window 8 x 4.5 around {target}, scaled by {zoom} per frame",
+            "last_frame_roots": int(host[(n_frames - 1) % 2].sum()),
+            "note": "host wall clock over the sequence; frame f's copy to pinned memory overlaps frame f+1"}
 
 
 ADJOINT_METRIC = "deg-6 polys/s through forward roots + implicit-differentiation adjoint"

@@ -4,7 +4,8 @@ nodes -> L2 coefficients -> roots -> own-tile clip -> histogram).
 Pins: (1) a polynomial f of degree 6 is reproduced exactly by the L2 step
 (quadrature exactness), so g(w) = f(c + rho w) and the kept roots are exactly
 the zeros of f, each counted once; its coefficients are the Taylor
-coefficients rho^j f^(j)(c) / j!. (2) For f = sin(z^3) + z/2, the
+coefficients rho^j f^(j)(c) / j!. (2) For f = sin(z^3) + z/2 on the
+benchmark's tile size (where the degree-6 fit resolves f), the
 coefficients equal the oracle's L2 approximation of the same samples, the
 roots kept in their own tiles the oracle's kept roots of its coefficients,
 and the histogram the oracle's clip and binning of the GPU roots bit for
@@ -106,11 +107,14 @@ def _kept(z, tiles, nx, ny, with_tiles=False):
 
 @pytest.mark.parametrize("mode", ["mixed", "plain"])
 def test_sin_cube_field_matches_oracle(dev, orc, mode):
-    """f = sin(z^3) + z/2 on a 97 x 53 grid over [-4,4] x [-2.25,2.25]."""
-    tiles = api.Window(-4.0, 4.0, -2.25, 2.25)
-    nx, ny = 97, 53
-    W, H = 1920, 1080
-    centres, rho, _, _ = WL.tiles(-4.0, 4.0, -2.25, 2.25, nx, ny)
+    """f = sin(z^3) + z/2 with the benchmark's tiles of 1/60 on [2, 4] x
+    [-0.5, 0.5] shifted by half a tile (7,200 tiles, ragged over 32-tile
+    groups; y = 0 mid-tile): 18 zeros, none within 8e-5 of a tile edge (the
+    oracle's own pipeline)."""
+    tiles = api.Window(2.0, 4.0, -0.5 + 1 / 120, 0.5 + 1 / 120)
+    nx, ny = 120, 60
+    W, H = 480, 240  # pixels of 1/240, as the 1920 x 1080 image of [-4,4] x [-2.25,2.25]
+    centres, rho, _, _ = WL.tiles(*tiles.tuple(), nx, ny)
     spec = api.field_spec(tiles, nx, ny, radius=rho)
     h, co, r, st_, st = _run(dev, spec, tiles, W, H, mode=mode)
     samples = WL.f_sin_cube(centres[:, None] + rho * orc.l2_nodes(16, 32)[None, :])
@@ -118,33 +122,20 @@ def test_sin_cube_field_matches_oracle(dev, orc, mode):
     scale = np.abs(co_ref).max(axis=1, keepdims=True)
     assert (np.abs(co - co_ref) / scale).max() <= 1e-12
     # the roots that count, those inside their own tile, against the oracle's
-    # kept roots of its own coefficients (the far roots of a degree-6 fit are
-    # set by its smallest coefficients and are not compared)
+    # kept roots of its own coefficients
     r_ref, ref_st, _, _ = orc.solve(co_ref)
-    assert (st_ == 0).mean() > 0.98, np.bincount(st_, minlength=4)
+    assert (st_ == 0).mean() > 0.999, np.bincount(st_, minlength=4)
     z = orc.affine(r, centres, rho)
-    z_ref = orc.affine(r_ref, centres, rho)
-    k_gpu, t_gpu = _kept(z, tiles, nx, ny, with_tiles=True)
-    k_ref = _kept(z_ref, tiles, nx, ny)
-    assert abs(k_gpu.size - k_ref.size) <= 2 and k_gpu.size >= 20
-    # the two coefficient sets differ by delta (<= 1e-12 of a tile's largest
-    # coefficient, asserted above), which moves a root w of g by about
-    # delta * kappa_n, kappa_n = max|a| sum_k |w|^k / |g'(w)|: near the window
-    # corners |f| spans orders of magnitude over one sub-disk and kappa_n is large
-    delta = (np.abs(co - co_ref) / scale).max(axis=1)
-    w = (k_gpu - centres[t_gpu]) / rho
-    a = co_ref[t_gpu]
-    dg = sum(k * a[:, k] * w ** (k - 1) for k in range(1, 7))
-    kappa_n = scale[t_gpu, 0] * sum(np.abs(w) ** k for k in range(7)) / np.abs(dg)
-    near = np.abs(k_gpu[:, None] - k_ref[None, :]).min(axis=1) / rho
-    bound = 100 * np.maximum(delta[t_gpu], 1e-16) * kappa_n + 1e-12
-    assert (near <= bound).sum() >= k_gpu.size - 2, (near / bound).max()
-    assert (near <= 1e-9).mean() > 0.8
+    k_gpu = _kept(z, tiles, nx, ny)
+    k_ref = _kept(orc.affine(r_ref, centres, rho), tiles, nx, ny)
+    assert k_gpu.size == k_ref.size == 18
+    assert np.abs(np.sort_complex(k_gpu) - np.sort_complex(k_ref)).max() <= 1e-9
+    step = np.abs(WL.f_sin_cube(k_gpu) / (3 * k_gpu ** 2 * np.cos(k_gpu ** 3) + 0.5))
+    assert step.max() < 1e-8
     # histogram: the oracle's clip + binning of the GPU roots, bit for bit
     h_ref, oow, dropped = orc.hist_tiled(z, np.arange(nx * ny), nx, ny, tiles.tuple(), W, H)
     assert np.array_equal(h, h_ref)
-    assert st["clipped"] == dropped and st["binned"] == int(h_ref.sum()) and st["polys"] == nx * ny
-    assert st["binned"] == k_gpu.size
+    assert st["clipped"] == dropped and st["binned"] == int(h_ref.sum()) == 18 and st["polys"] == nx * ny
 
 
 def test_full_grid_fused_equals_split_path(dev, orc):
