@@ -316,6 +316,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         elapsed_pl, kern_pl, st_pl, clk_pl = timed_leg("plain")
         plain = {"elapsed_ms": elapsed_pl, "kern_ms": kern_pl, "stats": st_pl, "clocks": clk_pl}
 
+    # the small plain-FP64 configuration's latency: 65,536 monic degree-6
+    # polynomials with seeded roots in the unit disk (complex128), roots +
+    # histogram over [-1.5,1.5]x[-0.84375,0.84375], one CUDA-graph replay per
+    # call, median of 20 after 3 warm-ups
+    latency = small_batch_latency(api, WL, torch, dev, stream) if rank == 0 else None
+
     # one exchange step: sum the per-rank images (after the timed region)
     reduce_ms = None
     if world > 1:
@@ -384,6 +390,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         line["mixed_over_plain"] = value / pv
     if e2e is not None:
         line["e2e"] = e2e
+    if latency is not None:
+        line["small_batch_latency"] = latency
     if reduce_ms is not None:
         line["hist_reduce_ms"] = reduce_ms
     if not args.no_cpu:
@@ -835,6 +843,44 @@ def run_pipeline(args, rank, world, local_rank):
         "status": {k: st[k] for k in ("status_ok", "status_not_converged", "status_rejected", "status_degenerate")},
         "gpu_launches": 4 * args.steps, "clocks": clk,
     }), flush=True)
+
+
+def small_batch_latency(api, WL, torch, dev, stream, reps=20, warmup=3):
+    """Median latency of one roots + histogram call on 65,536 unit-disk
+    degree-6 polynomials in plain FP64, replayed from a CUDA graph."""
+    import numpy as np
+    n = 65536
+    co, _ = WL.unit_disk_roots(1, n)
+    coeffs = torch.from_numpy(np.ascontiguousarray(co.T)).to(dev)
+    hist = api.new_hist(W_PIX, H_PIX, dev)
+    win = api.Window(-1.5, 1.5, -0.84375, 0.84375)
+    p = api.params("plain")
+    api.roots_density(coeffs, win, hist, mode="plain", params_=p)  # loads the kernel, sizes the grid
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            api.hist_clear(hist)
+            api.roots_density(coeffs, win, hist, mode="plain", params_=p)
+    stream.wait_stream(side)
+    for _ in range(warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    times.sort()
+    med = times[len(times) // 2]
+    return {"polys": n, "mode": "plain FP64 (tol 1e-13)", "median_ms": med, "min_ms": times[0],
+            "polys_per_s": n / (med * 1e-3), "binned": int(hist.sum()),
+            "note": "unit-disk roots (seed 1), complex128, one graph replay = histogram clear + fused solve"}
 
 
 def render_frames(api, torch, dev, stream, n_frames=60):
