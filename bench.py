@@ -402,6 +402,34 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     print(json.dumps(line), flush=True)
 
 
+def bind_to_gpu_local_cpus(torch, dev):
+    """Restrict this process to the CPUs the kernel lists as local to the GPU
+    (sysfs local_cpulist of its PCI function), so that page-locked buffers
+    allocated next land on the memory node next to it (the caller restores
+    the previous set afterwards). Best effort: returns what was done, or why
+    not."""
+    try:
+        props = torch.cuda.get_device_properties(dev)
+        bdf = f"{props.pci_domain_id:04x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0"
+        with open(f"/sys/bus/pci/devices/{bdf}/local_cpulist") as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return {"bound": False, "why": f"no allowed CPU in {spec}", "pci": bdf}
+        before = os.sched_getaffinity(0)
+        os.sched_setaffinity(0, cpus)
+        return {"bound": True, "pci": bdf, "cpus": spec, "_restore": before}
+    except (OSError, AttributeError, ValueError) as e:
+        return {"bound": False, "why": f"{type(e).__name__}: {e}"[:120]}
+
+
 def run_e2e(args, coeffs_dev, win, dev, world):
     """Same metric through the public API with the inputs in pinned host memory:
     per step, the chunks are copied host-to-device on a copy stream while the
@@ -413,10 +441,13 @@ def run_e2e(args, coeffs_dev, win, dev, world):
     n = coeffs_dev.shape[1]
     chunk = min(n, 1 << E2E_CHUNK_LOG2)
     nchunks = (n + chunk - 1) // chunk
+    affinity = bind_to_gpu_local_cpus(torch, dev)  # page-locked buffers on the GPU's own memory node
     host = []
     for c in range(nchunks):
         part = coeffs_dev[:, c * chunk:(c + 1) * chunk].contiguous().cpu().pin_memory()
         host.append(part)
+    if "_restore" in affinity:  # the pages are placed; give the CPUs back to the other legs
+        os.sched_setaffinity(0, affinity.pop("_restore"))
     bufs = [torch.empty((DEGREE + 1) * chunk, dtype=torch.complex64, device=dev) for _ in range(2)]
     hist = api.new_hist(W_PIX, H_PIX, dev)
     stats = api.new_stats(dev)
@@ -487,7 +518,8 @@ def run_e2e(args, coeffs_dev, win, dev, world):
         pass
     return {"value": n * world * args.steps / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": ms / args.steps, "chunks_per_step": nchunks,
-            "gpu_launches_per_step": 2 + nchunks, "h2d_copy_only_gbs": h2d_gbs, "clocks": e2e_clocks}
+            "gpu_launches_per_step": 2 + nchunks, "h2d_copy_only_gbs": h2d_gbs, "host_affinity": affinity,
+            "clocks": e2e_clocks}
 
 
 UNEVEN_SEED = 3
