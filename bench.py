@@ -93,13 +93,15 @@ def profiled_traffic():
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
-    """nvidia-smi samples every 200 ms while running (the timed region)."""
+    """nvidia-smi samples every interval_ms (default 200) while running (the
+    timed region)."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 200):
         self.gpu = gpu_index
+        self.interval_ms = interval_ms
         self.proc = None
         self.lines = []
 
@@ -107,7 +109,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.interval_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
         return self
@@ -430,7 +432,74 @@ def bind_to_gpu_local_cpus(torch, dev):
         return {"bound": False, "why": f"{type(e).__name__}: {e}"[:120]}
 
 
+def release_pinned(torch):
+    """Return cached page-locked host memory and device blocks to the system."""
+    import gc
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    try:
+        torch._C._host_emptyCache()
+    except AttributeError:
+        pass
+
+
 def run_e2e(args, coeffs_dev, win, dev, world):
+    """Same metric through the public API with the inputs in page-locked host
+    memory: each step, rd_roots_density reads the 56 B of every polynomial
+    straight from host memory across the host link while it solves (the
+    buffer is mapped into the device address space; zero copy), then the
+    histogram and counters are read back to the host. The chunked variant
+    with explicit copies on a copy stream is measured beside it."""
+    import torch
+
+    from paper_2507_02164_gb300 import api, dist as D
+
+    n = coeffs_dev.shape[1]
+    affinity = bind_to_gpu_local_cpus(torch, dev)
+    host = coeffs_dev.cpu().pin_memory()
+    if "_restore" in affinity:
+        os.sched_setaffinity(0, affinity.pop("_restore"))
+    hist = api.new_hist(W_PIX, H_PIX, dev)
+    stats = api.new_stats(dev)
+    hist_h = torch.empty_like(hist, device="cpu").pin_memory()
+    stats_h = torch.empty_like(stats, device="cpu").pin_memory()
+    comp = torch.cuda.current_stream()
+    p = api.params("mixed")
+
+    def step():
+        api.hist_clear(hist)
+        api.hist_clear(stats)
+        api.roots_density(host, win, hist, mode="mixed", params_=p, stats=stats)
+        hist_h.copy_(hist, non_blocking=True)
+        stats_h.copy_(stats, non_blocking=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index or 0) as clk:
+        t0.record(comp)
+        for _ in range(args.steps):
+            step()
+        t1.record(comp)
+        torch.cuda.synchronize()
+    ms = D.max_over_ranks(t0.elapsed_time(t1), device=dev)
+    h2d = host.numel() * host.element_size()
+    d2h = hist_h.numel() * hist_h.element_size() + stats_h.numel() * stats_h.element_size()
+    out = {"value": n * world * args.steps / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": ms / args.steps, "gpu_launches_per_step": 3,
+           "input": "page-locked host memory, read by the solve kernel across the host link (zero copy)",
+           "host_link_gbs_needed": h2d / (ms / args.steps * 1e-3) / 1e9, "host_affinity": affinity,
+           "clocks": clk.summary()}
+    del host
+    release_pinned(torch)
+    out["copy_engine"] = run_e2e_copies(args, coeffs_dev, win, dev, world)
+    return out
+
+
+def run_e2e_copies(args, coeffs_dev, win, dev, world):
     """Same metric through the public API with the inputs in pinned host memory:
     per step, the chunks are copied host-to-device on a copy stream while the
     previous chunk is solved, and the histogram and counters are read back."""
@@ -508,14 +577,7 @@ def run_e2e(args, coeffs_dev, win, dev, world):
     h2d_gbs = h2d / (c0.elapsed_time(c1) * 1e-3) / 1e9
     # release the pinned staging buffers now (3.76 GB of page-locked host memory)
     del host, bufs
-    import gc
-    gc.collect()
-    torch.cuda.synchronize()
-    torch.cuda.empty_cache()
-    try:
-        torch._C._host_emptyCache()
-    except AttributeError:
-        pass
+    release_pinned(torch)
     return {"value": n * world * args.steps / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": ms / args.steps, "chunks_per_step": nchunks,
             "gpu_launches_per_step": 2 + nchunks, "h2d_copy_only_gbs": h2d_gbs, "host_affinity": affinity,
@@ -613,14 +675,51 @@ def run_uneven(args, rank: int, world: int, local_rank: int):
     if world > 1:
         D.reduce_images(hist, dst=0)
 
-    # end to end: inputs from pinned host memory, copied in every step
+    # end to end: inputs in page-locked host memory. Main: the graph's own
+    # kernels (count, pack) read them across the host link (zero copy);
+    # beside it: explicit copies into the device buffers before each replay
     e2e = None
     if not args.no_e2e:
         hp, hd, ho = (packed.cpu().pin_memory(), deg.cpu().pin_memory(), off.cpu().pin_memory())
         hist_h = torch.empty_like(hist, device="cpu").pin_memory()
         stats_h = torch.empty_like(stats, device="cpu").pin_memory()
+        h2d = hp.numel() * hp.element_size() + hd.numel() + ho.numel() * 8
+        d2h = hist_h.numel() * 4 + stats_h.numel() * 8
 
-        def e2e_step():
+        def host_body():
+            api.hist_clear(hist)
+            api.hist_clear(stats)
+            api.roots_uneven(hp, hd, ho, ws, mode="mixed", params_=p, tuning=tuning, window=win, hist=hist,
+                             stats=stats, want_roots=False, want_status=False)
+
+        host_body()
+        torch.cuda.synchronize()
+        graph_h = torch.cuda.CUDAGraph()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph_h, stream=side):
+                host_body()
+        stream.wait_stream(side)
+
+        def time_e2e(step):
+            for _ in range(args.warmup):
+                step()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return D.max_over_ranks(e0.elapsed_time(e1), device=dev)
+
+        def zero_copy_step():
+            graph_h.replay()
+            hist_h.copy_(hist, non_blocking=True)
+            stats_h.copy_(stats, non_blocking=True)
+
+        def copy_step():
             packed.copy_(hp, non_blocking=True)
             deg.copy_(hd, non_blocking=True)
             off.copy_(ho, non_blocking=True)
@@ -628,20 +727,14 @@ def run_uneven(args, rank: int, world: int, local_rank: int):
             hist_h.copy_(hist, non_blocking=True)
             stats_h.copy_(stats, non_blocking=True)
 
-        for _ in range(args.warmup):
-            e2e_step()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ems = D.max_over_ranks(e0.elapsed_time(e1), device=dev)
-        e2e = {"value": n * world * args.steps / (ems * 1e-3), "unit": UNIT,
-               "h2d_bytes_per_step": hp.numel() * hp.element_size() + hd.numel() + ho.numel() * 8,
-               "d2h_bytes_per_step": hist_h.numel() * 4 + stats_h.numel() * 8, "ms_per_step": ems / args.steps}
+        ems = time_e2e(zero_copy_step)
+        cms = time_e2e(copy_step)
+        e2e = {"value": n * world * args.steps / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": ems / args.steps,
+               "input": "page-locked host memory, read by the graph's count and pack kernels across the host "
+                        "link (zero copy)",
+               "copy_engine": {"value": n * world * args.steps / (cms * 1e-3), "ms_per_step": cms / args.steps,
+                               "note": "explicit host-to-device copies of the inputs before each replay"}}
     if rank != 0:
         return
     mhz = clk.summary().get("sm_max_mhz") or 2070.0

@@ -183,6 +183,18 @@ int rd_density_accumulate(const double *roots, int64_t n_roots, rd_window window
 /* Zero `words` 32-bit words of device memory (histogram or rd_stats). */
 int rd_hist_clear(uint32_t *hist, int64_t words, void *stream);
 
+/* ---- inputs in page-locked host memory ---------------------------------------
+ * Every input array of the solve entry points (coefficients, degrees,
+ * offsets, samples) is read by the kernels through its address, so it may be
+ * device memory or page-locked host memory that the CUDA runtime maps into the
+ * device address space at the same address (unified addressing): the kernels
+ * then read it across the host link while they compute (zero copy). Passing
+ * any other host address faults the kernel. rd_pointer_is_device_accessible
+ * returns 1 for device or managed memory and for page-locked host memory whose
+ * device address equals its host address, 0 otherwise (also when no GPU is
+ * present). Host-side only; it enqueues nothing. */
+int rd_pointer_is_device_accessible(const void *p);
+
 /* ---- uneven degrees (1..12) in one pass -------------------------------------
  * Packed poly-major batch: polynomial i has degree degrees[i] and its
  * coefficients a_0..a_d are coeffs[offsets[i] .. offsets[i+1]-1] (offsets has

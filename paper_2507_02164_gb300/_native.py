@@ -62,6 +62,7 @@ STATIC_SCRATCH_BYTES = 32 * 1024 * 1024  # RD_STATIC_SCRATCH_BYTES
 P, I32, I64, F64, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
 SIGNATURES = {
     "rd_abi_version": (I32, []),
+    "rd_pointer_is_device_accessible": (I32, [P]),
     "rd_last_error": (ctypes.c_char_p, []),
     "rd_device_sm_count": (I32, []),
     "rd_default_params": (None, [I32, ctypes.POINTER(Params)]),

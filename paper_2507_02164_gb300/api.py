@@ -78,8 +78,27 @@ def stats_dict(stats: torch.Tensor) -> dict:
     return dict(zip(N.STATS_FIELDS, vals))
 
 
+def _check_input(name: str, t: torch.Tensor, dtype=None):
+    """An input array the kernels read: a CUDA tensor, or a page-locked CPU
+    tensor mapped into the device address space (the kernels then read it
+    across the host link, zero copy), checked through the CUDA runtime."""
+    if not t.is_cuda:
+        if not (t.is_pinned() and N.load().rd_pointer_is_device_accessible(ctypes.c_void_p(t.data_ptr())) == 1):
+            raise ValueError(f"{name} must be a CUDA tensor or page-locked host memory mapped for the device")
+    _check_cuda(name, t, dtype) if t.is_cuda else None
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _out_device(t: torch.Tensor) -> torch.device:
+    """Where outputs go for input t: its GPU, or the current GPU for host input."""
+    return t.device if t.is_cuda else torch.device("cuda", torch.cuda.current_device())
+
+
 def _coeff_args(coeffs: torch.Tensor):
-    _check_cuda("coeffs", coeffs)
+    _check_input("coeffs", coeffs)
     if coeffs.dtype not in DTYPES:
         raise ValueError("coeffs must be complex64 or complex128")
     if coeffs.dim() != 2 or coeffs.shape[0] < 2:
@@ -89,9 +108,10 @@ def _coeff_args(coeffs: torch.Tensor):
 
 def roots_batched(coeffs: torch.Tensor, mode="mixed", params_=None, roots=None, status=None, stats=None,
                   want_roots=True, want_status=True, stream=None):
-    """Roots of every column of coeffs ([d+1, n]). Returns (roots [d, n] c128, status [n] u8)."""
+    """Roots of every column of coeffs ([d+1, n]; on the GPU or in page-locked
+    host memory). Returns (roots [d, n] c128, status [n] u8) on the GPU."""
     dt, d, n = _coeff_args(coeffs)
-    dev = coeffs.device
+    dev = _out_device(coeffs)
     if want_roots and roots is None:
         roots = torch.empty((d, n), dtype=torch.complex128, device=dev)
     if want_status and status is None:
@@ -127,7 +147,9 @@ def make_clip(centres: torch.Tensor, radius: float, nx: int, ny: int, tiles: Win
 
 def roots_density(coeffs: torch.Tensor, window: Window, hist: torch.Tensor, mode="mixed", params_=None,
                   clip=None, roots=None, status=None, stats=None, stream=None):
-    """Fused roots + binning into hist ([H, W] int32 viewed as uint32, accumulated)."""
+    """Fused roots + binning into hist ([H, W] int32 viewed as uint32, accumulated).
+    coeffs may be on the GPU or in page-locked host memory (read by the kernel
+    across the host link)."""
     dt, d, n = _coeff_args(coeffs)
     _check_cuda("hist", hist)
     H, W = hist.shape
@@ -172,20 +194,24 @@ def roots_uneven(coeffs: torch.Tensor, degrees: torch.Tensor, offsets: torch.Ten
                  status=None, stats=None, stream=None, want_roots=True, want_status=True):
     """Roots of a packed uneven-degree batch (coefficients lowest power first,
     polynomial i at coeffs[offsets[i]:offsets[i+1]]); roots packed without the
-    leading coefficient. Optionally bins them into hist over window."""
-    _check_cuda("coeffs", coeffs)
+    leading coefficient. Optionally bins them into hist over window. The
+    inputs (coeffs, degrees, offsets) may be on the GPU or in page-locked host
+    memory; workspace and outputs are on the GPU."""
+    _check_input("coeffs", coeffs)
     if coeffs.dtype not in DTYPES or coeffs.dim() != 1:
         raise ValueError("coeffs must be a 1-D complex64/complex128 tensor")
-    _check_cuda("degrees", degrees, torch.uint8)
-    _check_cuda("offsets", offsets, torch.int64)
+    _check_input("degrees", degrees, torch.uint8)
+    _check_input("offsets", offsets, torch.int64)
+    _check_cuda("workspace", workspace)
     n = degrees.numel()
     if offsets.numel() != n + 1:
         raise ValueError("offsets must have n+1 entries")
     ncoef = coeffs.numel()
+    dev = workspace.device
     if roots is None and want_roots:
-        roots = torch.empty(ncoef - n, dtype=torch.complex128, device=coeffs.device)
+        roots = torch.empty(ncoef - n, dtype=torch.complex128, device=dev)
     if status is None and want_status:
-        status = torch.empty(n, dtype=torch.uint8, device=coeffs.device)
+        status = torch.empty(n, dtype=torch.uint8, device=dev)
     p = params_ if params_ is not None else params(mode)
     H, W = hist.shape if hist is not None else (0, 0)
     win = ctypes.byref(window.c()) if window is not None else None

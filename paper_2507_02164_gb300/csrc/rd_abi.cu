@@ -196,6 +196,25 @@ extern "C" {
 
 int rd_abi_version(void) { return RD_ABI_VERSION; }
 
+int rd_pointer_is_device_accessible(const void *p)
+{
+    if (!p) return 0;
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free error of the query
+        return 0;
+    }
+    switch (attr.type) {
+    case cudaMemoryTypeDevice:
+    case cudaMemoryTypeManaged:
+        return 1;
+    case cudaMemoryTypeHost:
+        return attr.devicePointer == p ? 1 : 0;
+    default:
+        return 0;
+    }
+}
+
 const char *rd_last_error(void) { return g_err; }
 
 int rd_device_sm_count(void)

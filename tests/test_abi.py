@@ -187,3 +187,18 @@ def test_field_density_argument_validation_without_gpu():
 def test_python_binding_raises_on_error():
     with pytest.raises(N.RootDensityError):
         N.call("rd_hist_clear", ctypes.c_void_p(0), 5, ctypes.c_void_p(0))
+
+
+def test_device_accessibility_query_without_gpu():
+    """No GPU: nothing is device-accessible, and the query does not fail."""
+    L = N.load()
+    buf = (ctypes.c_char * 64)()
+    assert L.rd_pointer_is_device_accessible(ctypes.cast(buf, ctypes.c_void_p)) == 0
+    assert L.rd_pointer_is_device_accessible(None) == 0
+
+
+def test_host_inputs_must_be_mapped_page_locked_memory():
+    import torch
+    from paper_2507_02164_gb300 import api
+    with pytest.raises(ValueError, match="page-locked"):
+        api.roots_batched(torch.zeros((7, 4), dtype=torch.complex64), mode="mixed")

@@ -317,3 +317,27 @@ def test_roots_do_not_depend_on_a_power_of_two_scale(dev, mode, lanes):
     for e in (130, -130, 600):
         r, s, _, _ = _solve(to_soa(co * 2.0 ** e, dev), mode, lanes=lanes)
         assert np.array_equal(r, r0) and np.array_equal(s, s0), e
+
+
+def test_inputs_in_page_locked_host_memory_give_identical_results(dev):
+    """Zero copy: coefficients in page-locked host memory are read by the
+    kernel across the host link; roots, status and histogram equal those of
+    the same coefficients on the device, bit for bit. Pageable host memory
+    is refused before any kernel sees it."""
+    co = to_soa(WL.gaussian(13, 20000 + 7, 6), dev, torch.complex64)
+    host = co.cpu().pin_memory()
+    r_d, s_d, h_d, st_d = _solve(co, "mixed", WIN2)
+    hist = api.new_hist(W, H, dev)
+    roots = torch.empty((6, co.shape[1]), dtype=torch.complex128, device=dev)
+    status = torch.empty(co.shape[1], dtype=torch.uint8, device=dev)
+    stats = api.new_stats(dev)
+    api.roots_density(host, WIN2, hist, mode="mixed", roots=roots, status=status, stats=stats)
+    torch.cuda.synchronize()
+    assert np.array_equal(roots_poly_major(roots), r_d) and np.array_equal(status.cpu().numpy(), s_d)
+    assert torch.equal(hist, h_d) and api.stats_dict(stats) == st_d
+    r_b, s_b = api.roots_batched(host, mode="plain")
+    r_c, s_c = api.roots_batched(co, mode="plain")
+    torch.cuda.synchronize()
+    assert r_b.is_cuda and torch.equal(r_b, r_c) and torch.equal(s_b, s_c)
+    with pytest.raises(ValueError, match="page-locked"):
+        api.roots_batched(co.cpu(), mode="mixed")

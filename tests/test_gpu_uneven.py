@@ -164,3 +164,21 @@ def test_full_size_batch_sampled(dev, orc):
         ref, ref_st, _, _ = orc.solve(rows)
         good = (s[idx] == 0) & (ref_st == 0)
         compare_roots(r_gpu[good], ref[good], rows[good], orc, 1e-9, 1e3)
+
+
+def test_uneven_inputs_in_page_locked_host_memory(dev):
+    """The count and pack kernels read coefficients, degrees and offsets from
+    page-locked host memory (zero copy): same roots, status and histogram as
+    from device memory."""
+    n = 30000 + 5
+    packed, deg, off = WL.uneven_gaussian(7, n)
+    c_d, d_d, o_d = (torch.from_numpy(x).to(dev) for x in (packed, deg, off))
+    c_h, d_h, o_h = (torch.from_numpy(x).pin_memory() for x in (packed, deg, off))
+    ws = api.new_uneven_workspace(n, packed.size, torch.complex64, dev)
+    out = []
+    for c, d, o in ((c_d, d_d, o_d), (c_h, d_h, o_h)):
+        hist = api.new_hist(W, H, dev)
+        r, s = api.roots_uneven(c, d, o, ws, mode="mixed", window=WIN3, hist=hist)
+        torch.cuda.synchronize()
+        out.append((r.cpu(), s.cpu(), hist.cpu()))
+    assert all(torch.equal(a, b) for a, b in zip(out[0], out[1]))
