@@ -62,7 +62,9 @@ __device__ __forceinline__ cx<double> field_eval(const FieldArgs<N> &F, cx<doubl
         // from one exponential: (e^y +- e^-y) / 2. For small |y| the
         // difference loses relative accuracy in sinh y but not absolute
         // accuracy (about 1e-16), which is what the L2 fit of f needs.
-        const cx<double> z3 = mul(mul(z, z), z);
+        // z^3 = x (x^2 - 3 y^2) + i y (3 x^2 - y^2)
+        const double x2 = z.re * z.re, y2 = z.im * z.im;
+        const cx<double> z3 = {z.re * fma(-3.0, y2, x2), z.im * fma(3.0, x2, -y2)};
         double sa, ca;
         sincos(z3.re, &sa, &ca);
         const double e = exp(z3.im), ei = 1.0 / e;
@@ -96,9 +98,11 @@ struct TileMap {
 template <int N>
 struct FieldSmem {
     static constexpr size_t tw_bytes = (size_t)(N + 1) * FIELD_NT * 4 * sizeof(float);
+    static constexpr size_t node_bytes = (size_t)FIELD_NR * FIELD_NT * sizeof(double2);  // rho r_p e^{i theta_q}
     static constexpr size_t coef_per_warp = (size_t)(N + 1) * 32;      // double2
     static constexpr size_t samp_per_warp = (size_t)FIELD_NR * FIELD_NT;  // double2
-    static constexpr size_t bytes = tw_bytes + FIELD_WARPS * (coef_per_warp + samp_per_warp) * sizeof(double2);
+    static constexpr size_t bytes =
+        tw_bytes + node_bytes + FIELD_WARPS * (coef_per_warp + samp_per_warp) * sizeof(double2);
 };
 
 template <int N, int MODE>
@@ -111,9 +115,10 @@ __global__ void __launch_bounds__(FIELD_WARPS * 32, MODE != MODE_PLAIN ? 2 : 1)
     using SM = FieldSmem<N>;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float(*s_tw)[FIELD_NT][4] = reinterpret_cast<float(*)[FIELD_NT][4]>(smem);  // hi re, hi im, lo re, lo im
-    double2 *s_coef = reinterpret_cast<double2 *>(smem + SM::tw_bytes) + wid * SM::coef_per_warp;
-    double2 *s_samp = reinterpret_cast<double2 *>(smem + SM::tw_bytes) + FIELD_WARPS * SM::coef_per_warp +
-                      wid * SM::samp_per_warp;
+    double2 *s_node = reinterpret_cast<double2 *>(smem + SM::tw_bytes);        // [p][q]
+    double2 *s_coef = reinterpret_cast<double2 *>(smem + SM::tw_bytes + SM::node_bytes) + wid * SM::coef_per_warp;
+    double2 *s_samp = reinterpret_cast<double2 *>(smem + SM::tw_bytes + SM::node_bytes) +
+                      FIELD_WARPS * SM::coef_per_warp + wid * SM::samp_per_warp;
     for (int i = threadIdx.x; i < (N + 1) * FIELD_NT; i += blockDim.x) {
         const int j = i / FIELD_NT, q = i % FIELD_NT;
         s_tw[j][q][0] = F.thi[j][q][0];
@@ -121,9 +126,13 @@ __global__ void __launch_bounds__(FIELD_WARPS * 32, MODE != MODE_PLAIN ? 2 : 1)
         s_tw[j][q][2] = F.tlo[j][q][0];
         s_tw[j][q][3] = F.tlo[j][q][1];
     }
+    // node offsets rho (r_p cos theta_q, r_p sin theta_q), once per CTA
+    for (int i = threadIdx.x; i < FIELD_NR * FIELD_NT; i += blockDim.x) {
+        const int p = i / FIELD_NT, q = i % FIELD_NT;
+        s_node[i] = make_double2(__dmul_rn(F.rho, F.r[p] * F.ct[q]), __dmul_rn(F.rho, F.r[p] * F.st[q]));
+    }
     const CtaStats S = stats_begin(acc, A.stats);  // its barrier (when stats are kept) publishes s_tw
     if (!A.stats) __syncthreads();
-    const double ct = F.ct[lane], st = F.st[lane];
     const int64_t ntiles = (int64_t)F.nx * F.ny;
     const int64_t groups = (ntiles + 31) / 32;
     const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -140,8 +149,8 @@ __global__ void __launch_bounds__(FIELD_WARPS * 32, MODE != MODE_PLAIN ? 2 : 1)
             unsigned emax = 0;
 #pragma unroll 1
             for (int p = 0; p < FIELD_NR; ++p) {
-                const double wr = F.r[p] * ct, wi = F.r[p] * st;
-                const cx<double> z = {__dadd_rn(cxr, __dmul_rn(F.rho, wr)), __dadd_rn(cxi, __dmul_rn(F.rho, wi))};
+                const double2 w = s_node[p * FIELD_NT + lane];
+                const cx<double> z = {__dadd_rn(cxr, w.x), __dadd_rn(cxi, w.y)};
                 const cx<double> v = field_eval(F, z);
                 s_samp[p * FIELD_NT + lane] = make_double2(v.re, v.im);
                 const unsigned ex = ((unsigned)__double2hiint(v.re) >> 20) & 0x7ffu;
