@@ -65,7 +65,15 @@ def splat(roots: torch.Tensor, window=WINDOW, W: int = W_IMG, H: int = H_IMG, si
     return SplatFn.apply(roots, tuple(float(v) for v in window), int(W), int(H), float(sigma), 1.0 / norm)
 
 
-def loss(roots: torch.Tensor, target: torch.Tensor, lam: float = 1.0, **kw) -> torch.Tensor:
-    """sum |z|^2 + lam * sum (splat(roots) - target)^2."""
+def loss(roots: torch.Tensor, target: torch.Tensor, lam: float = 1.0, global_sum=None, **kw) -> torch.Tensor:
+    """sum |z|^2 + lam * sum (splat(roots) - target)^2.
+
+    Across ranks: pass n_norm = the number of roots of all ranks and
+    global_sum = dist.global_density; the image term then uses the summed
+    image and the |z|^2 term is this rank's share (the loss value is the sum
+    of the ranks' |z|^2 terms plus one image term; the gradients of every
+    rank's roots are those of that global loss)."""
     d = splat(roots, **kw)
+    if global_sum is not None:
+        d = global_sum(d)
     return (roots.real ** 2 + roots.imag ** 2).sum() + lam * ((d - target) ** 2).sum()

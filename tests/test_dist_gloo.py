@@ -93,3 +93,54 @@ def test_shard_ranges_are_disjoint_and_cover():
     assert rs == [(0, 10), (10, 20), (20, 30), (30, 40)]
     with pytest.raises(ValueError):
         D.shard_range(-1, 0)
+
+
+# ----------------------------------- differentiation workload across ranks
+
+def _density_worker(rank, world, port, out_dir):
+    """Each rank: a leaf x_r, its image D_r = M_r x_r (a differentiable stand-in
+    for the soft-density splat, which runs on the GPU), the global image
+    sum_r D_r through dist.global_density, the loss |x_r|^2 + sum (D - T)^2,
+    and the backward pass."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=20))
+    from paper_2507_02164_gb300 import dist as D
+    try:
+        g = torch.Generator().manual_seed(100 + rank)
+        M = torch.randn(20, 3, generator=g, dtype=torch.float64)
+        x = torch.randn(3, generator=g, dtype=torch.float64).requires_grad_(True)
+        img = D.global_density((M @ x).reshape(4, 5))
+        T = torch.linspace(0.0, 1.0, 20, dtype=torch.float64).reshape(4, 5)
+        L = (x ** 2).sum() + ((img - T) ** 2).sum()
+        L.backward()
+        np.savez(os.path.join(out_dir, f"rank{rank}.npz"), M=M.numpy(), x=x.detach().numpy(),
+                 grad=x.grad.numpy(), img=img.detach().numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_global_density_gradients_across_two_ranks(tmp_path):
+    """The summed image is the same on both ranks, and each rank's gradient
+    equals that of the global loss sum_r |x_r|^2 + sum (sum_r M_r x_r - T)^2
+    computed in one process."""
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=_density_worker, args=(r, 2, port, str(tmp_path))) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert not p.is_alive() and p.exitcode == 0
+    res = [np.load(tmp_path / f"rank{r}.npz") for r in range(2)]
+    D = sum(r["M"] @ r["x"] for r in res)
+    T = np.linspace(0.0, 1.0, 20)
+    for r in res:
+        assert np.allclose(r["img"].reshape(-1), D, rtol=0, atol=1e-14)
+        ref = 2 * r["x"] + 2 * r["M"].T @ (D - T)
+        assert np.allclose(r["grad"], ref, rtol=1e-13, atol=1e-13)
+
+
+def test_global_density_is_the_identity_in_one_process():
+    from paper_2507_02164_gb300 import dist as D
+    x = torch.ones(3, requires_grad=True)
+    assert D.global_density(x) is x
