@@ -341,3 +341,34 @@ def test_inputs_in_page_locked_host_memory_give_identical_results(dev):
     assert r_b.is_cuda and torch.equal(r_b, r_c) and torch.equal(s_b, s_c)
     with pytest.raises(ValueError, match="page-locked"):
         api.roots_batched(co.cpu(), mode="mixed")
+
+
+@pytest.mark.parametrize("window,W_,H_", [((-2.0, 2.0, -1.125, 1.125), 1920, 1080),
+                                          ((-0.3, 1.7, -0.9, 0.2), 777, 333),
+                                          ((1e6, 1e6 + 2.0, -1.0, 0.5), 1920, 1080)])
+def test_binning_at_pixel_edges_matches_fp64_bit_for_bit(dev, orc, window, W_, H_):
+    """The pixel index is taken in double-float with an FP64 fallback within
+    1e-6 pixel of an edge; against the oracle's FP64 binning: random points,
+    points on every kind of edge and 1..4 ulps beside them, far and non-finite
+    points, and a window (the last) whose size disables the fast path."""
+    g = np.random.default_rng(W_)
+    xmin, xmax, ymin, ymax = window
+    n = 200000
+    pts = [g.uniform(xmin - 0.1 * (xmax - xmin), xmax, n) + 1j * g.uniform(ymin, ymax + 0.1 * (ymax - ymin), n)]
+    ex = xmin + (xmax - xmin) * g.integers(0, W_ + 1, 5000) / W_  # pixel edges, as the host computes them
+    ey = ymax - (ymax - ymin) * g.integers(0, H_ + 1, 5000) / H_
+    def ulps(v, k):  # v moved by k ulps
+        for _ in range(abs(k)):
+            v = np.nextafter(v, np.inf if k > 0 else -np.inf)
+        return v
+
+    for k in range(-4, 5):
+        pts.append(ulps(ex, k) + 1j * g.uniform(ymin, ymax, 5000) if k else ex + 1j * ey)
+        pts.append(g.uniform(xmin, xmax, 5000) + 1j * (ulps(ey, k) if k else ey))
+    pts.append(np.array([complex(np.nan, 0), complex(0, np.inf), complex(1e300, 0), complex(-1e200, 1e200)]))
+    z = np.concatenate(pts)
+    hist = api.new_hist(W_, H_, dev)
+    api.density_accumulate(torch.from_numpy(z).to(dev), api.Window(*window), hist)
+    torch.cuda.synchronize()
+    ref, _ = orc.hist(z, window, W_, H_)
+    assert np.array_equal(hist_np(hist), ref)
