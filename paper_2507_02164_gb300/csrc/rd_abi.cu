@@ -79,12 +79,6 @@ bool window_ok(const rd_window &w)
            w.xmin < w.xmax && w.ymin < w.ymax;
 }
 
-void df_pair(double v, float &hi, float &lo)
-{
-    hi = (float)v;
-    lo = (float)(v - (double)hi);
-}
-
 rd::Binner make_binner(const rd_window &w, int W, int H)
 {
     rd::Binner b;
@@ -94,16 +88,6 @@ rd::Binner make_binner(const rd_window &w, int W, int H)
     b.sy = (double)H / (w.ymax - w.ymin);
     b.W = W;
     b.H = H;
-    // the double-float pixel index is exact up to 2^-25 pixel when the window's
-    // origin, scale and size stay below 2^20 pixels (see pixel_of_fast)
-    const double lim = 1048576.0;
-    b.df_ok = W < lim && H < lim && std::fabs(w.xmin) * b.sx < lim && std::fabs(w.ymax) * b.sy < lim &&
-              b.sx > 1e-30 && b.sx < 1e30 && b.sy > 1e-30 && b.sy < 1e30 && std::fabs(w.xmin) < 1e30 &&
-              std::fabs(w.ymax) < 1e30;
-    df_pair(b.xmin, b.xmin_hi, b.xmin_lo);
-    df_pair(b.ymax, b.ymax_hi, b.ymax_lo);
-    df_pair(b.sx, b.sx_hi, b.sx_lo);
-    df_pair(b.sy, b.sy_hi, b.sy_lo);
     return b;
 }
 

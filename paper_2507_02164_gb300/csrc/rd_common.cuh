@@ -298,10 +298,6 @@ __device__ __forceinline__ unsigned warp_sum_u32(unsigned v)
 struct Binner {
     double xmin, ymax, sx, sy;  // sx = W / (xmax - xmin), sy = H / (ymax - ymin)
     int W, H;
-    // xmin, ymax, sx, sy as double-float pairs (hi + lo), for pixel_of_fast;
-    // df_ok = 0 where the window is outside its exactness conditions
-    float xmin_hi, xmin_lo, ymax_hi, ymax_lo, sx_hi, sx_lo, sy_hi, sy_lo;
-    int df_ok;
 };
 
 // Pixel index of z, or -1 when outside the window or NaN. FP64, no
@@ -318,60 +314,6 @@ __device__ __forceinline__ int pixel_of(const Binner &b, double x, double y)
     int iy = __double2int_rd(fy);
     bool in = finite_bits(x) && finite_bits(y) && ix >= 0 && ix < b.W && iy >= 0 && iy < b.H;
     return in ? iy * b.W + ix : -1;
-}
-
-// One axis of pixel_of_fast: f = t * s in double-float (t, s double-float),
-// then floor(f). Returns 0 with *i = floor(f) when the fractional part is at
-// least 1e-6 from either edge, 1 when f is certainly outside [0, n), 2 when f
-// lies within 1e-6 of an integer (the caller then takes the FP64 path).
-__device__ __forceinline__ int pixel_axis_df(dfl t, dfl s, int n, int *i)
-{
-    const dfl f = df_mul(t, s);
-    const float hi = f.hi, lo = f.lo;
-    if (!(hi >= -1.0f && hi < (float)n + 1.0f)) return 1;
-    // floor(hi) for hi in [-1, n+1): adding 2^23 with rounding down leaves
-    // 2^23 + floor(hi) in the float (spacing 1 there); no conversion issued
-    int k = hi < 0.0f ? -1 : __float_as_int(__fadd_rd(hi, 0x1p23f)) - 0x4B000000;
-    const float kf = k < 0 ? -1.0f : __fsub_rn(__int_as_float(0x4B000000 + k), 0x1p23f);  // (float)k exactly
-    float r = __fadd_rn(__fsub_rn(hi, kf), lo);  // hi - k is exact
-    if (r < 0.0f) {
-        k -= 1;
-        r = __fadd_rn(r, 1.0f);
-    } else if (r >= 1.0f) {
-        k += 1;
-        r = __fsub_rn(r, 1.0f);
-    }
-    if (r < 1e-6f || r > 1.0f - 1e-6f) return 2;
-    *i = k;
-    return 0;
-}
-
-// pixel_of's result, with the FP64 pipe used only for the rare root within
-// 1e-6 pixel of an edge (or far outside): (x - xmin) sx and (ymax - y) sy in
-// double-float on the FP32 pipe are within 2^-25 of the exact values for every
-// root that is not clearly outside (the host enables it only for windows with
-// |xmin| sx, |ymax| sy, W, H < 2^20), and pixel_of's FP64 values within 2^-31,
-// so both floor to the same pixel whenever the fractional part is 1e-6 from
-// an edge. Non-finite coordinates give -1 as in pixel_of.
-__device__ __forceinline__ int pixel_of_fast(const Binner &b, double x, double y)
-{
-    if (!b.df_ok) return pixel_of(b, x, y);
-    const unsigned ex = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
-    const unsigned ey = ((unsigned)__double2hiint(y) >> 20) & 0x7ffu;
-    if (ex == 0x7ffu || ey == 0x7ffu) return -1;
-    if (ex > 1023u + 60u || ey > 1023u + 60u) return pixel_of(b, x, y);
-    const dfl xd = split_scaled(x, 0), yd = split_scaled(y, 0);
-    // t = x - xmin and ymax - y as double-float differences
-    dfl sx_ = two_sum(xd.hi, -b.xmin_hi);
-    const dfl tx = fast_two_sum(sx_.hi, __fadd_rn(__fsub_rn(xd.lo, b.xmin_lo), sx_.lo));
-    dfl sy_ = two_sum(b.ymax_hi, -yd.hi);
-    const dfl ty = fast_two_sum(sy_.hi, __fadd_rn(__fsub_rn(b.ymax_lo, yd.lo), sy_.lo));
-    int ix = 0, iy = 0;
-    const int cx = pixel_axis_df(tx, dfl{b.sx_hi, b.sx_lo}, b.W, &ix);
-    const int cy = pixel_axis_df(ty, dfl{b.sy_hi, b.sy_lo}, b.H, &iy);
-    if (cx == 1 || cy == 1) return -1;
-    if (cx == 2 || cy == 2) return pixel_of(b, x, y);
-    return (ix >= 0 && ix < b.W && iy >= 0 && iy < b.H) ? iy * b.W + ix : -1;
 }
 
 // Warp-aggregated histogram increment: lanes holding the same pixel elect one

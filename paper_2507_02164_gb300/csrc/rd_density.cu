@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(256) density_kernel(const double2 *__restrict_
         int pix = -1;
         if (i < n) {
             double2 z = __ldg(roots + i);
-            pix = pixel_of_fast(bin, z.x, z.y);
+            pix = pixel_of(bin, z.x, z.y);
             binned += pix >= 0 ? 1u : 0u;
             oow += pix < 0 ? 1u : 0u;
         }

@@ -588,12 +588,12 @@ __device__ __forceinline__ void solve_warp(const SolveArgs &A, const void *coeff
                 if (A.clip_on) {
                     x = __dadd_rn(__dmul_rn(A.radius, x), cen.re);  // z = c + rho w, no contraction
                     y = __dadd_rn(__dmul_rn(A.radius, y), cen.im);
-                    int t = pixel_of_fast(A.tiles, x, y);
+                    int t = pixel_of(A.tiles, x, y);
                     bool in_tile = (t >= 0) && ((int64_t)t == my_tile);
                     n_clipped += (valid && !in_tile) ? 1u : 0u;
                     keep = keep && in_tile;
                 }
-                int pix = keep ? pixel_of_fast(A.bin, x, y) : -1;
+                int pix = keep ? pixel_of(A.bin, x, y) : -1;
                 n_binned += (pix >= 0) ? 1u : 0u;
                 n_oow += (keep && pix < 0) ? 1u : 0u;
                 hist_add(A.hist, pix);
