@@ -308,9 +308,15 @@ int rd_l2_approx(const double *samples, int64_t n, int nr, int nt, int degree, i
  * gradient convention) of a loss L(img), given grad_img = dL/dimg (device
  * double [H][W]); grad_roots: device rd_c128 [n], overwritten. */
 int rd_splat(const double *roots, int64_t n, rd_window window, int W, int H, double sigma, double scale,
-             double *img, void *stream);
+             int precision, double *img, void *stream);
 int rd_splat_backward(const double *roots, int64_t n, rd_window window, int W, int H, double sigma, double scale,
-                      const double *grad_img, double *grad_roots, void *stream);
+                      int precision, const double *grad_img, double *grad_roots, void *stream);
+/* precision: RD_SPLAT_FP64 computes the stencil in FP64 (~1e-14 relative);
+ * RD_SPLAT_FP32 in FP32 on the FP32 pipe (~1e-6 relative; for complex64
+ * coefficients, whose roots carry ~1e-7 anyway). Image and gradients are
+ * float64 in both. */
+#define RD_SPLAT_FP64 0
+#define RD_SPLAT_FP32 1
 
 /* ---- the whole path for an analytic f, one launch -----------------------------
  * Sec. II: the region is covered by sub-disks; on each, f is approximated by a

@@ -51,6 +51,7 @@ class FieldSpec(ctypes.Structure):
 
 
 F_SIN_CUBE, F_POLY = 0, 1
+SPLAT_FP64, SPLAT_FP32 = 0, 1
 
 STATS_FIELDS = ("polys", "status_ok", "status_not_converged", "status_rejected", "status_degenerate",
                 "sweeps", "pair_updates", "rotations", "newton_steps", "binned", "out_of_window", "clipped",
@@ -79,8 +80,8 @@ SIGNATURES = {
                                      ctypes.POINTER(UnevenTuning), ctypes.POINTER(Window), I32, I32, P, P, P, P, P]),
     "rd_l2_nodes": (I32, [I32, P, P]),
     "rd_l2_approx": (I32, [P, I64, I32, I32, I32, I32, P, P]),
-    "rd_splat": (I32, [P, I64, Window, I32, I32, F64, F64, P, P]),
-    "rd_splat_backward": (I32, [P, I64, Window, I32, I32, F64, F64, P, P, P]),
+    "rd_splat": (I32, [P, I64, Window, I32, I32, F64, F64, I32, P, P]),
+    "rd_splat_backward": (I32, [P, I64, Window, I32, I32, F64, F64, I32, P, P, P]),
     "rd_field_density": (I32, [I32, ctypes.POINTER(FieldSpec), I32, ctypes.POINTER(Params), Window, I32, I32, P, P,
                                P, P, P, P]),
 }

@@ -30,9 +30,9 @@ int launch_l2(const double *samples, int64_t n, int nr, int degree, double *coef
 int launch_field(const SolveArgs &a, const rd_field_spec &spec, int func, double rho, bool mixed, double *coeffs,
                  int ctas_per_sm, cudaStream_t st);
 int launch_splat(const double *roots, int64_t n, const rd_window &w, int W, int H, double sigma, double scale,
-                 double *img, cudaStream_t st);
+                 int precision, double *img, cudaStream_t st);
 int launch_splat_backward(const double *roots, int64_t n, const rd_window &w, int W, int H, double sigma,
-                          double scale, const double *G, double *grad, cudaStream_t st);
+                          double scale, int precision, const double *G, double *grad, cudaStream_t st);
 }  // namespace rd
 
 static thread_local char g_err[512] = "";
@@ -371,8 +371,11 @@ int rd_l2_approx(const double *samples, int64_t n, int nr, int nt, int degree, i
 }
 
 namespace {
-int check_splat(const double *roots, int64_t n, const rd_window &window, int W, int H, double sigma, double scale)
+int check_splat(const double *roots, int64_t n, const rd_window &window, int W, int H, double sigma, double scale,
+                int precision)
 {
+    if (precision != RD_SPLAT_FP64 && precision != RD_SPLAT_FP32)
+        return rd_set_error(RD_EINVAL, "precision must be RD_SPLAT_FP64 or RD_SPLAT_FP32");
     if (n < 0) return rd_set_error(RD_EINVAL, "n < 0");
     if (n > 0 && (!roots || !aligned(roots, 16))) return rd_set_error(RD_EINVAL, "roots null or misaligned (16 B)");
     if (!window_ok(window)) return rd_set_error(RD_EINVAL, "window must be finite with xmin < xmax, ymin < ymax");
@@ -383,26 +386,27 @@ int check_splat(const double *roots, int64_t n, const rd_window &window, int W, 
 }
 }  // namespace
 
-int rd_splat(const double *roots, int64_t n, rd_window window, int W, int H, double sigma, double scale, double *img,
-             void *stream)
+int rd_splat(const double *roots, int64_t n, rd_window window, int W, int H, double sigma, double scale,
+             int precision, double *img, void *stream)
 {
-    int rc = check_splat(roots, n, window, W, H, sigma, scale);
+    int rc = check_splat(roots, n, window, W, H, sigma, scale, precision);
     if (rc) return rc;
     if (!img || !aligned(img, 8)) return rd_set_error(RD_EINVAL, "img null or misaligned");
     if (n == 0) return RD_OK;
-    return rd::launch_splat(roots, n, window, W, H, sigma, scale, img, reinterpret_cast<cudaStream_t>(stream));
+    return rd::launch_splat(roots, n, window, W, H, sigma, scale, precision, img,
+                            reinterpret_cast<cudaStream_t>(stream));
 }
 
 int rd_splat_backward(const double *roots, int64_t n, rd_window window, int W, int H, double sigma, double scale,
-                      const double *grad_img, double *grad_roots, void *stream)
+                      int precision, const double *grad_img, double *grad_roots, void *stream)
 {
-    int rc = check_splat(roots, n, window, W, H, sigma, scale);
+    int rc = check_splat(roots, n, window, W, H, sigma, scale, precision);
     if (rc) return rc;
     if (!grad_img || !aligned(grad_img, 8)) return rd_set_error(RD_EINVAL, "grad_img null or misaligned");
     if (n > 0 && (!grad_roots || !aligned(grad_roots, 16)))
         return rd_set_error(RD_EINVAL, "grad_roots null or misaligned (16 B)");
     if (n == 0) return RD_OK;
-    return rd::launch_splat_backward(roots, n, window, W, H, sigma, scale, grad_img, grad_roots,
+    return rd::launch_splat_backward(roots, n, window, W, H, sigma, scale, precision, grad_img, grad_roots,
                                      reinterpret_cast<cudaStream_t>(stream));
 }
 

@@ -136,6 +136,103 @@ __global__ void __launch_bounds__(256) splat_backward_kernel(const double2 *__re
     }
 }
 
+// ---- FP32 variant: the stencil arithmetic on the FP32 pipe -----------------
+// The same stencil, recurrence and tests in float (about 1e-6 relative on
+// the image and the gradient); the root's pixel coordinates u, v stay FP64
+// (two FP64 operations per root), the image stays float64: weights are
+// widened and the image gradient narrowed with integer bit operations (a
+// conversion instruction would issue to the FP64 pipe again), and the atomic
+// adds are FP64 additions in L2, not on the SM's FP64 pipe.
+struct SplatGeomF {
+    float sigma, inv_2s2, inv_s2, step, cut, scale, cut_s;
+};
+
+__device__ __forceinline__ int splat_axis_f(const SplatGeomF &g, double u, int n_pix, int &i0, float (&e)[SPLAT_K],
+                                            float &d0)
+{
+    if (!finite_bits(u)) return 0;
+    double a = ceil(u - 0.5 - 3.0 * (double)g.sigma), b = floor(u - 0.5 + 3.0 * (double)g.sigma);
+    a = fmax(a, 0.0);
+    b = fmin(b, n_pix - 1.0);
+    if (!(a <= b)) return 0;
+    i0 = (int)a;
+    const int cnt = (int)(b - a) + 1;
+    d0 = d2f(u - (a + 0.5));
+    float ek = __expf(-d0 * d0 * g.inv_2s2);
+    float q = __expf((2.0f * d0 - 1.0f) * g.inv_2s2);
+#pragma unroll
+    for (int k = 0; k < SPLAT_K; ++k) {
+        e[k] = ek;
+        ek *= q;
+        q *= g.step;
+    }
+    return cnt;
+}
+
+__global__ void __launch_bounds__(256) splat_kernel_f32(const double2 *__restrict__ roots, int64_t n, SplatGeom g,
+                                                        SplatGeomF gf, double *img)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const double2 z = __ldg(roots + j);
+        const double u = (z.x - g.xmin) / g.px, v = (g.ymax - z.y) / g.py;
+        float ex[SPLAT_K], ey[SPLAT_K], dx0, dy0;
+        int x0, y0;
+        const int nx = splat_axis_f(gf, u, g.W, x0, ex, dx0);
+        const int ny = nx ? splat_axis_f(gf, v, g.H, y0, ey, dy0) : 0;
+        if (!ny) continue;
+#pragma unroll
+        for (int ky = 0; ky < SPLAT_K; ++ky) {
+            if (ky >= ny) break;
+            double *row = img + (size_t)(y0 + ky) * g.W + x0;
+            const float eys = ey[ky] * gf.scale;
+#pragma unroll
+            for (int kx = 0; kx < SPLAT_K; ++kx) {
+                const float w = fmaf(ex[kx], eys, -gf.cut_s);
+                if (kx < nx && __float_as_int(w) > 0) atomicAdd(row + kx, f2d(w));
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) splat_backward_kernel_f32(const double2 *__restrict__ roots, int64_t n,
+                                                                 SplatGeom g, SplatGeomF gf,
+                                                                 const double *__restrict__ G, double2 *grad)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const double2 z = __ldg(roots + j);
+        const double u = (z.x - g.xmin) / g.px, v = (g.ymax - z.y) / g.py;
+        float ex[SPLAT_K], ey[SPLAT_K], dx0, dy0;
+        int x0, y0;
+        const int nx = splat_axis_f(gf, u, g.W, x0, ex, dx0);
+        const int ny = nx ? splat_axis_f(gf, v, g.H, y0, ey, dy0) : 0;
+        float gu = 0.0f, gv = 0.0f;
+        if (ny) {
+            const int cut_bits = __float_as_int(gf.cut);
+#pragma unroll
+            for (int ky = 0; ky < SPLAT_K; ++ky) {
+                if (ky >= ny) break;
+                const double *row = G + (size_t)(y0 + ky) * g.W + x0;
+                float su = 0.0f, sv = 0.0f;
+#pragma unroll
+                for (int kx = 0; kx < SPLAT_K; ++kx) {
+                    const float e = ex[kx] * ey[ky];
+                    if (kx < nx && __float_as_int(e) > cut_bits) {
+                        const float ge = d2f(__ldg(row + kx)) * e;
+                        su = fmaf(ge, dx0 - (float)kx, su);
+                        sv += ge;
+                    }
+                }
+                gu += su;
+                gv = fmaf(sv, dy0 - (float)ky, gv);
+            }
+        }
+        const float k = -gf.scale * gf.inv_s2;
+        grad[j] = make_double2(f2d(k * gu) / g.px, -f2d(k * gv) / g.py);
+    }
+}
+
 static SplatGeom splat_geom(const rd_window &w, int W, int H, double sigma, double scale)
 {
     SplatGeom g;
@@ -163,19 +260,43 @@ static unsigned splat_grid(int64_t n)
     return (unsigned)(ctas < 1 ? 1 : ctas);
 }
 
-int launch_splat(const double *roots, int64_t n, const rd_window &w, int W, int H, double sigma, double scale,
-                 double *img, cudaStream_t st)
+static SplatGeomF splat_geom_f(const SplatGeom &g)
 {
-    splat_kernel<<<splat_grid(n), 256, 0, st>>>(reinterpret_cast<const double2 *>(roots), n,
-                                                splat_geom(w, W, H, sigma, scale), img);
+    SplatGeomF f;
+    f.sigma = (float)g.sigma;
+    f.inv_2s2 = (float)g.inv_2s2;
+    f.inv_s2 = (float)g.inv_s2;
+    f.step = (float)g.step;
+    f.cut = (float)g.cut;
+    f.scale = (float)g.scale;
+    f.cut_s = (float)g.cut_s;
+    return f;
+}
+
+int launch_splat(const double *roots, int64_t n, const rd_window &w, int W, int H, double sigma, double scale,
+                 int precision, double *img, cudaStream_t st)
+{
+    const SplatGeom g = splat_geom(w, W, H, sigma, scale);
+    if (precision == RD_SPLAT_FP32) {
+        splat_kernel_f32<<<splat_grid(n), 256, 0, st>>>(reinterpret_cast<const double2 *>(roots), n, g,
+                                                        splat_geom_f(g), img);
+        return rd_check_launch("splat_kernel_f32");
+    }
+    splat_kernel<<<splat_grid(n), 256, 0, st>>>(reinterpret_cast<const double2 *>(roots), n, g, img);
     return rd_check_launch("splat_kernel");
 }
 
 int launch_splat_backward(const double *roots, int64_t n, const rd_window &w, int W, int H, double sigma,
-                          double scale, const double *G, double *grad, cudaStream_t st)
+                          double scale, int precision, const double *G, double *grad, cudaStream_t st)
 {
-    splat_backward_kernel<<<splat_grid(n), 256, 0, st>>>(reinterpret_cast<const double2 *>(roots), n,
-                                                         splat_geom(w, W, H, sigma, scale), G,
+    const SplatGeom g = splat_geom(w, W, H, sigma, scale);
+    if (precision == RD_SPLAT_FP32) {
+        splat_backward_kernel_f32<<<splat_grid(n), 256, 0, st>>>(reinterpret_cast<const double2 *>(roots), n, g,
+                                                                 splat_geom_f(g), G,
+                                                                 reinterpret_cast<double2 *>(grad));
+        return rd_check_launch("splat_backward_kernel_f32");
+    }
+    splat_backward_kernel<<<splat_grid(n), 256, 0, st>>>(reinterpret_cast<const double2 *>(roots), n, g, G,
                                                          reinterpret_cast<double2 *>(grad));
     return rd_check_launch("splat_backward_kernel");
 }

@@ -30,39 +30,44 @@ def _stream():
     return torch.cuda.current_stream().cuda_stream
 
 
+PRECISIONS = {"fp64": N.SPLAT_FP64, "fp32": N.SPLAT_FP32}
+
+
 class SplatFn(torch.autograd.Function):
     """img [H, W] float64 = scale * sum over roots of the truncated bump."""
 
     @staticmethod
-    def forward(ctx, roots, window, W, H, sigma, scale):
+    def forward(ctx, roots, window, W, H, sigma, scale, precision):
         z = roots.detach().reshape(-1).contiguous()
         img = torch.zeros((H, W), dtype=torch.float64, device=z.device)
         win = N.Window(*window)
-        N.call("rd_splat", z.data_ptr(), z.numel(), win, W, H, float(sigma), float(scale), img.data_ptr(),
-               _stream())
+        N.call("rd_splat", z.data_ptr(), z.numel(), win, W, H, float(sigma), float(scale), precision,
+               img.data_ptr(), _stream())
         ctx.save_for_backward(z)
-        ctx.args = (win, W, H, float(sigma), float(scale), roots.shape)
+        ctx.args = (win, W, H, float(sigma), float(scale), precision, roots.shape)
         return img
 
     @staticmethod
     def backward(ctx, grad_img):
         (z,) = ctx.saved_tensors
-        win, W, H, sigma, scale, shape = ctx.args
+        win, W, H, sigma, scale, precision, shape = ctx.args
         g = grad_img.detach().to(torch.float64).contiguous()
         out = torch.empty_like(z)
-        N.call("rd_splat_backward", z.data_ptr(), z.numel(), win, W, H, sigma, scale, g.data_ptr(),
+        N.call("rd_splat_backward", z.data_ptr(), z.numel(), win, W, H, sigma, scale, precision, g.data_ptr(),
                out.data_ptr(), _stream())
-        return out.reshape(shape), None, None, None, None, None
+        return out.reshape(shape), None, None, None, None, None, None
 
 
 def splat(roots: torch.Tensor, window=WINDOW, W: int = W_IMG, H: int = H_IMG, sigma: float = SIGMA,
-          n_norm: int | None = None) -> torch.Tensor:
+          n_norm: int | None = None, precision: str = "fp64") -> torch.Tensor:
     """Soft density image [H, W] (float64) of the complex128 CUDA roots (any
-    shape), normalised by n_norm (default: the number of roots)."""
+    shape), normalised by n_norm (default: the number of roots). precision
+    "fp64" (~1e-14) or "fp32" (the stencil on the FP32 pipe, ~1e-6)."""
     if not (isinstance(roots, torch.Tensor) and roots.is_cuda and roots.dtype == torch.complex128):
         raise ValueError("splat needs a complex128 CUDA tensor of roots")
     norm = float(n_norm if n_norm is not None else roots.numel())
-    return SplatFn.apply(roots, tuple(float(v) for v in window), int(W), int(H), float(sigma), 1.0 / norm)
+    return SplatFn.apply(roots, tuple(float(v) for v in window), int(W), int(H), float(sigma), 1.0 / norm,
+                         PRECISIONS[precision])
 
 
 def loss(roots: torch.Tensor, target: torch.Tensor, lam: float = 1.0, global_sum=None, **kw) -> torch.Tensor:

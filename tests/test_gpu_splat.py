@@ -29,31 +29,49 @@ def _roots(seed, n):
     return z
 
 
+# (precision, relative tolerance on the image, on the gradient)
+PRECISION = [(api.N.SPLAT_FP64, 1e-13, 1e-12), (api.N.SPLAT_FP32, 2e-6, 2e-5)]
+
+
+@pytest.mark.parametrize("precision,tol_img,tol_grad", PRECISION)
 @pytest.mark.parametrize("sigma,W,H", [(1.5, 256, 144), (1.0, 320, 180), (2.0, 97, 61)])
-def test_splat_forward_matches_oracle(dev, orc, sigma, W, H):
+def test_splat_forward_matches_oracle(dev, orc, sigma, W, H, precision, tol_img, tol_grad):
     z = _roots(3, 200003)
     img = torch.zeros((H, W), dtype=torch.float64, device=dev)
     api.N.call("rd_splat", api._ptr(torch.from_numpy(z).to(dev)), z.size, api.N.Window(*SP.WINDOW), W, H, sigma,
-               0.25, api._ptr(img), api._stream())
+               0.25, precision, api._ptr(img), api._stream())
     torch.cuda.synchronize()
     ref = orc.splat(z, SP.WINDOW, W, H, sigma, 0.25)
-    assert np.abs(img.cpu().numpy() - ref).max() <= 1e-13 * ref.max()
-    # pixels the oracle leaves at zero stay zero (nothing beyond 3 sigma)
-    assert not img.cpu().numpy()[ref == 0].any()
+    got = img.cpu().numpy()
+    assert np.abs(got - ref).max() <= tol_img * ref.max()
+    # pixels the oracle leaves at zero stay zero (nothing beyond 3 sigma); in
+    # FP32 a pixel centre on the 3-sigma circle may take a weight of ~1e-7
+    if precision == api.N.SPLAT_FP64:
+        assert not got[ref == 0].any()
+    else:
+        assert np.abs(got[ref == 0]).max(initial=0.0) <= tol_img * ref.max()
 
 
+@pytest.mark.parametrize("precision,tol_img,tol_grad", PRECISION)
 @pytest.mark.parametrize("sigma,W,H", [(1.5, 256, 144), (2.0, 97, 61)])
-def test_splat_backward_matches_oracle(dev, orc, sigma, W, H):
+def test_splat_backward_matches_oracle(dev, orc, sigma, W, H, precision, tol_img, tol_grad):
     z = _roots(4, 100003)
     G = np.random.default_rng(5).standard_normal((H, W))
     zt = torch.from_numpy(z).to(dev)
     out = torch.empty_like(zt)
-    api.N.call("rd_splat_backward", api._ptr(zt), z.size, api.N.Window(*SP.WINDOW), W, H, sigma, 0.5,
+    api.N.call("rd_splat_backward", api._ptr(zt), z.size, api.N.Window(*SP.WINDOW), W, H, sigma, 0.5, precision,
                api._ptr(torch.from_numpy(G).to(dev)), api._ptr(out), api._stream())
     torch.cuda.synchronize()
     got = out.cpu().numpy()
     ref = orc.splat_grad(z, G, SP.WINDOW, W, H, sigma, 0.5)
-    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    if precision == api.N.SPLAT_FP64:
+        assert np.abs(got - ref).max() <= tol_grad * np.abs(ref).max()
+    else:
+        # FP32: a pixel whose centre lies within ~1e-6 of the 3-sigma circle can
+        # fall on the other side of the cut, where dw/du jumps by 0.02 of its
+        # peak; such roots are rare and their error bounded by that jump
+        err = np.abs(got - ref) / np.abs(ref).max()
+        assert np.mean(err <= tol_grad) > 0.9995 and err.max() <= 0.05, (np.mean(err <= tol_grad), err.max())
     assert got[0] == 0 and got[1] == 0  # non-finite roots
 
 

@@ -28,22 +28,24 @@ def test_splat_argument_validation_without_gpu():
         return rc, L.rd_last_error().decode()
 
     for sigma in (0.0, -1.0, 2.5, float("nan")):
-        rc, msg = err(L.rd_splat(fake, 4, w, 256, 144, sigma, 1.0, fake, null))
+        rc, msg = err(L.rd_splat(fake, 4, w, 256, 144, sigma, 1.0, 0, fake, null))
         assert rc == N.RD_EINVAL and "sigma" in msg
-    rc, msg = err(L.rd_splat(fake, 4, N.Window(1.0, -1.0, 0.0, 1.0), 256, 144, 1.5, 1.0, fake, null))
+    rc, msg = err(L.rd_splat(fake, 4, N.Window(1.0, -1.0, 0.0, 1.0), 256, 144, 1.5, 1.0, 0, fake, null))
     assert rc == N.RD_EINVAL and "window" in msg
-    rc, msg = err(L.rd_splat(fake, 4, w, 0, 144, 1.5, 1.0, fake, null))
+    rc, msg = err(L.rd_splat(fake, 4, w, 0, 144, 1.5, 1.0, 0, fake, null))
     assert rc == N.RD_EINVAL and "size" in msg
-    rc, msg = err(L.rd_splat(ctypes.c_void_p(8), 4, w, 256, 144, 1.5, 1.0, fake, null))
+    rc, msg = err(L.rd_splat(ctypes.c_void_p(8), 4, w, 256, 144, 1.5, 1.0, 0, fake, null))
     assert rc == N.RD_EINVAL and "roots" in msg
-    rc, msg = err(L.rd_splat(fake, 4, w, 256, 144, 1.5, 1.0, null, null))
+    rc, msg = err(L.rd_splat(fake, 4, w, 256, 144, 1.5, 1.0, 0, null, null))
     assert rc == N.RD_EINVAL and "img" in msg
-    rc, msg = err(L.rd_splat(fake, 4, w, 256, 144, 1.5, -1.0, fake, null))
+    rc, msg = err(L.rd_splat(fake, 4, w, 256, 144, 1.5, -1.0, 0, fake, null))
     assert rc == N.RD_EINVAL and "scale" in msg
-    rc, msg = err(L.rd_splat(fake, -1, w, 256, 144, 1.5, 1.0, fake, null))
+    rc, msg = err(L.rd_splat(fake, -1, w, 256, 144, 1.5, 1.0, 0, fake, null))
     assert rc == N.RD_EINVAL
-    assert L.rd_splat(null, 0, w, 256, 144, 1.5, 1.0, fake, null) == 0  # nothing to do
-    rc, msg = err(L.rd_splat_backward(fake, 4, w, 256, 144, 1.5, 1.0, null, fake, null))
+    assert L.rd_splat(null, 0, w, 256, 144, 1.5, 1.0, 0, fake, null) == 0  # nothing to do
+    rc, msg = err(L.rd_splat_backward(fake, 4, w, 256, 144, 1.5, 1.0, 0, null, fake, null))
     assert rc == N.RD_EINVAL and "grad_img" in msg
-    rc, msg = err(L.rd_splat_backward(fake, 4, w, 256, 144, 1.5, 1.0, fake, ctypes.c_void_p(8), null))
+    rc, msg = err(L.rd_splat_backward(fake, 4, w, 256, 144, 1.5, 1.0, 0, fake, ctypes.c_void_p(8), null))
     assert rc == N.RD_EINVAL and "grad_roots" in msg
+    rc, msg = err(L.rd_splat(fake, 4, w, 256, 144, 1.5, 1.0, 2, fake, null))
+    assert rc == N.RD_EINVAL and "precision" in msg
