@@ -930,7 +930,6 @@ def run_pipeline(args, rank, world, local_rank):
     clip = api.make_clip(c, rho, 480, 270, win)
     stream = torch.cuda.current_stream()
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    split = []
 
     def make_step(precision):
         def step():
