@@ -44,8 +44,9 @@ W_PIX, H_PIX = 1920, 1080
 E2E_CHUNK_LOG2 = 22
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "solve_mixed_littlewood_deg6.md")
 # files that define the timed solve kernel; the ncu traffic figure is valid only for this source
+# The solve kernel's code and its launch (the .cu files only dispatch to it).
 KERNEL_SOURCES = ["paper_2507_02164_gb300/csrc/rd_solve.cuh", "paper_2507_02164_gb300/csrc/rd_common.cuh",
-                  "paper_2507_02164_gb300/csrc/rd_solve_launch.cuh", "paper_2507_02164_gb300/csrc/rd_solve_mixed.cu"]
+                  "paper_2507_02164_gb300/csrc/rd_solve_launch.cuh"]
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 SMSPs x 32)
 FP64_FMA_PER_SM_CLK = 2   # FP64 FMA per SM per clock: 1.25 TFLOP/s / (152 SMs x 2 flop x 2.07 GHz)
 

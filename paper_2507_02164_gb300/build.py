@@ -46,6 +46,15 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+# Units that instantiate the register-resident solver for many degrees take
+# 10-25 s each, the rest 1-9 s: start them first so the pool ends together.
+HEAVY = ("rd_solve", "rd_uneven_bins", "rd_backward")
+
+
+def _compile_order(srcs):
+    return sorted(srcs, key=lambda s: (not os.path.basename(s).startswith(HEAVY), s))
+
+
 def _deps():
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
@@ -76,7 +85,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             sys.stderr.write(r.stderr)
         return obj
 
-    srcs = sources()
+    srcs = _compile_order(sources())
     with ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
     libdir = _cuda_lib_dir(nvcc)

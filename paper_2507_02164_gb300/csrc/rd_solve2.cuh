@@ -506,4 +506,44 @@ __global__ void __maxnreg__(two_lane_regs(N, MODE)) solve2_kernel(SolveArgs A)
     stats_end(S, A.stats);
 }
 
+// Launch of solve2_kernel for one degree (grid: enough warps for A.n / 16,
+// capped at ctas_per_sm per SM, or the occupancy limit when that is 0).
+template <int N, typename In, int MODE>
+static int launch_two(const SolveArgs &a, int block, int ctas_per_sm, cudaStream_t st)
+{
+    using T = typename std::conditional<MODE != MODE_PLAIN, float, double>::type;
+    auto kern = solve2_kernel<N, T, In, MODE>;
+    int per_sm = ctas_per_sm;
+    if (per_sm <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+    }
+    int64_t warps_needed = (a.n + 15) / 16;
+    int64_t ctas_needed = (warps_needed + (block / 32) - 1) / (block / 32);
+    int64_t grid = (int64_t)per_sm * rd_sm_count_cached();
+    if (grid > ctas_needed) grid = ctas_needed;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, block, 0, st>>>(a);
+    return rd_check_launch("solve2_kernel");
+}
+
+template <typename In, int MODE>
+static int launch_two_degree(int degree, const SolveArgs &a, int block, int ctas_per_sm, cudaStream_t st)
+{
+    switch (degree) {
+    case 2: return launch_two<2, In, MODE>(a, block, ctas_per_sm, st);
+    case 3: return launch_two<3, In, MODE>(a, block, ctas_per_sm, st);
+    case 4: return launch_two<4, In, MODE>(a, block, ctas_per_sm, st);
+    case 5: return launch_two<5, In, MODE>(a, block, ctas_per_sm, st);
+    case 6: return launch_two<6, In, MODE>(a, block, ctas_per_sm, st);
+    case 7: return launch_two<7, In, MODE>(a, block, ctas_per_sm, st);
+    case 8: return launch_two<8, In, MODE>(a, block, ctas_per_sm, st);
+    case 9: return launch_two<9, In, MODE>(a, block, ctas_per_sm, st);
+    case 10: return launch_two<10, In, MODE>(a, block, ctas_per_sm, st);
+    case 11: return launch_two<11, In, MODE>(a, block, ctas_per_sm, st);
+    case 12: return launch_two<12, In, MODE>(a, block, ctas_per_sm, st);
+    default: return rd_set_error(RD_EUNSUPPORTED, "two-lane solver built for degrees 2..12, not %d", degree);
+    }
+}
+
 }  // namespace rd

@@ -14,49 +14,12 @@
 // no synchronisation): clear header -> count -> scan -> pack -> one
 // persistent solve kernel per degree, largest degree first, each with its
 // own register allocation and its own task queue.
-#include "rd_solve2.cuh"
+#include "rd_uneven.cuh"
 
 namespace rd {
 
 int launch_clear(uint32_t *p, int64_t words, cudaStream_t st);
 
-constexpr int UNEVEN_MAX_DEG = 12;
-
-struct UnevenHeader {
-    uint32_t count[16];      // polynomials per degree
-    uint32_t cursor[16];     // pack cursors per degree
-    uint32_t poly_base[16];  // first slot of each degree's bin in perm
-    uint32_t head[16];       // task queue head of each degree's solve kernel
-    uint32_t bad;            // polynomials whose offsets disagree with their degree
-    uint32_t pad[3];
-    int64_t coef_base[16];   // first element of each degree's bin in the bins region
-};
-static_assert(sizeof(UnevenHeader) <= 512, "header must fit its 512-byte slot");
-
-constexpr size_t UNEVEN_HEADER_BYTES = 512;
-
-__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-struct UnevenLayout {
-    UnevenHeader *hdr;
-    uint32_t *perm;
-    char *bins;
-};
-
-inline size_t uneven_bytes(int64_t n, int64_t n_coeffs, size_t elem)
-{
-    return UNEVEN_HEADER_BYTES + align256((size_t)n * 4) + align256((size_t)n_coeffs * elem);
-}
-
-inline UnevenLayout uneven_layout(void *ws, int64_t n)
-{
-    char *p = reinterpret_cast<char *>(ws);
-    UnevenLayout L;
-    L.hdr = reinterpret_cast<UnevenHeader *>(p);
-    L.perm = reinterpret_cast<uint32_t *>(p + UNEVEN_HEADER_BYTES);
-    L.bins = p + UNEVEN_HEADER_BYTES + align256((size_t)n * 4);
-    return L;
-}
 
 struct UnevenArgs {
     const uint8_t *degrees;
@@ -180,97 +143,6 @@ __global__ void __launch_bounds__(256) uneven_pack_kernel(UnevenArgs U, const E 
     }
 }
 
-// Persistent solver for the degree-N bin: each warp takes the next task of
-// the bin's queue (task = 32 consecutive slots) until the queue is empty.
-// One kernel per degree keeps each degree's own register allocation.
-template <int N, typename In, int MODE>
-__global__ void __launch_bounds__(256, (MODE != MODE_PLAIN && N <= 6) ? 2 : 1)
-    uneven_solve_kernel(SolveArgs A, UnevenHeader *hdr, const uint32_t *perm, const char *bins, const int64_t *offsets)
-{
-    using T = typename std::conditional<MODE != MODE_PLAIN, float, double>::type;
-    __shared__ unsigned long long acc[ST_WORDS];
-    const CtaStats S = stats_begin(acc, A.stats);
-    const int lane = threadIdx.x & 31;
-    const int64_t cnt = hdr->count[N];
-    const unsigned tasks = (unsigned)((cnt + 31) / 32);
-    const PackedMap map{{}, perm + hdr->poly_base[N], offsets};
-    const void *base = bins + (size_t)hdr->coef_base[N] * sizeof(In);
-    for (;;) {
-        unsigned t = 0;
-        if (lane == 0) t = atomicAdd(&hdr->head[N], 1u);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= tasks) break;
-        solve_warp<N, T, In, MODE>(A, base, cnt, (int64_t)t * 32, map, S);
-    }
-    stats_end(S, A.stats);
-}
-
-// The same with two lanes per polynomial (rd_solve2.cuh): tasks of 16 slots.
-template <int N, typename In, int MODE>
-__global__ void __maxnreg__(two_lane_regs(N, MODE))
-    uneven_solve2_kernel(SolveArgs A, UnevenHeader *hdr, const uint32_t *perm, const char *bins, const int64_t *offsets)
-{
-    using T = typename std::conditional<MODE != MODE_PLAIN, float, double>::type;
-    __shared__ unsigned long long acc[ST_WORDS];
-    const CtaStats S = stats_begin(acc, A.stats);
-    const int lane = threadIdx.x & 31;
-    const int64_t cnt = hdr->count[N];
-    const unsigned tasks = (unsigned)((cnt + 15) / 16);
-    const PackedMap map{{}, perm + hdr->poly_base[N], offsets};
-    const void *base = bins + (size_t)hdr->coef_base[N] * sizeof(In);
-    for (;;) {
-        unsigned t = 0;
-        if (lane == 0) t = atomicAdd(&hdr->head[N], 1u);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= tasks) break;
-        solve_warp2<N, T, In, MODE>(A, base, cnt, (int64_t)t * 16, map, S);
-    }
-    stats_end(S, A.stats);
-}
-
-int lanes_for(int degree, bool mixed, int polish_mode, int requested);
-
-template <typename K>
-static int launch_persistent(K kern, const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, int block,
-                             int ctas_per_sm, cudaStream_t st, const char *what)
-{
-    int per_sm = ctas_per_sm;
-    if (per_sm <= 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0) != cudaSuccess || per_sm < 1)
-            per_sm = 1;
-    }
-    int grid = per_sm * rd_sm_count_cached();
-    kern<<<grid, block, 0, st>>>(a, L.hdr, L.perm, L.bins, offsets);
-    return rd_check_launch(what);
-}
-
-template <int N, typename In, int MODE>
-static int launch_degree_bin(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, int block,
-                             int ctas_per_sm, int lanes, cudaStream_t st)
-{
-    if constexpr (N >= 2 && MODE != MODE_MIXED_DF) {
-        if (lanes_for(N, MODE != MODE_PLAIN, a.polish_mode, lanes) == 2)
-            return launch_persistent(uneven_solve2_kernel<N, In, MODE>, a, L, offsets, block, ctas_per_sm, st,
-                                     "uneven_solve2_kernel");
-    }
-    return launch_persistent(uneven_solve_kernel<N, In, MODE>, a, L, offsets, block, ctas_per_sm, st,
-                             "uneven_solve_kernel");
-}
-
-// Degree bins largest first: the most expensive work starts first.
-template <typename In, int MODE>
-static int launch_bins(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, const int *block,
-                       const int *cps, const int *lanes, cudaStream_t st)
-{
-    int rc = 0;
-#define RD_BIN(D) \
-    if (!rc) rc = launch_degree_bin<D, In, MODE>(a, L, offsets, block[D], cps[D], lanes[D], st);
-    RD_BIN(12) RD_BIN(11) RD_BIN(10) RD_BIN(9) RD_BIN(8) RD_BIN(7)
-    RD_BIN(6) RD_BIN(5) RD_BIN(4) RD_BIN(3) RD_BIN(2) RD_BIN(1)
-#undef RD_BIN
-    return rc;
-}
-
 size_t uneven_workspace_bytes(int64_t n, int64_t n_coeffs, rd_dtype dt)
 {
     return uneven_bytes(n, n_coeffs, dt == RD_C64 ? 8 : 16);
@@ -302,13 +174,13 @@ int launch_uneven(const SolveArgs &a, rd_dtype dt, const uint8_t *degrees, const
     if ((rc = rd_check_launch("uneven_pack_kernel"))) return rc;
     const int mode = !mixed ? MODE_PLAIN : (a.polish_mode == RD_POLISH_DF ? MODE_MIXED_DF : MODE_MIXED_FP64);
     if (dt == RD_C64) {
-        if (mode == MODE_PLAIN) return launch_bins<float2, MODE_PLAIN>(a, L, offsets, block, cps, lanes, st);
-        if (mode == MODE_MIXED_DF) return launch_bins<float2, MODE_MIXED_DF>(a, L, offsets, block, cps, lanes, st);
-        return launch_bins<float2, MODE_MIXED_FP64>(a, L, offsets, block, cps, lanes, st);
+        if (mode == MODE_PLAIN) return launch_uneven_bins<float2, MODE_PLAIN>(a, L, offsets, block, cps, lanes, st);
+        if (mode == MODE_MIXED_DF) return launch_uneven_bins<float2, MODE_MIXED_DF>(a, L, offsets, block, cps, lanes, st);
+        return launch_uneven_bins<float2, MODE_MIXED_FP64>(a, L, offsets, block, cps, lanes, st);
     }
-    if (mode == MODE_PLAIN) return launch_bins<double2, MODE_PLAIN>(a, L, offsets, block, cps, lanes, st);
-    if (mode == MODE_MIXED_DF) return launch_bins<double2, MODE_MIXED_DF>(a, L, offsets, block, cps, lanes, st);
-    return launch_bins<double2, MODE_MIXED_FP64>(a, L, offsets, block, cps, lanes, st);
+    if (mode == MODE_PLAIN) return launch_uneven_bins<double2, MODE_PLAIN>(a, L, offsets, block, cps, lanes, st);
+    if (mode == MODE_MIXED_DF) return launch_uneven_bins<double2, MODE_MIXED_DF>(a, L, offsets, block, cps, lanes, st);
+    return launch_uneven_bins<double2, MODE_MIXED_FP64>(a, L, offsets, block, cps, lanes, st);
 }
 
 }  // namespace rd

@@ -1,0 +1,57 @@
+// rd_uneven.cuh -- workspace layout of the uneven-degree solve and the
+// per-bin launcher that rd_uneven.cu calls once the batch is binned. The
+// launcher is defined in rd_uneven_bins.cuh and instantiated once per
+// storage type and precision mode, each in a translation unit of its own
+// (rd_uneven_bins_*.cu), so that the 144 solve kernels compile in parallel.
+#pragma once
+
+#include "rd_solve.cuh"
+
+namespace rd {
+
+constexpr int UNEVEN_MAX_DEG = 12;
+
+struct UnevenHeader {
+    uint32_t count[16];      // polynomials per degree
+    uint32_t cursor[16];     // pack cursors per degree
+    uint32_t poly_base[16];  // first slot of each degree's bin in perm
+    uint32_t head[16];       // task queue head of each degree's solve kernel
+    uint32_t bad;            // polynomials whose offsets disagree with their degree
+    uint32_t pad[3];
+    int64_t coef_base[16];   // first element of each degree's bin in the bins region
+};
+static_assert(sizeof(UnevenHeader) <= 512, "header must fit its 512-byte slot");
+
+constexpr size_t UNEVEN_HEADER_BYTES = 512;
+
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct UnevenLayout {
+    UnevenHeader *hdr;
+    uint32_t *perm;
+    char *bins;
+};
+
+inline size_t uneven_bytes(int64_t n, int64_t n_coeffs, size_t elem)
+{
+    return UNEVEN_HEADER_BYTES + align256((size_t)n * 4) + align256((size_t)n_coeffs * elem);
+}
+
+inline UnevenLayout uneven_layout(void *ws, int64_t n)
+{
+    char *p = reinterpret_cast<char *>(ws);
+    UnevenLayout L;
+    L.hdr = reinterpret_cast<UnevenHeader *>(p);
+    L.perm = reinterpret_cast<uint32_t *>(p + UNEVEN_HEADER_BYTES);
+    L.bins = p + UNEVEN_HEADER_BYTES + align256((size_t)n * 4);
+    return L;
+}
+
+// Solve every degree bin of a packed batch (one persistent kernel per
+// degree, largest degree first) with the per-degree launch shapes
+// block[d], cps[d] and lanes per polynomial lanes[d].
+template <typename In, int MODE>
+int launch_uneven_bins(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, const int *block,
+                       const int *cps, const int *lanes, cudaStream_t st);
+
+}  // namespace rd

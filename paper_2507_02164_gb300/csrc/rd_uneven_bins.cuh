@@ -1,0 +1,110 @@
+// rd_uneven_bins.cuh -- the persistent solve kernels of the uneven-degree
+// path (one per degree, tasks pulled from the bin's atomic queue) and
+// launch_uneven_bins. Included only by the rd_uneven_bins_*.cu files, each
+// of which instantiates it for one storage type and precision mode.
+#pragma once
+
+#include "rd_solve2.cuh"
+#include "rd_uneven.cuh"
+
+namespace rd {
+
+
+// Persistent solver for the degree-N bin: each warp takes the next task of
+// the bin's queue (task = 32 consecutive slots) until the queue is empty.
+// One kernel per degree keeps each degree's own register allocation.
+template <int N, typename In, int MODE>
+__global__ void __launch_bounds__(256, (MODE != MODE_PLAIN && N <= 6) ? 2 : 1)
+    uneven_solve_kernel(SolveArgs A, UnevenHeader *hdr, const uint32_t *perm, const char *bins, const int64_t *offsets)
+{
+    using T = typename std::conditional<MODE != MODE_PLAIN, float, double>::type;
+    __shared__ unsigned long long acc[ST_WORDS];
+    const CtaStats S = stats_begin(acc, A.stats);
+    const int lane = threadIdx.x & 31;
+    const int64_t cnt = hdr->count[N];
+    const unsigned tasks = (unsigned)((cnt + 31) / 32);
+    const PackedMap map{{}, perm + hdr->poly_base[N], offsets};
+    const void *base = bins + (size_t)hdr->coef_base[N] * sizeof(In);
+    for (;;) {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(&hdr->head[N], 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= tasks) break;
+        solve_warp<N, T, In, MODE>(A, base, cnt, (int64_t)t * 32, map, S);
+    }
+    stats_end(S, A.stats);
+}
+
+// The same with two lanes per polynomial (rd_solve2.cuh): tasks of 16 slots.
+template <int N, typename In, int MODE>
+__global__ void __maxnreg__(two_lane_regs(N, MODE))
+    uneven_solve2_kernel(SolveArgs A, UnevenHeader *hdr, const uint32_t *perm, const char *bins, const int64_t *offsets)
+{
+    using T = typename std::conditional<MODE != MODE_PLAIN, float, double>::type;
+    __shared__ unsigned long long acc[ST_WORDS];
+    const CtaStats S = stats_begin(acc, A.stats);
+    const int lane = threadIdx.x & 31;
+    const int64_t cnt = hdr->count[N];
+    const unsigned tasks = (unsigned)((cnt + 15) / 16);
+    const PackedMap map{{}, perm + hdr->poly_base[N], offsets};
+    const void *base = bins + (size_t)hdr->coef_base[N] * sizeof(In);
+    for (;;) {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(&hdr->head[N], 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= tasks) break;
+        solve_warp2<N, T, In, MODE>(A, base, cnt, (int64_t)t * 16, map, S);
+    }
+    stats_end(S, A.stats);
+}
+
+int lanes_for(int degree, bool mixed, int polish_mode, int requested);
+
+template <typename K>
+static int launch_persistent(K kern, const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, int block,
+                             int ctas_per_sm, cudaStream_t st, const char *what)
+{
+    int per_sm = ctas_per_sm;
+    if (per_sm <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+    }
+    int grid = per_sm * rd_sm_count_cached();
+    kern<<<grid, block, 0, st>>>(a, L.hdr, L.perm, L.bins, offsets);
+    return rd_check_launch(what);
+}
+
+template <int N, typename In, int MODE>
+static int launch_degree_bin(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, int block,
+                             int ctas_per_sm, int lanes, cudaStream_t st)
+{
+    if constexpr (N >= 2 && MODE != MODE_MIXED_DF) {
+        if (lanes_for(N, MODE != MODE_PLAIN, a.polish_mode, lanes) == 2)
+            return launch_persistent(uneven_solve2_kernel<N, In, MODE>, a, L, offsets, block, ctas_per_sm, st,
+                                     "uneven_solve2_kernel");
+    }
+    return launch_persistent(uneven_solve_kernel<N, In, MODE>, a, L, offsets, block, ctas_per_sm, st,
+                             "uneven_solve_kernel");
+}
+
+// Degree bins largest first: the most expensive work starts first.
+template <typename In, int MODE>
+int launch_uneven_bins(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, const int *block,
+                       const int *cps, const int *lanes, cudaStream_t st)
+{
+    int rc = 0;
+#define RD_BIN(D) \
+    if (!rc) rc = launch_degree_bin<D, In, MODE>(a, L, offsets, block[D], cps[D], lanes[D], st);
+    RD_BIN(12) RD_BIN(11) RD_BIN(10) RD_BIN(9) RD_BIN(8) RD_BIN(7)
+    RD_BIN(6) RD_BIN(5) RD_BIN(4) RD_BIN(3) RD_BIN(2) RD_BIN(1)
+#undef RD_BIN
+    return rc;
+}
+
+}  // namespace rd
+
+#define RD_UNEVEN_BINS(IN, MODE)                                                                          \
+    namespace rd {                                                                                      \
+    template int launch_uneven_bins<IN, MODE>(const SolveArgs &, const UnevenLayout &, const int64_t *, \
+                                              const int *, const int *, const int *, cudaStream_t);     \
+    }
