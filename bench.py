@@ -42,11 +42,15 @@ DEGREE = 6
 WINDOW = (-2.0, 2.0, -1.125, 1.125)
 W_PIX, H_PIX = 1920, 1080
 E2E_CHUNK_LOG2 = 22
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "solve_mixed_littlewood_deg6.md")
-# files that define the timed solve kernel; the ncu traffic figure is valid only for this source
-# The solve kernel's code and its launch (the .cu files only dispatch to it).
-KERNEL_SOURCES = ["paper_2507_02164_gb300/csrc/rd_solve.cuh", "paper_2507_02164_gb300/csrc/rd_common.cuh",
-                  "paper_2507_02164_gb300/csrc/rd_solve_launch.cuh"]
+# ncu summary of each form of the headline kernel, with the source hash it was taken on
+PROFILE_SUMMARY = {"one_role": os.path.join(ROOT, "profiles", "solve_mixed_littlewood_deg6.md"),
+                   "ws": os.path.join(ROOT, "profiles", "solve_ws_littlewood_deg6.md")}
+# Each solve kernel's code and its launch (the .cu files only dispatch to them); an ncu
+# traffic figure is valid only for the source it was taken on.
+KERNEL_SOURCES = {"one_role": ["paper_2507_02164_gb300/csrc/rd_solve.cuh", "paper_2507_02164_gb300/csrc/rd_common.cuh",
+                               "paper_2507_02164_gb300/csrc/rd_solve_launch.cuh"],
+                  "ws": ["paper_2507_02164_gb300/csrc/rd_solve.cuh", "paper_2507_02164_gb300/csrc/rd_common.cuh",
+                         "paper_2507_02164_gb300/csrc/rd_solve_ws.cuh"]}
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 SMSPs x 32)
 FP64_FMA_PER_SM_CLK = 2   # FP64 FMA per SM per clock: 1.25 TFLOP/s / (152 SMs x 2 flop x 2.07 GHz)
 
@@ -69,24 +73,25 @@ def parse_args():
     return ap.parse_args()
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(form: str = "one_role") -> str:
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in KERNEL_SOURCES[form]:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """Per-launch DRAM bytes of the solve kernel from the committed ncu summary,
-    or None when the summary is missing or was taken on other kernel source."""
+def profiled_traffic(form: str = "one_role"):
+    """Per-launch DRAM bytes of the solve kernel (form "one_role" or "ws") from
+    the committed ncu summary, or None when the summary is missing or was
+    taken on other kernel source."""
     try:
-        text = open(PROFILE_SUMMARY).read()
+        text = open(PROFILE_SUMMARY[form]).read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
-    if not m or not s or s.group(1) != kernel_source_hash():
+    if not m or not s or s.group(1) != kernel_source_hash(form):
         return None
     return float(m.group(1))
 
@@ -309,10 +314,15 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     # after the device-resident leg (before the slower comparison legs)
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, coeffs, win, dev, world)
+        e2e = run_e2e(args, coeffs, win, dev, world, autotune.degree_params(tuned["mixed"], DEGREE, "mixed"))
 
-    # the double-float polish variant on the same batch (not the headline)
-    elapsed_df, kern_df, st_df, clk_df = timed_leg("mixed", polish_mode=api.N.POLISH_DF)
+    # the same batch with every warp sweeping and then polishing its own
+    # polynomials (the fastest such shape), and the double-float polish
+    # variant, which has only that form (neither is the headline)
+    one = tuned["mixed"]["degrees"][str(DEGREE)]["one_role"]
+    one_shape = dict(block=one["block"], ctas_per_sm=one["ctas_per_sm"], lanes=one["lanes"], polish_warps=0)
+    elapsed_or, kern_or, st_or, clk_or = timed_leg("mixed", **one_shape)
+    elapsed_df, kern_df, st_df, clk_df = timed_leg("mixed", polish_mode=api.N.POLISH_DF, **one_shape)
 
     plain = None
     if not args.no_plain:
@@ -343,9 +353,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     f32, f64 = algorithmic_flops(st_mx)
     t_k = kern_mx * 1e-3
     frac32, frac64 = f32 / p32 / t_k, f64 / p64 / t_k
-    traffic = profiled_traffic()
+    traffic = profiled_traffic("ws" if tuned["mixed"]["degrees"][str(DEGREE)].get("polish_warps", 0) else "one_role")
+    pw = tuned["mixed"]["degrees"][str(DEGREE)].get("polish_warps", 0)
+    blk = tuned["mixed"]["degrees"][str(DEGREE)]["block"]
+    kernel_name = (f"rd::solve_ws_kernel<6, float2> (warp-specialised: {pw} polish warps of {blk // 32})" if pw
+                   else "rd::solve_kernel<6, float, float2, MIXED>")
     roofline = {
-        "bound": "alu", "kernel": "rd::solve_kernel<6, float, float2, MIXED>",
+        "bound": "alu", "kernel": kernel_name,
         "achieved": (f32 + f64 * p32 / p64) / t_k / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
         "frac": frac32 + frac64, "traffic": traffic,
         "note": "FP32-equivalent: FP64 flops weighted by the FP32/FP64 peak ratio; frac = fp32_frac + fp64_frac",
@@ -373,6 +387,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                   "paper_equiv_gflops": value * 41.9e3 / 1e9,
                   "equiv_qr_sweeps_per_s": value * st_mx["sweeps"] / max(1, st_mx["polys"])},
     }
+    o32, o64 = algorithmic_flops(st_or)
+    line["mixed_one_role"] = {
+        "value": polys_total / (elapsed_or * 1e-3), "unit": UNIT, "ms_per_step": elapsed_or / args.steps,
+        "kernel_ms": kern_or, "fp32_frac": o32 / p32 / (kern_or * 1e-3), "fp64_frac": o64 / p64 / (kern_or * 1e-3),
+        "shape": one_shape, "identical_histogram_counters": st_or == st_mx,
+        "note": "rd::solve_kernel: every warp sweeps and then polishes its own 32 polynomials", "clocks": clk_or}
     g32, g64 = algorithmic_flops(st_df)
     t_df = kern_df * 1e-3
     line["mixed_df_polish"] = {
@@ -445,13 +465,13 @@ def release_pinned(torch):
         pass
 
 
-def run_e2e(args, coeffs_dev, win, dev, world):
+def run_e2e(args, coeffs_dev, win, dev, world, p):
     """Same metric through the public API with the inputs in page-locked host
-    memory: each step, rd_roots_density reads the 56 B of every polynomial
-    straight from host memory across the host link while it solves (the
-    buffer is mapped into the device address space; zero copy), then the
-    histogram and counters are read back to the host. The chunked variant
-    with explicit copies on a copy stream is measured beside it."""
+    memory: each step, rd_roots_density (launch shape p) reads the 56 B of
+    every polynomial straight from host memory across the host link while it
+    solves (the buffer is mapped into the device address space; zero copy),
+    then the histogram and counters are read back to the host. The chunked
+    variant with explicit copies on a copy stream is measured beside it."""
     import torch
 
     from paper_2507_02164_gb300 import api, dist as D
@@ -466,7 +486,6 @@ def run_e2e(args, coeffs_dev, win, dev, world):
     hist_h = torch.empty_like(hist, device="cpu").pin_memory()
     stats_h = torch.empty_like(stats, device="cpu").pin_memory()
     comp = torch.cuda.current_stream()
-    p = api.params("mixed")
 
     def step():
         api.hist_clear(hist)
@@ -496,11 +515,11 @@ def run_e2e(args, coeffs_dev, win, dev, world):
            "clocks": clk.summary()}
     del host
     release_pinned(torch)
-    out["copy_engine"] = run_e2e_copies(args, coeffs_dev, win, dev, world)
+    out["copy_engine"] = run_e2e_copies(args, coeffs_dev, win, dev, world, p)
     return out
 
 
-def run_e2e_copies(args, coeffs_dev, win, dev, world):
+def run_e2e_copies(args, coeffs_dev, win, dev, world, p):
     """Same metric through the public API with the inputs in pinned host memory:
     per step, the chunks are copied host-to-device on a copy stream while the
     previous chunk is solved, and the histogram and counters are read back."""
@@ -525,7 +544,6 @@ def run_e2e_copies(args, coeffs_dev, win, dev, world):
     stats_h = torch.empty_like(stats, device="cpu").pin_memory()
     comp = torch.cuda.current_stream()
     copy = torch.cuda.Stream(device=dev)
-    p = api.params("mixed")
     freed = [torch.cuda.Event() for _ in range(2)]
     loaded = [torch.cuda.Event() for _ in range(2)]
 

@@ -78,6 +78,16 @@ typedef struct {
                               exchanged by warp shuffles; degree >= 2 and RD_POLISH_FP64
                               only, degree 1 always runs one lane). Two lanes measured
                               slower on GB300 at degrees 6..12; the autotuner times both   */
+    int32_t polish_warps;  /* RD_MIXED, RD_POLISH_FP64, one lane, rd_roots_batched and
+                              rd_roots_density: 0 = every warp sweeps and then polishes its
+                              own 32 polynomials; P > 0 = warp-specialised CTAs, P warps of
+                              each polish, check, store and bin what the other block/32 - P
+                              warps sweep, handed over through a shared-memory ring, so the
+                              FP64 pipe (polish) and the FP32 pipe (sweeps) work at the same
+                              time. block may then be up to 512 (degrees <= 6) or 256
+                              (degrees >= 7). Same roots bit for bit                       */
+    int32_t ring_slots;    /* polish_warps > 0: ring slots of 32 polynomials per CTA (2..64);
+                              0 = 2 x block/32                                             */
 } rd_params;
 
 /* RD_POLISH_FP64: every Newton step evaluates p(z) by FP64 Horner.
@@ -117,6 +127,9 @@ typedef struct {
     uint64_t clipped;        /* roots dropped by a tile clip                             */
     uint64_t flops_fp32;     /* algorithmic FP32 flops of the solve (see below)          */
     uint64_t flops_fp64;     /* algorithmic FP64 flops of the solve                      */
+    uint64_t wait_timeouts;  /* polynomials the warp-specialised solver abandoned after a
+                                bounded wait (status REJECTED, no roots written or binned);
+                                0 unless its hand-off between warps failed                */
 } rd_stats;
 /* Algorithmic flop convention (the method's own work, not what the hardware
  * executes): a sweep at active size m costs 20 (m(m+1) - 2) for its rotated
@@ -162,6 +175,18 @@ int rd_device_sm_count(void);
 int rd_roots_batched(const void *coeffs, rd_dtype dtype, int degree, int64_t n, rd_mode mode,
                      const rd_params *params, double *roots, uint8_t *status, rd_stats *stats,
                      void *stream);
+
+/* ---- self-test of the warp-specialised solver's bounded waits ------------
+ * Runs the degree-6 complex64 warp-specialised kernel (params.polish_warps)
+ * on coeffs [7][n] with every warp of its CTAs in the polish role, so that no
+ * ring slot is ever filled: each CTA's first wait runs out after 2 s and sets
+ * the CTA's abort flag, no later wait starts, and the kernel returns with
+ * status[i] = RD_STATUS_REJECTED for every i < n and stats->wait_timeouts and
+ * stats->status[RD_STATUS_REJECTED] increased by n. It exercises the failure
+ * path of the hand-off without a GPU fault. 1 <= n <= 1024 (one wave of
+ * CTAs: about 2 s); coeffs, status and stats are device pointers (required).
+ * Returns RD_EINVAL on bad arguments; does not synchronise. */
+int rd_ws_selftest_timeout(const void *coeffs, int64_t n, uint8_t *status, rd_stats *stats, void *stream);
 
 /* ---- fused roots + root-density histogram ---------------------------------
  * rd_roots_batched, then every root is binned into hist (+=, uint32, row-major

@@ -26,7 +26,8 @@ class Params(ctypes.Structure):
                 ("residual_tol", ctypes.c_double), ("collapse_tol", ctypes.c_double),
                 ("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("polish_extra", ctypes.c_int32), ("fixed_sweeps", ctypes.c_int32),
-                ("polish_mode", ctypes.c_int32), ("lanes", ctypes.c_int32)]
+                ("polish_mode", ctypes.c_int32), ("lanes", ctypes.c_int32),
+                ("polish_warps", ctypes.c_int32), ("ring_slots", ctypes.c_int32)]
 
 
 class Window(ctypes.Structure):
@@ -55,13 +56,14 @@ SPLAT_FP64, SPLAT_FP32 = 0, 1
 
 STATS_FIELDS = ("polys", "status_ok", "status_not_converged", "status_rejected", "status_degenerate",
                 "sweeps", "pair_updates", "rotations", "newton_steps", "binned", "out_of_window", "clipped",
-                "flops_fp32", "flops_fp64")
+                "flops_fp32", "flops_fp64", "wait_timeouts")
 STATS_WORDS = len(STATS_FIELDS)  # uint64 words of rd_stats
 STATIC_SCRATCH_BYTES = 32 * 1024 * 1024  # RD_STATIC_SCRATCH_BYTES
 
 # entry point -> (restype, argtypes); every name here is declared in include/rootdensity.h
 P, I32, I64, F64, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
 SIGNATURES = {
+    "rd_ws_selftest_timeout": (I32, [P, I64, P, P, P]),
     "rd_abi_version": (I32, []),
     "rd_pointer_is_device_accessible": (I32, [P]),
     "rd_last_error": (ctypes.c_char_p, []),

@@ -14,6 +14,9 @@ namespace rd {
 int launch_solve_mixed(int degree, rd_dtype dt, const SolveArgs &a, int block, int ctas_per_sm, cudaStream_t st);
 int launch_solve_plain(int degree, rd_dtype dt, const SolveArgs &a, int block, int ctas_per_sm, cudaStream_t st);
 int launch_solve2(int degree, rd_dtype dt, bool mixed, const SolveArgs &a, int block, int ctas_per_sm, cudaStream_t st);
+int launch_solve_ws(int degree, rd_dtype dt, const SolveArgs &a, int block, int ctas_per_sm, int polish_warps,
+                    int ring_slots, cudaStream_t st);
+int launch_solve_ws_selftest(const SolveArgs &a, cudaStream_t st);
 int lanes_for(int degree, bool mixed, int polish_mode, int requested);
 int launch_density(const double *roots, int64_t n, const Binner &bin, uint32_t *hist, rd_stats *stats,
                    cudaStream_t st);
@@ -100,8 +103,12 @@ int check_params(const rd_params &p)
     if (p.polish_steps < 0 || p.polish_steps > 8) return rd_set_error(RD_EINVAL, "params.polish_steps must be in [0, 8]");
     if (!std::isfinite(p.residual_tol) || !std::isfinite(p.collapse_tol) || p.collapse_tol < 0)
         return rd_set_error(RD_EINVAL, "params.residual_tol / collapse_tol invalid");
-    if (p.block != 0 && (p.block < 32 || p.block > 256 || p.block % 32 != 0))
-        return rd_set_error(RD_EINVAL, "params.block must be 0 or a multiple of 32 in [32, 256]");
+    if (p.polish_warps < 0 || p.polish_warps > 15) return rd_set_error(RD_EINVAL, "params.polish_warps must be in [0, 15]");
+    if (p.ring_slots != 0 && (p.ring_slots < 2 || p.ring_slots > 64))
+        return rd_set_error(RD_EINVAL, "params.ring_slots must be 0 or in [2, 64]");
+    const int block_max = p.polish_warps > 0 ? 512 : 256;
+    if (p.block != 0 && (p.block < 32 || p.block > block_max || p.block % 32 != 0))
+        return rd_set_error(RD_EINVAL, "params.block must be 0 or a multiple of 32 in [32, %d]", block_max);
     if (p.ctas_per_sm < 0 || p.ctas_per_sm > 64) return rd_set_error(RD_EINVAL, "params.ctas_per_sm must be in [0, 64]");
     if (p.polish_extra < 0 || p.polish_extra > 16) return rd_set_error(RD_EINVAL, "params.polish_extra must be in [0, 16]");
     if (p.polish_mode != RD_POLISH_FP64 && p.polish_mode != RD_POLISH_DF)
@@ -111,6 +118,8 @@ int check_params(const rd_params &p)
         return rd_set_error(RD_EINVAL, "params.lanes = 2 needs polish_mode RD_POLISH_FP64");
     if (p.fixed_sweeps < 0 || p.fixed_sweeps > p.max_iters)
         return rd_set_error(RD_EINVAL, "params.fixed_sweeps must be in [0, max_iters]");
+    if (p.polish_warps > 0 && (p.polish_mode != RD_POLISH_FP64 || p.lanes == 2))
+        return rd_set_error(RD_EINVAL, "params.polish_warps > 0 needs polish_mode RD_POLISH_FP64 and one lane");
     return RD_OK;
 }
 
@@ -182,8 +191,12 @@ int solve_common(const void *coeffs, rd_dtype dtype, int degree, int64_t n, rd_m
     a.coeffs = coeffs;
     a.n = n;
     if (n == 0) return RD_OK;
-    int block = p.block ? p.block : 128;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (p.polish_warps > 0) {
+        if (mode != RD_MIXED) return rd_set_error(RD_EINVAL, "params.polish_warps > 0 needs RD_MIXED");
+        return rd::launch_solve_ws(degree, dtype, a, p.block, p.ctas_per_sm, p.polish_warps, p.ring_slots, st);
+    }
+    int block = p.block ? p.block : 128;
     if (rd::lanes_for(degree, mode == RD_MIXED, p.polish_mode, p.lanes) == 2)
         return rd::launch_solve2(degree, dtype, mode == RD_MIXED, a, block, p.ctas_per_sm, st);
     if (mode == RD_MIXED) return rd::launch_solve_mixed(degree, dtype, a, block, p.ctas_per_sm, st);
@@ -242,6 +255,23 @@ void rd_default_params(rd_mode mode, rd_params *out)
     out->fixed_sweeps = 0;
     out->polish_mode = RD_POLISH_FP64;
     out->lanes = 0;
+    out->polish_warps = 0;
+    out->ring_slots = 0;
+}
+
+int rd_ws_selftest_timeout(const void *coeffs, int64_t n, uint8_t *status, rd_stats *stats, void *stream)
+{
+    if (n < 1 || n > 1024) return rd_set_error(RD_EINVAL, "n must be in [1, 1024]");
+    if (!coeffs || !aligned(coeffs, 8)) return rd_set_error(RD_EINVAL, "coeffs null or misaligned");
+    if (!status || !stats || !aligned(stats, 8)) return rd_set_error(RD_EINVAL, "status and stats are required");
+    rd::SolveArgs a;
+    rd_params p;
+    int rc = build_solve_args(RD_C64, 6, RD_MIXED, nullptr, nullptr, nullptr, 0, 0, nullptr, nullptr, status, stats,
+                              a, p);
+    if (rc) return rc;
+    a.coeffs = coeffs;
+    a.n = n;
+    return rd::launch_solve_ws_selftest(a, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int rd_roots_batched(const void *coeffs, rd_dtype dtype, int degree, int64_t n, rd_mode mode, const rd_params *params,
@@ -301,6 +331,7 @@ int rd_roots_uneven(const void *coeffs, rd_dtype dtype, const uint8_t *degrees, 
     int rc = build_solve_args(dtype, 12, mode, params, nullptr, window, W, H, hist, roots, status, stats, a, p);
     if (rc) return rc;
     if (p.residual_tol <= 0) a.residual_tol = -1.0;  // per-degree default 64 d 2^-53, set in the kernel
+    if (p.polish_warps != 0) return rd_set_error(RD_EINVAL, "params.polish_warps must be 0 for uneven batches");
     if (n == 0) return RD_OK;
     size_t el = dtype == RD_C64 ? 8 : 16;
     if (!coeffs || !aligned(coeffs, el)) return rd_set_error(RD_EINVAL, "coeffs null or misaligned");
@@ -438,6 +469,7 @@ int rd_field_density(rd_field f, const rd_field_spec *spec, rd_mode mode, const 
     int rc = build_solve_args(RD_C128, sp.degree, mode, params, nullptr, &window, W, H, hist, roots, status, stats, a, p);
     if (rc) return rc;
     if (p.lanes == 2) return rd_set_error(RD_EINVAL, "params.lanes must be 0 or 1 here");
+    if (p.polish_warps != 0) return rd_set_error(RD_EINVAL, "params.polish_warps must be 0 here");
     if (mode == RD_MIXED && p.polish_mode != RD_POLISH_FP64)
         return rd_set_error(RD_EINVAL, "params.polish_mode must be RD_POLISH_FP64 here");
     a.n = (int64_t)sp.nx * sp.ny;

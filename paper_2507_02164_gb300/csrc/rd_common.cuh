@@ -331,7 +331,8 @@ __device__ __forceinline__ void hist_add(uint32_t *hist, int pix)
 // ---- per-call counters ---------------------------------------------------
 // rd_stats word indices
 enum : int { ST_POLYS = 0, ST_STATUS0 = 1, ST_SWEEPS = 5, ST_PAIRS = 6, ST_ROTS = 7, ST_NEWTON = 8,
-             ST_BINNED = 9, ST_OOW = 10, ST_CLIPPED = 11, ST_F32 = 12, ST_F64 = 13, ST_WORDS = 14 };
+             ST_BINNED = 9, ST_OOW = 10, ST_CLIPPED = 11, ST_F32 = 12, ST_F64 = 13, ST_TIMEOUT = 14,
+             ST_WORDS = 15 };
 
 // Counters are summed over the warp as soon as they are produced and kept
 // per CTA in shared memory, so no thread carries them in registers through

@@ -247,20 +247,20 @@ struct PackedMap : ClipFromArrays {
     __device__ int64_t root(int64_t p, int j) const { return __ldg(offsets + p) - p + j; }
 };
 
-// One warp solves (and bins) the 32 polynomials base .. base+31 of a
-// coefficient-major batch `coeffs` of n polynomials of degree N. All 32
-// lanes must call it together.
-template <int N, typename T, typename In, int MODE, class Map>
-__device__ __forceinline__ void solve_warp(const SolveArgs &A, const void *coeffs, int64_t n, int64_t base,
-                                           const Map &map, const CtaStats &S)
+// Sweep half of one lane's solve: local polynomial i (< n: valid) of a
+// coefficient-major batch `coeffs` of n polynomials of degree N is loaded,
+// normalised and swept to the diagonal d (its eigenvalues in the sweep
+// precision T). All 32 lanes of the warp must call it together (the sweep
+// size is warp-uniform).
+template <int N, typename T, typename In, int MODE>
+__device__ __forceinline__ void sweep_lane(const SolveArgs &A, const void *coeffs, int64_t n, int64_t i,
+                                           const CtaStats &S, cx<T> (&d)[N], bool &degenerate_out,
+                                           bool &not_conv_out)
 {
     constexpr bool MIXED = MODE != MODE_PLAIN;
-    const int lane = threadIdx.x & 31;
     const T tol = (T)A.tol;
     {
-        const int64_t i = base + lane;
         const bool valid = i < n;
-        const int64_t pid = valid ? map.poly(i) : 0;  // the polynomial's index in the caller's batch
 
         // ---- load a_0..a_N (coefficient-major, coalesced) and normalise
         cx<T> b[N];
@@ -350,6 +350,25 @@ __device__ __forceinline__ void solve_warp(const SolveArgs &A, const void *coeff
         // algorithmic flops of the sweeps, in the sweep precision (rd_stats convention)
         const unsigned sweep_flops = 20u * n_pairs + 24u * n_rots + 60u * n_sweeps;
         S.add(MIXED ? ST_F32 : ST_F64, sweep_flops);
+#pragma unroll
+        for (int j = 0; j < N; ++j) d[j] = h[j][j];
+        degenerate_out = degenerate;
+        not_conv_out = not_conv;
+    }
+}
+
+// Finish half: polish (RD_MIXED) and check the eigenvalues d of local
+// polynomial i, write its status and roots, and bin them. All 32 lanes of
+// the warp must call it together (warp votes decide the rare paths).
+template <int N, typename T, typename In, int MODE, class Map>
+__device__ __forceinline__ void finish_lane(const SolveArgs &A, const void *coeffs, int64_t n, int64_t i,
+                                            const Map &map, const CtaStats &S, const cx<T> (&d)[N],
+                                            bool degenerate, bool not_conv)
+{
+    constexpr bool MIXED = MODE != MODE_PLAIN;
+    {
+        const bool valid = i < n;
+        const int64_t pid = valid ? map.poly(i) : 0;  // the polynomial's index in the caller's batch
 
         // ---- roots: the diagonal; MIXED polishes them in FP64
         uint8_t st = degenerate ? RD_STATUS_DEGENERATE : (not_conv ? RD_STATUS_NOT_CONVERGED : RD_STATUS_OK);
@@ -359,11 +378,11 @@ __device__ __forceinline__ void solve_warp(const SolveArgs &A, const void *coeff
         cx<double> z[N];
         if constexpr (!MIXED) {
 #pragma unroll
-            for (int j = 0; j < N; ++j) z[j] = {(double)h[j][j].re, (double)h[j][j].im};
+            for (int j = 0; j < N; ++j) z[j] = {(double)d[j].re, (double)d[j].im};
         } else {
             cx<float> zq[N];
 #pragma unroll
-            for (int j = 0; j < N; ++j) zq[j] = {h[j][j].re, h[j][j].im};
+            for (int j = 0; j < N; ++j) zq[j] = {d[j].re, d[j].im};
             unsigned newton = 0;
             const bool polish = A.polish_steps > 0 || A.polish_extra > 0;
             if (!polish) {
@@ -605,6 +624,20 @@ __device__ __forceinline__ void solve_warp(const SolveArgs &A, const void *coeff
             S.add(ST_OOW, n_oow);
         }
     }
+}
+
+// One warp solves (and bins) the 32 polynomials base .. base+31 of a
+// coefficient-major batch `coeffs` of n polynomials of degree N. All 32
+// lanes must call it together.
+template <int N, typename T, typename In, int MODE, class Map>
+__device__ __forceinline__ void solve_warp(const SolveArgs &A, const void *coeffs, int64_t n, int64_t base,
+                                           const Map &map, const CtaStats &S)
+{
+    const int64_t i = base + (threadIdx.x & 31);
+    cx<T> d[N];
+    bool degenerate, not_conv;
+    sweep_lane<N, T, In, MODE>(A, coeffs, n, i, S, d, degenerate, not_conv);
+    finish_lane<N, T, In, MODE>(A, coeffs, n, i, map, S, d, degenerate, not_conv);
 }
 
 // Uniform batch: warps stride over A.n polynomials, 32 at a time.

@@ -37,12 +37,12 @@ def test_every_declared_symbol_is_exported_and_bound():
 
 
 def test_struct_sizes_match_header_layout():
-    assert ctypes.sizeof(N.Params) == 64
+    assert ctypes.sizeof(N.Params) == 72
     assert ctypes.sizeof(N.Window) == 32
     assert ctypes.sizeof(N.Clip) == 64
     assert ctypes.sizeof(N.UnevenTuning) == 3 * 16 * 4
     assert ctypes.sizeof(N.FieldSpec) == 32 + 8 + 8 + 16 + 26 * 8
-    assert N.STATS_WORDS == 14
+    assert N.STATS_WORDS == 15
 
 
 def test_default_params():
@@ -138,6 +138,43 @@ def test_argument_validation_without_gpu():
     rc, msg = _err(L.rd_roots_batched(ctypes.c_void_p(64), N.C64, 6, 5, N.MIXED, ctypes.byref(bad), null, null,
                                       null, null))
     assert rc == N.RD_EINVAL and "lanes" in msg
+
+
+def test_warp_specialised_argument_validation_without_gpu():
+    """params.polish_warps / ring_slots: every bad combination is refused on
+    the host before anything is launched."""
+    L = N.load()
+    null = ctypes.c_void_p(0)
+    co = ctypes.c_void_p(64)
+
+    def batched(degree=6, mode=N.MIXED, **kw):
+        q = N.default_params(mode)
+        for k, v in kw.items():
+            setattr(q, k, v)
+        return _err(L.rd_roots_batched(co, N.C64, degree, 5, mode, ctypes.byref(q), null, null, null, null))
+
+    for kw, word in [(dict(polish_warps=16), "polish_warps"), (dict(polish_warps=-1), "polish_warps"),
+                     (dict(polish_warps=2, ring_slots=1), "ring_slots"),
+                     (dict(polish_warps=2, ring_slots=65), "ring_slots"),
+                     (dict(polish_warps=2, block=544), "block"), (dict(block=512), "block"),
+                     (dict(polish_warps=2, polish_mode=N.POLISH_DF), "polish_warps"),
+                     (dict(polish_warps=2, lanes=2), "polish_warps"),
+                     (dict(polish_warps=4, block=128), "polish_warps"),  # no sweep warp left
+                     (dict(polish_warps=1, block=512), "block")]:  # degree 8: at most 256 threads
+        rc, msg = batched(8 if kw.get("block") == 512 else 6, **kw)
+        assert rc == N.RD_EINVAL and word in msg, (kw, rc, msg)
+    rc, msg = batched(mode=N.PLAIN_FP64, polish_warps=2)
+    assert rc == N.RD_EINVAL and "polish_warps" in msg
+    # uneven batches and the one-launch field path have no warp-specialised form
+    q = N.default_params(N.MIXED)
+    q.polish_warps = 2
+    rc, msg = _err(L.rd_roots_uneven(co, N.C64, null, null, 0, 0, N.MIXED, ctypes.byref(q), None, None, 0, 0, null,
+                                     null, null, null, null, 0, null))
+    assert rc == N.RD_EINVAL and "polish_warps" in msg
+    # the bounded-wait self-test: 1 <= n <= 1024, status and stats required
+    for n, st, stats in [(0, co, co), (1025, co, co), (32, null, co), (32, co, null)]:
+        rc, _ = _err(L.rd_ws_selftest_timeout(co, n, st, stats, null))
+        assert rc == N.RD_EINVAL
 
 
 def test_field_density_argument_validation_without_gpu():
