@@ -932,7 +932,7 @@ def run_pipeline(args, rank, world, local_rank):
     the split path's sampling time."""
     import torch
 
-    from paper_2507_02164_gb300 import api, build, workloads as WL
+    from paper_2507_02164_gb300 import api, autotune, build, workloads as WL
     build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -947,6 +947,9 @@ def run_pipeline(args, rank, world, local_rank):
     stats = api.new_stats(dev)
     win = api.Window(*win_t)
     clip = api.make_clip(c, rho, 480, 270, win)
+    # the roots step's launch shape, tuned at this batch size (complex128, degree 6)
+    roots_shape = autotune.tune("mixed", dtype=torch.complex128, degrees=[6], n=n)["degrees"]["6"]
+    p_roots = autotune.degree_params({"degrees": {"6": roots_shape}}, 6, "mixed")
     stream = torch.cuda.current_stream()
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
 
@@ -957,7 +960,7 @@ def run_pipeline(args, rank, world, local_rank):
             e[0].record(stream)
             api.l2_approx(samples, 16, 32, 6, coeffs=coeffs, precision=precision)
             e[1].record(stream)
-            api.roots_density(coeffs, win, hist, mode="mixed", clip=clip, stats=stats)
+            api.roots_density(coeffs, win, hist, mode="mixed", params_=p_roots, clip=clip, stats=stats)
             e[2].record(stream)
         return step
 
@@ -1011,7 +1014,9 @@ def run_pipeline(args, rank, world, local_rank):
         "config": {"workload": "480x270 tiles of 1/60 on [-4,4]x[-2.25,2.25], rho = tile half-diagonal, 16x32 polar "
                                "nodes, degree 6, mixed roots, clip to own tile, 1920x1080 histogram",
                    "sub_disks": n, "l2_flush": "inputs larger than L2 (1.06 GB of samples per step)",
-                   "parallelism": f"dp{world}"},
+                   "parallelism": f"dp{world}",
+                   "roots_launch_shape": {x: roots_shape[x] for x in ("lanes", "block", "ctas_per_sm", "polish_warps",
+                                                                      "ms")}},
         "l2_approx_ms": l2_ms, "roots_density_ms": solve_ms, "l2_precision": "double-float (RD_L2_DF)",
         "l2_roofline": {"bound": "hbm", "achieved": n * 512 * 16 / (l2_ms * 1e-3) / 1e9, "peak": 6777.6,
                         "unit": "GB/s", "frac": n * 512 * 16 / (l2_ms * 1e-3) / 1e9 / 6777.6,
@@ -1130,27 +1135,30 @@ def run_adjoint(args, rank, world, local_rank):
     import numpy as np
     import torch
 
-    from paper_2507_02164_gb300 import api, build, workloads as WL
+    from paper_2507_02164_gb300 import api, autotune, build, workloads as WL
     build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     from paper_2507_02164_gb300 import splat as SP
     n = 1 << 20
     co = WL.gaussian(4, n, 6)
-    out = {}
+    out, shapes = {}, {}
     stream = torch.cuda.current_stream()
     # target image: the splat of a second seeded batch (2^16 polynomials)
     tgt_co = torch.from_numpy(np.ascontiguousarray(WL.gaussian(5, 1 << 16, 6).T)).to(dev)
     target = SP.splat(api.roots_batched(tgt_co, mode="mixed")[0])
     for name, dt in (("c128", torch.complex128), ("c64", torch.complex64)):
         coeffs = torch.from_numpy(np.ascontiguousarray(co.T)).to(dev).to(dt)
+        # the forward solve in the autotuner's launch shape for this storage type
+        shapes[name] = autotune.tune("mixed", dtype=dt, degrees=[6])["degrees"]["6"]
+        p = autotune.degree_params({"degrees": {"6": shapes[name]}}, 6, "mixed")
         roots = torch.empty((6, n), dtype=torch.complex128, device=dev)
         status = torch.empty(n, dtype=torch.uint8, device=dev)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
 
         def step():
             ev[0].record(stream)
-            api.roots_batched(coeffs, mode="mixed", roots=roots, status=status)
+            api.roots_batched(coeffs, mode="mixed", params_=p, roots=roots, status=status)
             ev[1].record(stream)
             api.roots_backward(coeffs, roots, 2.0 * roots)
             ev[2].record(stream)
@@ -1169,7 +1177,7 @@ def run_adjoint(args, rank, world, local_rank):
 
         def loss_step():
             co_g.grad = None
-            z, _ = api.roots(co_g, "mixed")
+            z, _ = api.roots(co_g, "mixed", p)
             L = SP.loss(z, target, precision=precision)
             L.backward()
 
@@ -1187,7 +1195,9 @@ def run_adjoint(args, rank, world, local_rank):
         "config": {"workload": "2^20 deg-6, forward mixed roots + adjoint of L = sum |z|^2; loss_step: "
                                "L = sum |z|^2 + sum (D - T)^2 with D the 256x144 soft-density image "
                                "(sigma 1.5 px) of the roots, forward and backward through autograd",
-                   "l2_flush": "none (inputs 112 MB c128, 56 MB c64)", "parallelism": f"dp{world}"},
+                   "l2_flush": "none (inputs 112 MB c128, 56 MB c64)", "parallelism": f"dp{world}",
+                   "launch_shapes": {k: {x: v[x] for x in ("lanes", "block", "ctas_per_sm", "polish_warps", "ms")}
+                                     for k, v in shapes.items()}},
         "c128": out["c128"], "c64": out["c64"], "gpu_launches": 2 * args.steps, "clocks": out["c128"]["clocks"],
     }), flush=True)
 

@@ -266,12 +266,13 @@ def l2_approx(samples: torch.Tensor, nr: int = 16, nt: int = 32, degree: int = 6
 
 
 class RootsFn(torch.autograd.Function):
-    """roots = RootsFn.apply(coeffs [d+1, n], mode): forward by the QR solver,
-    backward by the implicit-differentiation adjoint (no QR history kept)."""
+    """roots = RootsFn.apply(coeffs [d+1, n], mode, params): forward by the QR
+    solver (rd_params or None for the defaults), backward by the
+    implicit-differentiation adjoint (no QR history kept)."""
 
     @staticmethod
-    def forward(ctx, coeffs, mode="mixed"):
-        roots, status = roots_batched(coeffs.detach().contiguous(), mode=mode)
+    def forward(ctx, coeffs, mode="mixed", params_=None):
+        roots, status = roots_batched(coeffs.detach().contiguous(), mode=mode, params_=params_)
         ctx.save_for_backward(coeffs, roots)
         ctx.mark_non_differentiable(status)
         return roots, status
@@ -280,14 +281,15 @@ class RootsFn(torch.autograd.Function):
     def backward(ctx, grad_roots, grad_status):
         coeffs, roots = ctx.saved_tensors
         if grad_roots is None:
-            return None, None
+            return None, None, None
         g = roots_backward(coeffs.detach().contiguous(), roots, grad_roots.contiguous().to(torch.complex128))
-        return g, None
+        return g, None, None
 
 
-def roots(coeffs: torch.Tensor, mode="mixed"):
-    """Differentiable roots: (roots [d, n] complex128, status [n] uint8)."""
-    return RootsFn.apply(coeffs, mode)
+def roots(coeffs: torch.Tensor, mode="mixed", params_=None):
+    """Differentiable roots: (roots [d, n] complex128, status [n] uint8);
+    params_ as in roots_batched (e.g. an autotuned launch shape)."""
+    return RootsFn.apply(coeffs, mode, params_)
 
 
 def field_spec(tiles: Window, nx: int, ny: int, radius: float = 0.0, poly=None, degree: int = 6,

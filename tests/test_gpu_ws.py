@@ -110,6 +110,19 @@ def test_tile_clip_bit_identical(dev):
     assert torch.equal(h0, h1) and s0 == s1 and s0["clipped"] > 0
 
 
+def test_histogram_only_without_optional_outputs(dev):
+    """roots, status and stats are optional: the histogram alone, as the
+    benchmark's zero-copy leg asks for it, equals the one-role kernel's."""
+    co = WL.littlewood_soa_torch(2, 5, 70001, dev)
+    hists = []
+    for kw in ({}, dict(block=512, polish_warps=10)):
+        hist = api.new_hist(W, H, dev)
+        api.roots_density(co, WIN2, hist, "mixed", api.params("mixed", **kw))
+        torch.cuda.synchronize()
+        hists.append(hist)
+    assert torch.equal(hists[0], hists[1]) and int(hists[0].sum()) > 0
+
+
 def test_graph_replay_bit_identical(dev):
     n = 1 << 16
     co = WL.littlewood_soa_torch(2, 99, n, dev)
@@ -170,3 +183,17 @@ def test_bounded_wait_runs_out_and_reports(dev):
     # the context still solves
     ref = _run(co, 6, WIN2)
     _same(_run(co, 6, WIN2, block=256, polish_warps=2), ref)
+
+
+def test_autograd_roots_with_a_warp_specialised_shape(dev):
+    """api.roots(..., params_) forwards the launch shape: the same roots, and
+    so the same adjoint gradients, bit for bit."""
+    co = to_soa(WL.gaussian(9, 20001, 6), dev, torch.complex128)
+    grads = []
+    for p in (None, api.params("mixed", block=512, polish_warps=10)):
+        c = co.clone().requires_grad_(True)
+        z, _ = api.roots(c, "mixed", p)
+        (z.real ** 2 + z.imag ** 2).sum().backward()
+        grads.append((z.detach(), c.grad))
+    assert torch.equal(torch.view_as_real(grads[0][0]), torch.view_as_real(grads[1][0]))
+    assert torch.equal(torch.view_as_real(grads[0][1]), torch.view_as_real(grads[1][1]))
