@@ -155,9 +155,12 @@ class ClockSampler:
 
 # ------------------------------------------------------------- CPU oracle
 
-def cpu_oracle_rate(seconds: float, start_index: int = 0):
+def cpu_oracle_rate(seconds: float, start_index: int = 0, first_idx=None):
     """Oracle solve + histogram on the host cores for about `seconds`; returns
-    (polys/s, threads used, polys done)."""
+    (polys/s, threads used, polys done, first chunk). The first chunk is the
+    polynomials first_idx when given (their oracle roots and status are
+    returned with their coefficients, for the root-error report), then
+    chunks of 65,536 consecutive polynomials of the stream."""
     import numpy as np
 
     import oracle
@@ -165,16 +168,22 @@ def cpu_oracle_rate(seconds: float, start_index: int = 0):
     oracle.build()
     chunk = 1 << 16
     done, elapsed, threads, k = 0, 0.0, 0, 0
-    while elapsed < seconds:
-        idx = np.arange(start_index + k * chunk, start_index + (k + 1) * chunk, dtype=np.uint64)
+    first = None
+    while elapsed < seconds or first is None:
+        if first is None and first_idx is not None:
+            idx = np.asarray(first_idx, dtype=np.uint64)
+        else:
+            idx = np.arange(start_index + k * chunk, start_index + (k + 1) * chunk, dtype=np.uint64)
+            k += 1
         co = WL.littlewood(SEED, idx).astype(np.complex128)
         t0 = time.perf_counter()
-        roots, _, _, threads = oracle.solve(co, tol=1e-13)
+        roots, status, _, threads = oracle.solve(co, tol=1e-13)
         oracle.hist(roots, WINDOW, W_PIX, H_PIX)
         elapsed += time.perf_counter() - t0
-        done += chunk
-        k += 1
-    return done / elapsed, threads, done
+        done += idx.size
+        if first is None:
+            first = (co, roots, status)
+    return done / elapsed, threads, done, first
 
 
 def run_reference(args, rank: int):
@@ -231,6 +240,47 @@ def workload_config(args, ref_sample=None):
 
 
 # ---------------------------------------------------------------- GPU leg
+
+def match_roots(gpu, ref):
+    """Reorder each row of gpu [n, d] to pair with the same row of ref: the
+    nearest-root pairing where it is a permutation, else the assignment of
+    least total distance (rows where roots lie closer together than their
+    errors)."""
+    import numpy as np
+    from scipy.optimize import linear_sum_assignment
+    dist = np.abs(gpu[:, None, :] - ref[:, :, None])  # [n, ref j, gpu k]
+    near = dist.argmin(axis=2)
+    ok = np.all(np.sort(near, axis=1) == np.arange(ref.shape[1])[None, :], axis=1)
+    out = np.take_along_axis(gpu, near, axis=1)
+    for i in np.nonzero(~ok)[0]:
+        rows, cols = linear_sum_assignment(np.nan_to_num(dist[i], nan=1e300, posinf=1e300))
+        out[i, rows] = gpu[i, cols]
+    return out
+
+
+def root_error_summary(gpu, status, ref, ref_status, coeffs, bar, kappa_cap):
+    """Relative error |z - z_ref| / max(1, |z_ref|) of matched roots where
+    both solvers report OK. Roots with condition number kappa =
+    sum |a_k| |z|^k / (|z| |p'(z)|) above kappa_cap (kappa 2^-53 > 1e-12: the
+    FP64 reference itself is not that accurate there) are reported apart."""
+    import numpy as np
+    ok = (status == 0) & (ref_status == 0)
+    g = match_roots(gpu[ok], ref[ok])
+    r, a = ref[ok], coeffs[ok]
+    err = np.abs(g - r) / np.maximum(1.0, np.abs(r))
+    d = a.shape[1] - 1
+    az = np.abs(r)
+    num = sum(np.abs(a[:, k:k + 1]) * az ** k for k in range(d + 1))
+    dp = sum(k * a[:, k:k + 1] * r ** (k - 1) for k in range(1, d + 1))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        kappa = num / (np.maximum(az, 1e-300) * np.abs(dp))
+    well = kappa <= kappa_cap
+    return {"max_rel_err": float(err[well].max(initial=0.0)), "median_rel_err": float(np.median(err[well])),
+            "roots_compared": int(well.sum()), "bar": bar, "within_bar": bool(err[well].max(initial=0.0) <= bar),
+            "ill_conditioned_roots": int((~well).sum()), "ill_conditioned_max_rel_err":
+            float(err[~well].max(initial=0.0)), "kappa_cap": kappa_cap,
+            "status_counts": np.bincount(status, minlength=4).tolist()}
+
 
 def algorithmic_flops(st: dict):
     """(FP32 flops, FP64 flops) of the counted launches, as the kernel counted
@@ -335,6 +385,18 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     # call, median of 20 after 3 warm-ups
     latency = small_batch_latency(api, WL, torch, dev, stream) if rank == 0 else None
 
+    # the root-error subsample i = 1024 k of this batch, solved again by each GPU
+    # path with its timed launch shape (a polynomial's roots do not depend on
+    # its neighbours in the batch); compared with the oracle in the CPU leg
+    sub_idx, sub_roots = None, {}
+    if rank == 0 and not args.no_cpu and n >= 1024:
+        import numpy as np
+        sub_idx = np.arange(min(1 << 16, n // 1024), dtype=np.int64) * 1024
+        sub = coeffs[:, torch.from_numpy(sub_idx).to(dev)].contiguous()
+        for mode in tuned:
+            r, stt = api.roots_batched(sub, mode=mode, params_=autotune.degree_params(tuned[mode], DEGREE, mode))
+            sub_roots[mode] = (r.cpu().numpy().T, stt.cpu().numpy())
+
     # one exchange step: sum the per-rank images (after the timed region)
     reduce_ms = None
     if world > 1:
@@ -418,10 +480,23 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if reduce_ms is not None:
         line["hist_reduce_ms"] = reduce_ms
     if not args.no_cpu:
-        v, threads, done = cpu_oracle_rate(args.cpu_seconds)
+        v, threads, done, (co_s, ref_s, ref_st) = cpu_oracle_rate(args.cpu_seconds, first_idx=sub_idx)
+        first = f"the {sub_idx.size} polynomials i = 1024 k, then " if sub_idx is not None else ""
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                "sample": f"first {done} polynomials of the same Littlewood stream, FP64 oracle "
-                                          f"solve (tol 1e-13) + histogram, chunks of 65536, ~{args.cpu_seconds:.0f} s"}
+                                "sample": f"{done} polynomials of the same Littlewood stream: {first}the first ones "
+                                          f"in chunks of 65536; FP64 oracle solve (tol 1e-13) + histogram, "
+                                          f"~{args.cpu_seconds:.0f} s"}
+        # root error of the GPU paths on that subsample (the oracle's first chunk)
+        if sub_idx is not None:
+            line["root_error"] = {
+                "subsample": f"the {sub_idx.size} polynomials i = 1024 k of the batch, GPU roots vs the FP64 "
+                             "oracle (tol 1e-13), matched per polynomial; error |z - z_oracle| / max(1, |z_oracle|)",
+                "mixed": root_error_summary(sub_roots["mixed"][0], sub_roots["mixed"][1], ref_s, ref_st, co_s,
+                                            1e-9, 1e3),
+            }
+            if "plain" in sub_roots:
+                line["root_error"]["plain_fp64"] = root_error_summary(sub_roots["plain"][0], sub_roots["plain"][1],
+                                                                      ref_s, ref_st, co_s, 1e-11, 1e2)
     print(json.dumps(line), flush=True)
 
 
@@ -609,7 +684,9 @@ UNEVEN_METRIC = "uneven-degree (2..12) complex polys rooted+binned/s, mixed, one
 
 
 def cpu_oracle_rate_uneven(seconds: float):
-    """Oracle solve + histogram of the uneven stream on the host cores for about `seconds`."""
+    """Oracle solve + histogram of the uneven stream on the host cores for about
+    `seconds`; returns (polys/s, threads, polys done, first chunk) with the
+    first chunk's {degree: (polynomial indices, coefficients, roots, status)}."""
     import numpy as np
 
     import oracle
@@ -627,13 +704,17 @@ def cpu_oracle_rate_uneven(seconds: float):
             if sel.size:
                 rows_by_deg[d] = packed[(off[sel][:, None] + np.arange(d + 1)[None, :])]
         t0 = time.perf_counter()
+        solved = {}
         for d, rows in rows_by_deg.items():
-            roots, _, _, threads = oracle.solve(rows, tol=1e-13)
+            roots, status, _, threads = oracle.solve(rows, tol=1e-13)
             oracle.hist(roots, UNEVEN_WINDOW, W_PIX, H_PIX)
+            solved[d] = (roots, status)
         elapsed += time.perf_counter() - t0
+        if k == 0:
+            first = {d: (np.nonzero(deg == d)[0], rows_by_deg[d], r, st) for d, (r, st) in solved.items()}
         done += chunk
         k += 1
-    return done / elapsed, threads, done
+    return done / elapsed, threads, done, first
 
 
 def run_uneven(args, rank: int, world: int, local_rank: int):
@@ -833,11 +914,40 @@ def run_uneven(args, rank: int, world: int, local_rank: int):
     }
     if e2e is not None:
         line["e2e"] = e2e
+    # the oracle's first chunk (polynomials 0..32767 of the stream), solved again
+    # on the GPU with the timed launch shapes, for the root-error report
+    sub = None
+    if not args.no_cpu and n >= 32768:
+        import numpy as np
+        m = 32768
+        off_h = off[:m + 1].cpu().numpy()
+        ws_s = api.new_uneven_workspace(m, int(off_h[m]), torch.complex64, dev)
+        r_s, st_s = api.roots_uneven(packed[:int(off_h[m])], deg[:m], off[:m + 1], ws_s, mode="mixed", params_=p,
+                                     tuning=tuning)
+        torch.cuda.synchronize()
+        sub = (r_s.cpu().numpy(), st_s.cpu().numpy(), off_h)
     if not args.no_cpu:
-        v, threads, done = cpu_oracle_rate_uneven(args.cpu_seconds)
+        v, threads, done, first = cpu_oracle_rate_uneven(args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"first {done} polynomials of the same uneven stream, FP64 oracle solve + "
                                           f"histogram per degree, ~{args.cpu_seconds:.0f} s"}
+        if sub is not None:
+            r_g, st_g, off_g = sub
+            per = {}
+            for d, (sel, co_d, r_o, st_o) in first.items():
+                base = off_g[sel] - sel  # where polynomial i's roots start in the packed roots
+                g = r_g[base[:, None] + np.arange(d)[None, :]]
+                per[d] = root_error_summary(g, st_g[sel], r_o, st_o, co_d, 1e-9, 1e3)
+            line["root_error"] = {
+                "subsample": "the first 32768 polynomials of the batch (the oracle's first chunk), GPU roots vs "
+                             "the FP64 oracle (tol 1e-13) per degree, matched per polynomial; error "
+                             "|z - z_oracle| / max(1, |z_oracle|), roots with kappa > 1e3 apart",
+                "max_rel_err": max(e["max_rel_err"] for e in per.values()), "bar": 1e-9,
+                "within_bar": all(e["within_bar"] for e in per.values()),
+                "roots_compared": sum(e["roots_compared"] for e in per.values()),
+                "ill_conditioned_roots": sum(e["ill_conditioned_roots"] for e in per.values()),
+                "per_degree": {str(d): {k: e[k] for k in ("max_rel_err", "roots_compared", "ill_conditioned_roots",
+                                                          "status_counts")} for d, e in sorted(per.items())}}
     print(json.dumps(line), flush=True)
 
 
@@ -923,6 +1033,27 @@ def run_paper(args, rank, world, local_rank):
 PIPELINE_METRIC = "sub-disks/s through L2 approximation + mixed roots + tile clip + histogram, f = sin(z^3) + 0.5 z"
 
 
+def newton_move_of_kept(roots_w, centres, rho, tiles, nx, ny):
+    """For every root w the tile clip keeps (z = c + rho w inside its own
+    tile), one FP64 Newton step on f(z) = sin(z^3) + z/2 itself: its length is
+    how far z lies from f's zero (the pipeline's accuracy check, bar 1e-6)."""
+    import numpy as np
+    w = roots_w.cpu().numpy().T
+    c = centres.cpu().numpy()[:, None]
+    z = c + rho * w
+    with np.errstate(invalid="ignore"):
+        tx = np.floor((z.real - tiles[0]) * nx / (tiles[1] - tiles[0]))
+        ty = np.floor((tiles[3] - z.imag) * ny / (tiles[3] - tiles[2]))
+    t = np.arange(c.shape[0])[:, None]
+    kept = (tx == t % nx) & (ty == t // nx) & np.isfinite(z)
+    zk = z[kept]
+    f = np.sin(zk ** 3) + 0.5 * zk
+    fp = 3 * zk ** 2 * np.cos(zk ** 3) + 0.5
+    move = np.abs(f / fp)
+    return {"kept_roots": int(kept.sum()), "max_newton_move": float(move.max(initial=0.0)),
+            "bar": 1e-6, "within_bar": bool(move.max(initial=0.0) <= 1e-6)}
+
+
 def run_pipeline(args, rank, world, local_rank):
     """The full pipeline: f(z) = sin(z^3) + 0.5 z on [-4,4]x[-2.25,2.25] in
     480 x 270 tiles; samples at the 16 x 32 nodes of every sub-disk are made
@@ -1000,6 +1131,14 @@ def run_pipeline(args, rank, world, local_rank):
     if rank != 0:
         return
     st = api.stats_dict(stats)
+    # accuracy (after the timed legs): every kept root of both paths, one FP64
+    # Newton step on f itself; the step is the distance to f's zero there
+    roots_t = torch.empty((6, n), dtype=torch.complex128, device=dev)
+    hist_a = api.new_hist(W_PIX, H_PIX, dev)
+    api.roots_density(coeffs, win, hist_a, mode="mixed", params_=p_roots, clip=clip, roots=roots_t)
+    accuracy = {"split": newton_move_of_kept(roots_t, c, rho, win_t, 480, 270)}
+    api.field_density(spec, win, hist_a, mode="mixed", roots=roots_t)
+    accuracy["one_launch"] = newton_move_of_kept(roots_t, c, rho, win_t, 480, 270)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clk.get("sm_max_mhz") or 2070.0
     p64 = sms * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6
@@ -1018,6 +1157,7 @@ def run_pipeline(args, rank, world, local_rank):
                    "roots_launch_shape": {x: roots_shape[x] for x in ("lanes", "block", "ctas_per_sm", "polish_warps",
                                                                       "ms")}},
         "l2_approx_ms": l2_ms, "roots_density_ms": solve_ms, "l2_precision": "double-float (RD_L2_DF)",
+        "root_error": accuracy,
         "l2_roofline": {"bound": "hbm", "achieved": n * 512 * 16 / (l2_ms * 1e-3) / 1e9, "peak": 6777.6,
                         "unit": "GB/s", "frac": n * 512 * 16 / (l2_ms * 1e-3) / 1e9 / 6777.6,
                         "note": "issue-bound double-float sums; bytes are the 1.06 GB of samples"},
@@ -1045,7 +1185,7 @@ def small_batch_latency(api, WL, torch, dev, stream, reps=20, warmup=3):
     degree-6 polynomials in plain FP64, replayed from a CUDA graph."""
     import numpy as np
     n = 65536
-    co, _ = WL.unit_disk_roots(1, n)
+    co, true_roots = WL.unit_disk_roots(1, n)
     coeffs = torch.from_numpy(np.ascontiguousarray(co.T)).to(dev)
     hist = api.new_hist(W_PIX, H_PIX, dev)
     win = api.Window(-1.5, 1.5, -0.84375, 0.84375)
@@ -1073,8 +1213,12 @@ def small_batch_latency(api, WL, torch, dev, stream, reps=20, warmup=3):
         times.append(e0.elapsed_time(e1))
     times.sort()
     med = times[len(times) // 2]
+    # root error of the same solve against the seeded roots the polynomials were built from
+    r, st = api.roots_batched(coeffs, mode="plain", params_=p)
+    err = root_error_summary(r.cpu().numpy().T, st.cpu().numpy(), true_roots, np.zeros(n, np.uint8), co, 1e-11, 1e2)
+    err["reference"] = "the seeded roots each polynomial was expanded from (FP64)"
     return {"polys": n, "mode": "plain FP64 (tol 1e-13)", "median_ms": med, "min_ms": times[0],
-            "polys_per_s": n / (med * 1e-3), "binned": int(hist.sum()),
+            "polys_per_s": n / (med * 1e-3), "binned": int(hist.sum()), "root_error": err,
             "note": "unit-disk roots (seed 1), complex128, one graph replay = histogram clear + fused solve"}
 
 
