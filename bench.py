@@ -50,7 +50,7 @@ PROFILE_SUMMARY = {"one_role": os.path.join(ROOT, "profiles", "solve_mixed_littl
 KERNEL_SOURCES = {"one_role": ["paper_2507_02164_gb300/csrc/rd_solve.cuh", "paper_2507_02164_gb300/csrc/rd_common.cuh",
                                "paper_2507_02164_gb300/csrc/rd_solve_launch.cuh"],
                   "ws": ["paper_2507_02164_gb300/csrc/rd_solve.cuh", "paper_2507_02164_gb300/csrc/rd_common.cuh",
-                         "paper_2507_02164_gb300/csrc/rd_solve_ws.cuh"]}
+                         "paper_2507_02164_gb300/csrc/rd_solve_ws.cuh"]}  # device code; launch: rd_solve_ws_launch.cuh
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 SMSPs x 32)
 FP64_FMA_PER_SM_CLK = 2   # FP64 FMA per SM per clock: 1.25 TFLOP/s / (152 SMs x 2 flop x 2.07 GHz)
 

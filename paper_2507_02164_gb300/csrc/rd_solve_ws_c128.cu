@@ -1,6 +1,6 @@
 // rd_solve_ws_c128.cu -- the warp-specialised RD_MIXED solver (rd_solve_ws.cuh)
 // for complex128 coefficients.
-#include "rd_solve_ws.cuh"
+#include "rd_solve_ws_launch.cuh"
 
 namespace rd {
 

@@ -1,7 +1,7 @@
 // rd_solve_ws_c64.cu -- the warp-specialised RD_MIXED solver (rd_solve_ws.cuh)
 // for complex64 coefficients, the dispatch by storage type, and the
 // self-test of its bounded waits.
-#include "rd_solve_ws.cuh"
+#include "rd_solve_ws_launch.cuh"
 
 namespace rd {
 
