@@ -538,17 +538,20 @@ __device__ __forceinline__ void finish_lane(const SolveArgs &A, const void *coef
                 bool reject = failed != 0;
                 // separation: two polished roots must not have collapsed onto one.
                 // A cheap FP32 screen first (FP32 copies are within ~1e-7 of the
-                // FP64 roots); the FP64 test runs only when a lane needs it.
+                // FP64 roots); the FP64 test runs only when a lane needs it. The
+                // screen's bound, max(1e-4, 2 collapse_tol), passes every pair the
+                // FP64 test can reject, the FP32 rounding of both roots included.
                 {
                     cx<float> zs[N];
 #pragma unroll
                     for (int j = 0; j < N; ++j) zs[j] = d2f(z[j]);
+                    const float screen = fmaxf(1e-4f, 2.0f * (float)A.collapse_tol);
                     bool near = false;
 #pragma unroll
                     for (int j = 0; j < N; ++j)
 #pragma unroll
                         for (int k = j + 1; k < N; ++k)
-                            near |= abs1(sub(zs[j], zs[k])) <= 1e-4f * fmaxf(1.0f, abs1(zs[j]));
+                            near |= abs1(sub(zs[j], zs[k])) <= screen * fmaxf(1.0f, abs1(zs[j]));
                     if (__any_sync(0xffffffffu, near) && near) {
 #pragma unroll
                         for (int j = 0; j < N; ++j)

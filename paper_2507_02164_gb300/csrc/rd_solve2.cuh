@@ -389,9 +389,11 @@ __device__ __forceinline__ void solve_warp2(const SolveArgs &A, const void *coef
 #pragma unroll
                 for (int j = 0; j < L; ++j) zo[j] = shfl_pair(zs[j]);
                 bool near = false;
+                // the screen passes every pair the FP64 test can reject (as in finish_lane)
+                const float screen = fmaxf(1e-4f, 2.0f * (float)A.collapse_tol);
 #pragma unroll
                 for (int j = 0; j < L; ++j) {
-                    const float lim = 1e-4f * fmaxf(1.0f, abs1(zs[j]));
+                    const float lim = screen * fmaxf(1.0f, abs1(zs[j]));
 #pragma unroll
                     for (int k = j + 1; k < L; ++k) near |= (k < nmine) && abs1(sub(zs[j], zs[k])) <= lim;
 #pragma unroll

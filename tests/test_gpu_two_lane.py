@@ -169,3 +169,13 @@ def test_uneven_batch_two_lanes_matches_oracle(dev, orc, lanes):
         compare_roots(rg[good], ref[good], rows[good], orc, MIXED_TOL, KAPPA_MIXED)
     st = api.stats_dict(stats)
     assert st["polys"] == n and st["status_ok"] == int((s == 0).sum())
+
+
+@pytest.mark.parametrize("degree", [6, 11])
+def test_two_lanes_honour_a_large_collapse_tolerance(dev, degree):
+    """collapse_tol far above the FP32 screen's 1e-4 floor: the pair of lanes
+    rejects exactly the polynomials one lane rejects, and many of them."""
+    co = to_soa(WL.gaussian(123 + degree, 4001, degree), dev, torch.complex128)
+    _, s1, _, _ = _solve(co, "mixed", lanes=1, collapse_tol=1.0)
+    _, s2, _, _ = _solve(co, "mixed", lanes=2, collapse_tol=1.0)
+    assert np.array_equal(s1, s2) and (s1 == 2).sum() > 400

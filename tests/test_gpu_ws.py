@@ -197,3 +197,33 @@ def test_autograd_roots_with_a_warp_specialised_shape(dev):
         grads.append((z.detach(), c.grad))
     assert torch.equal(torch.view_as_real(grads[0][0]), torch.view_as_real(grads[1][0]))
     assert torch.equal(torch.view_as_real(grads[0][1]), torch.view_as_real(grads[1][1]))
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(max_iters=1), dict(polish_steps=0, polish_extra=0),
+                                dict(residual_tol=1e-30, polish_extra=2), dict(collapse_tol=1.0),
+                                dict(shift="rayleigh", exc_period=3), dict(polish_steps=1, polish_extra=0)])
+def test_every_status_branch_bit_identical(dev, kw):
+    """Degenerate rows (NaN, infinite and zero-leading coefficients) and
+    parameter sets that drive NOT_CONVERGED (one sweep per level), no polish,
+    REJECTED by the residual or the separation check: the warp-specialised
+    kernel reproduces the one-role kernel's roots, status and counters."""
+    n = 9001
+    c = WL.gaussian(77, n, 6).astype(np.complex64)
+    c[5, 2] = np.nan
+    c[40, 6] = 0.0
+    c[41, :] = 0.0
+    c[700, 0] = np.inf
+    c[8999, 6] = 0.0
+    co = to_soa(c.astype(np.complex128), dev, torch.complex64)
+    ref = _run(co, 6, WIN3, **kw)
+    got = _run(co, 6, WIN3, block=512, polish_warps=10, **kw)
+    # NaN roots compare by bits, so degenerate rows must match exactly too
+    _same(got, ref)
+    st = ref[3]
+    assert st["status_degenerate"] == 5
+    if kw.get("max_iters") == 1:
+        assert st["status_not_converged"] > 0
+    if kw.get("residual_tol") == 1e-30:
+        assert st["status_rejected"] > 0
+    if kw.get("collapse_tol") == 1.0:  # a tolerance far above the screen's 1e-4 floor is honoured
+        assert st["status_rejected"] > n // 10
