@@ -899,8 +899,11 @@ def run_uneven(args, rank: int, world: int, local_rank: int):
                                f"over [-3,3]x[-1.6875,1.6875]", "polys_per_gpu": n,
                    "coefficients": int(packed.numel()), "l2_flush": "inputs larger than L2 (0.94 GB per step)",
                    "parallelism": f"dp{world}",
-                   "launch_shapes": {"per_degree": {d: {k: e[k] for k in ("lanes", "block", "ctas_per_sm", "ms")}
-                                                      for d, e in tuned["degrees"].items()},
+                   "launch_shapes": {"per_degree": {d: {k: e.get("one_role", e)[k]
+                                                        for k in ("lanes", "block", "ctas_per_sm", "ms")}
+                                                    for d, e in tuned["degrees"].items()},
+                                     "note": "each degree bin's fastest one-role shape (the bins have no "
+                                             "warp-specialised form)",
                                      "tuning_seconds": tuned["seconds"]}},
         "roofline": {"bound": "alu", "kernel": "whole step (pack + 12 uneven_solve_kernel launches)",
                      "achieved": (f32 + f64 * p32 / p64) / t / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
