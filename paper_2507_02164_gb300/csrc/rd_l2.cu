@@ -167,14 +167,22 @@ struct L2TablesDF {
     float thi[L2_MAX_DEG + 1][L2_NT][2], tlo[L2_MAX_DEG + 1][L2_NT][2];
 };
 
-__global__ void __launch_bounds__(256) l2_kernel_df(const double2 *__restrict__ samples, int64_t n, int nr,
-                                                    int degree, double2 *coeffs, const L2TablesDF T)
+// NR > 0, DEG >= 0: a build for that radial node count and degree (loops of
+// fixed length, arrays of DEG + 1 coefficients); NR = 0, DEG = -1: the runtime
+// nr and degree, with arrays for L2_MAX_DEG. Both do the same operations in
+// the same order.
+template <int NR, int DEG>
+__global__ void __launch_bounds__(256, 2) l2_kernel_df(const double2 *__restrict__ samples, int64_t n, int nr_arg,
+                                                    int degree_arg, double2 *coeffs, const L2TablesDF T)
 {
+    constexpr int JMAX = DEG >= 0 ? DEG : L2_MAX_DEG;
+    const int nr = NR > 0 ? NR : nr_arg;
+    const int degree = DEG >= 0 ? DEG : degree_arg;
     const int lane = threadIdx.x & 31;
     const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
-    dfl twr[L2_MAX_DEG + 1], twi[L2_MAX_DEG + 1];
+    dfl twr[JMAX + 1], twi[JMAX + 1];
 #pragma unroll
-    for (int j = 0; j <= L2_MAX_DEG; ++j) {
+    for (int j = 0; j <= JMAX; ++j) {
         twr[j] = {T.thi[j][lane][0], T.tlo[j][lane][0]};
         twi[j] = {T.thi[j][lane][1], T.tlo[j][lane][1]};
     }
@@ -182,6 +190,7 @@ __global__ void __launch_bounds__(256) l2_kernel_df(const double2 *__restrict__ 
         const double2 *g = samples + s * (int64_t)nr * L2_NT;
         // per sub-disk scale: the largest biased exponent of its samples
         unsigned emax = 0;
+#pragma unroll(NR > 0 ? NR : 1)
         for (int p = 0; p < nr; ++p) {
             double2 v = __ldg(g + p * L2_NT + lane);
             unsigned ex = ((unsigned)__double2hiint(v.x) >> 20) & 0x7ffu;
@@ -190,14 +199,15 @@ __global__ void __launch_bounds__(256) l2_kernel_df(const double2 *__restrict__ 
         }
         emax = __reduce_max_sync(0xffffffffu, emax);
         const int shift = (int)emax - 1023;
-        dfl ur[L2_MAX_DEG + 1], ui[L2_MAX_DEG + 1];
+        dfl ur[JMAX + 1], ui[JMAX + 1];
 #pragma unroll
-        for (int j = 0; j <= L2_MAX_DEG; ++j) ur[j] = ui[j] = dfl{0.0f, 0.0f};
+        for (int j = 0; j <= JMAX; ++j) ur[j] = ui[j] = dfl{0.0f, 0.0f};
+#pragma unroll 4
         for (int p = 0; p < nr; ++p) {
             double2 v = __ldg(g + p * L2_NT + lane);
             dfl gx = split_scaled(v.x, shift), gy = split_scaled(v.y, shift);
 #pragma unroll
-            for (int j = 0; j <= L2_MAX_DEG; ++j)
+            for (int j = 0; j <= JMAX; ++j)
                 if (j <= degree) {
                     const float wh = T.whi[p][j], wl = T.wlo[p][j];
                     // exact product hi and its error, then TwoSum into the accumulator
@@ -216,14 +226,14 @@ __global__ void __launch_bounds__(256) l2_kernel_df(const double2 *__restrict__ 
                 }
         }
 #pragma unroll
-        for (int j0 = 0; j0 <= L2_MAX_DEG; j0 += 8) {
+        for (int j0 = 0; j0 <= JMAX; j0 += 8) {
             if (j0 > degree) break;
             dfl val[16];
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) {
                 const int j = j0 + jj;
                 dfl vr = {0.0f, 0.0f}, vi = {0.0f, 0.0f};
-                if (j <= L2_MAX_DEG && j <= degree) {
+                if (j <= JMAX && j <= degree) {
                     dfl a = fast_two_sum(ur[j].hi, ur[j].lo), b = fast_two_sum(ui[j].hi, ui[j].lo);
                     vr = df_add(df_mul(a, twr[j]), df_neg(df_mul(b, twi[j])));
                     vi = df_add(df_mul(a, twi[j]), df_mul(b, twr[j]));
@@ -285,8 +295,12 @@ int launch_l2(const double *samples, int64_t n, int nr, int degree, double *coef
         int64_t cap = (int64_t)rd_sm_count_cached() * 8;
         if (ctas > cap) ctas = cap;
         if (ctas < 1) ctas = 1;
-        l2_kernel_df<<<(unsigned)ctas, block, 0, st>>>(reinterpret_cast<const double2 *>(samples), n, nr, degree,
-                                                       reinterpret_cast<double2 *>(coeffs), T);
+        const double2 *sp = reinterpret_cast<const double2 *>(samples);
+        double2 *cp = reinterpret_cast<double2 *>(coeffs);
+        if (nr == 16 && degree == 6)  // the full pipeline's 16 x 32 nodes and degree-6 fits
+            l2_kernel_df<16, 6><<<(unsigned)ctas, block, 0, st>>>(sp, n, nr, degree, cp, T);
+        else
+            l2_kernel_df<0, -1><<<(unsigned)ctas, block, 0, st>>>(sp, n, nr, degree, cp, T);
         return rd_check_launch("l2_kernel_df");
     }
     L2Tables T;
