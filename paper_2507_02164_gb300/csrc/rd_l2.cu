@@ -102,28 +102,35 @@ __device__ __forceinline__ double warp_reduce_scatter(double (&v)[V])
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-__global__ void __launch_bounds__(256) l2_kernel(const double2 *__restrict__ samples, int64_t n, int nr,
-                                                 int degree, double2 *coeffs, const L2Tables T)
+// NR > 0, DEG >= 0: a build for that node count and degree; NR = 0, DEG = -1:
+// runtime bounds (the same operations in the same order).
+template <int NR, int DEG>
+__global__ void __launch_bounds__(256) l2_kernel(const double2 *__restrict__ samples, int64_t n, int nr_arg,
+                                                 int degree_arg, double2 *coeffs, const L2Tables T)
 {
+    constexpr int JMAX = DEG >= 0 ? DEG : L2_MAX_DEG;
+    const int nr = NR > 0 ? NR : nr_arg;
+    const int degree = DEG >= 0 ? DEG : degree_arg;
     const int lane = threadIdx.x & 31;
     const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
     // this lane's twiddles, read once (lanes read different entries, which
     // the constant bank would serialise inside the loop)
-    double twr[L2_MAX_DEG + 1], twi[L2_MAX_DEG + 1];
+    double twr[JMAX + 1], twi[JMAX + 1];
 #pragma unroll
-    for (int j = 0; j <= L2_MAX_DEG; ++j) {
+    for (int j = 0; j <= JMAX; ++j) {
         twr[j] = T.tw[j][lane][0];
         twi[j] = T.tw[j][lane][1];
     }
     for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n; s += warps_total) {
         const double2 *g = samples + s * (int64_t)nr * L2_NT;
-        double ur[L2_MAX_DEG + 1], ui[L2_MAX_DEG + 1];
+        double ur[JMAX + 1], ui[JMAX + 1];
 #pragma unroll
-        for (int j = 0; j <= L2_MAX_DEG; ++j) ur[j] = ui[j] = 0.0;
+        for (int j = 0; j <= JMAX; ++j) ur[j] = ui[j] = 0.0;
+#pragma unroll 4
         for (int p = 0; p < nr; ++p) {
             double2 v = __ldg(g + p * L2_NT + lane);
 #pragma unroll
-            for (int j = 0; j <= L2_MAX_DEG; ++j)
+            for (int j = 0; j <= JMAX; ++j)
                 if (j <= degree) {
                     ur[j] = fma(T.wr[p][j], v.x, ur[j]);
                     ui[j] = fma(T.wr[p][j], v.y, ui[j]);
@@ -132,14 +139,14 @@ __global__ void __launch_bounds__(256) l2_kernel(const double2 *__restrict__ sam
         // angular sums v_j = sum_q u_j(q) e^{-i j theta_q}: this lane's term, then
         // warp sums, 8 coefficients (16 reals) per reduce-scatter pass
 #pragma unroll
-        for (int j0 = 0; j0 <= L2_MAX_DEG; j0 += 8) {
+        for (int j0 = 0; j0 <= JMAX; j0 += 8) {
             if (j0 > degree) break;
             double val[16];
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) {
                 const int j = j0 + jj;
                 double vr = 0.0, vi = 0.0;
-                if (j <= L2_MAX_DEG && j <= degree) {
+                if (j <= JMAX && j <= degree) {
                     vr = fma(ur[j], twr[j], -ui[j] * twi[j]);
                     vi = fma(ur[j], twi[j], ui[j] * twr[j]);
                 }
@@ -326,8 +333,12 @@ int launch_l2(const double *samples, int64_t n, int nr, int degree, double *coef
     int64_t cap = (int64_t)rd_sm_count_cached() * 8;
     if (ctas > cap) ctas = cap;
     if (ctas < 1) ctas = 1;
-    l2_kernel<<<(unsigned)ctas, block, 0, st>>>(reinterpret_cast<const double2 *>(samples), n, nr, degree,
-                                                reinterpret_cast<double2 *>(coeffs), T);
+    const double2 *sp = reinterpret_cast<const double2 *>(samples);
+    double2 *cp = reinterpret_cast<double2 *>(coeffs);
+    if (nr == 16 && degree == 6)
+        l2_kernel<16, 6><<<(unsigned)ctas, block, 0, st>>>(sp, n, nr, degree, cp, T);
+    else
+        l2_kernel<0, -1><<<(unsigned)ctas, block, 0, st>>>(sp, n, nr, degree, cp, T);
     return rd_check_launch("l2_kernel");
 }
 
