@@ -17,7 +17,8 @@ static int ws_allow_smem(size_t bytes)
 {
     static std::atomic<size_t> allowed[64];
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return rd_check_launch("cudaGetDevice");
+    if (cudaGetDevice(&dev) != cudaSuccess) return rd_check_launch("cudaGetDevice");
+    if (dev < 0 || dev >= 64) return rd_set_error(RD_EUNSUPPORTED, "device %d: at most 64 devices", dev);
     if (bytes <= 48 * 1024 || bytes <= allowed[dev].load()) return RD_OK;
     if (cudaFuncSetAttribute(solve_ws_kernel<N, In, MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
         cudaSuccess)
