@@ -53,9 +53,13 @@ __global__ void __launch_bounds__(256) backward_kernel(const void *coeffs, const
             cx<T> dp = scale((T)N, a[N]);
 #pragma unroll
             for (int k = N - 1; k >= 1; --k) dp = cfma(dp, z, scale((T)k, a[k]));
-            // singular: |p'(z)| <= 1e-300 (0 in FP32) or anything non-finite
-            bool bad = !(isfinite(dp.re) && isfinite(dp.im) && isfinite(z.re) && isfinite(z.im)) ||
-                       !(hypot(dp.re, dp.im) > tiny);
+            // singular: |p'(z)| <= 1e-300 (0 in FP32) or anything non-finite. The
+            // larger component m decides almost always (|p'| > tiny when m > tiny,
+            // |p'| <= tiny when m <= tiny / sqrt 2); hypot only in between.
+            const T m = fmax(fabs(dp.re), fabs(dp.im));
+            bool big = m > tiny;
+            if (!big && m > tiny * (T)0.70710678118654752) big = hypot(dp.re, dp.im) > tiny;
+            bool bad = !(isfinite(dp.re) && isfinite(dp.im) && isfinite(z.re) && isfinite(z.im)) || !big;
             singular |= bad;
             if (bad) continue;
             // u = conj(-1/dp) * gz = -(dp / |dp|^2) * gz
