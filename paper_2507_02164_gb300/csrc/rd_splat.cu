@@ -39,10 +39,13 @@ struct SplatGeom {
     double sigma, inv_2s2, inv_s2, step, cut, scale, cut_s;  // cut_s = cut * scale
 };
 
-// First pixel index and the count along one axis (<= SPLAT_K), and the 13
-// Gaussian factors e(d0 - k), d0 = u - (i0 + 1/2). Returns 0 when nothing is
+// First pixel index and the count along one axis, and the K Gaussian
+// factors e(d0 - k), d0 = u - (i0 + 1/2). K = floor(6 sigma) + 1 covers the
+// pixels within 3 sigma (a count above K, which only FP64 rounding of the box
+// ends can give, adds a pixel whose weight is 0). Returns 0 when nothing is
 // visited (non-finite coordinate or the box outside the image).
-__device__ __forceinline__ int splat_axis(const SplatGeom &g, double u, int n_pix, int &i0, double (&e)[SPLAT_K],
+template <int K>
+__device__ __forceinline__ int splat_axis(const SplatGeom &g, double u, int n_pix, int &i0, double (&e)[K],
                                           double &d0)
 {
     if (!finite_bits(u)) return 0;
@@ -56,7 +59,7 @@ __device__ __forceinline__ int splat_axis(const SplatGeom &g, double u, int n_pi
     double ek = exp(-d0 * d0 * g.inv_2s2);
     double q = exp((2.0 * d0 - 1.0) * g.inv_2s2);
 #pragma unroll
-    for (int k = 0; k < SPLAT_K; ++k) {
+    for (int k = 0; k < K; ++k) {
         e[k] = ek;
         ek *= q;
         q *= g.step;
@@ -64,6 +67,7 @@ __device__ __forceinline__ int splat_axis(const SplatGeom &g, double u, int n_pi
     return cnt;
 }
 
+template <int K>
 __global__ void __launch_bounds__(256) splat_kernel(const double2 *__restrict__ roots, int64_t n, SplatGeom g,
                                                     double *img)
 {
@@ -71,21 +75,21 @@ __global__ void __launch_bounds__(256) splat_kernel(const double2 *__restrict__ 
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         const double2 z = __ldg(roots + j);
         const double u = (z.x - g.xmin) / g.px, v = (g.ymax - z.y) / g.py;
-        double ex[SPLAT_K], ey[SPLAT_K], dx0, dy0;
+        double ex[K], ey[K], dx0, dy0;
         int x0, y0;
-        const int nx = splat_axis(g, u, g.W, x0, ex, dx0);
-        const int ny = nx ? splat_axis(g, v, g.H, y0, ey, dy0) : 0;
+        const int nx = splat_axis<K>(g, u, g.W, x0, ex, dx0);
+        const int ny = nx ? splat_axis<K>(g, v, g.H, y0, ey, dy0) : 0;
         if (!ny) continue;
         // scale * (e(du) e(dv) - cut) = e(du) (scale e(dv)) - scale cut: one FMA
         // per pixel; w > 0 is read off the sign and magnitude bits (an
         // integer compare: FP64 compares issue to the FP64 pipe)
 #pragma unroll
-        for (int ky = 0; ky < SPLAT_K; ++ky) {
+        for (int ky = 0; ky < K; ++ky) {
             if (ky >= ny) break;
             double *row = img + (size_t)(y0 + ky) * g.W + x0;
             const double eys = ey[ky] * g.scale;
 #pragma unroll
-            for (int kx = 0; kx < SPLAT_K; ++kx) {
+            for (int kx = 0; kx < K; ++kx) {
                 const double w = fma(ex[kx], eys, -g.cut_s);
                 if (kx < nx && __double_as_longlong(w) > 0) atomicAdd(row + kx, w);
             }
@@ -93,6 +97,7 @@ __global__ void __launch_bounds__(256) splat_kernel(const double2 *__restrict__ 
     }
 }
 
+template <int K>
 __global__ void __launch_bounds__(256) splat_backward_kernel(const double2 *__restrict__ roots, int64_t n, SplatGeom g,
                                                              const double *__restrict__ G, double2 *grad)
 {
@@ -100,24 +105,24 @@ __global__ void __launch_bounds__(256) splat_backward_kernel(const double2 *__re
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         const double2 z = __ldg(roots + j);
         const double u = (z.x - g.xmin) / g.px, v = (g.ymax - z.y) / g.py;
-        double ex[SPLAT_K], ey[SPLAT_K], dx0, dy0;
+        double ex[K], ey[K], dx0, dy0;
         int x0, y0;
-        const int nx = splat_axis(g, u, g.W, x0, ex, dx0);
-        const int ny = nx ? splat_axis(g, v, g.H, y0, ey, dy0) : 0;
+        const int nx = splat_axis<K>(g, u, g.W, x0, ex, dx0);
+        const int ny = nx ? splat_axis<K>(g, v, g.H, y0, ey, dy0) : 0;
         double gu = 0.0, gv = 0.0;
         if (ny) {
-            double dx[SPLAT_K];  // du of each column
+            double dx[K];  // du of each column
 #pragma unroll
-            for (int kx = 0; kx < SPLAT_K; ++kx) dx[kx] = dx0 - kx;
+            for (int kx = 0; kx < K; ++kx) dx[kx] = dx0 - kx;
             const long long cut_bits = __double_as_longlong(g.cut);
 #pragma unroll
-            for (int ky = 0; ky < SPLAT_K; ++ky) {
+            for (int ky = 0; ky < K; ++ky) {
                 if (ky >= ny) break;
                 const double *row = G + (size_t)(y0 + ky) * g.W + x0;
                 const double dv = dy0 - ky;
                 double su = 0.0, sv = 0.0;
 #pragma unroll
-                for (int kx = 0; kx < SPLAT_K; ++kx) {
+                for (int kx = 0; kx < K; ++kx) {
                     const double e = ex[kx] * ey[ky];
                     // e > cut for positive doubles, on the bits (integer pipe)
                     if (kx < nx && __double_as_longlong(e) > cut_bits) {
@@ -147,7 +152,8 @@ struct SplatGeomF {
     float sigma, inv_2s2, inv_s2, step, cut, scale, cut_s;
 };
 
-__device__ __forceinline__ int splat_axis_f(const SplatGeomF &g, double u, int n_pix, int &i0, float (&e)[SPLAT_K],
+template <int K>
+__device__ __forceinline__ int splat_axis_f(const SplatGeomF &g, double u, int n_pix, int &i0, float (&e)[K],
                                             float &d0)
 {
     if (!finite_bits(u)) return 0;
@@ -161,7 +167,7 @@ __device__ __forceinline__ int splat_axis_f(const SplatGeomF &g, double u, int n
     float ek = __expf(-d0 * d0 * g.inv_2s2);
     float q = __expf((2.0f * d0 - 1.0f) * g.inv_2s2);
 #pragma unroll
-    for (int k = 0; k < SPLAT_K; ++k) {
+    for (int k = 0; k < K; ++k) {
         e[k] = ek;
         ek *= q;
         q *= g.step;
@@ -169,6 +175,7 @@ __device__ __forceinline__ int splat_axis_f(const SplatGeomF &g, double u, int n
     return cnt;
 }
 
+template <int K>
 __global__ void __launch_bounds__(256) splat_kernel_f32(const double2 *__restrict__ roots, int64_t n, SplatGeom g,
                                                         SplatGeomF gf, double *img)
 {
@@ -176,18 +183,18 @@ __global__ void __launch_bounds__(256) splat_kernel_f32(const double2 *__restric
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         const double2 z = __ldg(roots + j);
         const double u = (z.x - g.xmin) / g.px, v = (g.ymax - z.y) / g.py;
-        float ex[SPLAT_K], ey[SPLAT_K], dx0, dy0;
+        float ex[K], ey[K], dx0, dy0;
         int x0, y0;
-        const int nx = splat_axis_f(gf, u, g.W, x0, ex, dx0);
-        const int ny = nx ? splat_axis_f(gf, v, g.H, y0, ey, dy0) : 0;
+        const int nx = splat_axis_f<K>(gf, u, g.W, x0, ex, dx0);
+        const int ny = nx ? splat_axis_f<K>(gf, v, g.H, y0, ey, dy0) : 0;
         if (!ny) continue;
 #pragma unroll
-        for (int ky = 0; ky < SPLAT_K; ++ky) {
+        for (int ky = 0; ky < K; ++ky) {
             if (ky >= ny) break;
             double *row = img + (size_t)(y0 + ky) * g.W + x0;
             const float eys = ey[ky] * gf.scale;
 #pragma unroll
-            for (int kx = 0; kx < SPLAT_K; ++kx) {
+            for (int kx = 0; kx < K; ++kx) {
                 const float w = fmaf(ex[kx], eys, -gf.cut_s);
                 if (kx < nx && __float_as_int(w) > 0) atomicAdd(row + kx, f2d(w));
             }
@@ -195,6 +202,7 @@ __global__ void __launch_bounds__(256) splat_kernel_f32(const double2 *__restric
     }
 }
 
+template <int K>
 __global__ void __launch_bounds__(256) splat_backward_kernel_f32(const double2 *__restrict__ roots, int64_t n,
                                                                  SplatGeom g, SplatGeomF gf,
                                                                  const double *__restrict__ G, double2 *grad)
@@ -203,20 +211,20 @@ __global__ void __launch_bounds__(256) splat_backward_kernel_f32(const double2 *
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         const double2 z = __ldg(roots + j);
         const double u = (z.x - g.xmin) / g.px, v = (g.ymax - z.y) / g.py;
-        float ex[SPLAT_K], ey[SPLAT_K], dx0, dy0;
+        float ex[K], ey[K], dx0, dy0;
         int x0, y0;
-        const int nx = splat_axis_f(gf, u, g.W, x0, ex, dx0);
-        const int ny = nx ? splat_axis_f(gf, v, g.H, y0, ey, dy0) : 0;
+        const int nx = splat_axis_f<K>(gf, u, g.W, x0, ex, dx0);
+        const int ny = nx ? splat_axis_f<K>(gf, v, g.H, y0, ey, dy0) : 0;
         float gu = 0.0f, gv = 0.0f;
         if (ny) {
             const int cut_bits = __float_as_int(gf.cut);
 #pragma unroll
-            for (int ky = 0; ky < SPLAT_K; ++ky) {
+            for (int ky = 0; ky < K; ++ky) {
                 if (ky >= ny) break;
                 const double *row = G + (size_t)(y0 + ky) * g.W + x0;
                 float su = 0.0f, sv = 0.0f;
 #pragma unroll
-                for (int kx = 0; kx < SPLAT_K; ++kx) {
+                for (int kx = 0; kx < K; ++kx) {
                     const float e = ex[kx] * ey[ky];
                     if (kx < nx && __float_as_int(e) > cut_bits) {
                         const float ge = d2f(__ldg(row + kx)) * e;
@@ -273,16 +281,31 @@ static SplatGeomF splat_geom_f(const SplatGeom &g)
     return f;
 }
 
+// Stencil width built for sigma: floor(6 sigma) + 1 pixels per axis, rounded
+// up to a built width (sigma in (0, 2]: at most 13).
+static int splat_width(double sigma)
+{
+    const int k = (int)std::floor(6.0 * sigma) + 1;
+    return k <= 4 ? 4 : (k <= 7 ? 7 : (k <= 10 ? 10 : SPLAT_K));
+}
+
 int launch_splat(const double *roots, int64_t n, const rd_window &w, int W, int H, double sigma, double scale,
                  int precision, double *img, cudaStream_t st)
 {
     const SplatGeom g = splat_geom(w, W, H, sigma, scale);
+    const int K = splat_width(sigma);
+    auto z = reinterpret_cast<const double2 *>(roots);
     if (precision == RD_SPLAT_FP32) {
-        splat_kernel_f32<<<splat_grid(n), 256, 0, st>>>(reinterpret_cast<const double2 *>(roots), n, g,
-                                                        splat_geom_f(g), img);
+#define RD_SPLAT_F(KK) \
+    if (K == KK) splat_kernel_f32<KK><<<splat_grid(n), 256, 0, st>>>(z, n, g, splat_geom_f(g), img);
+        RD_SPLAT_F(4) RD_SPLAT_F(7) RD_SPLAT_F(10) RD_SPLAT_F(13)
+#undef RD_SPLAT_F
         return rd_check_launch("splat_kernel_f32");
     }
-    splat_kernel<<<splat_grid(n), 256, 0, st>>>(reinterpret_cast<const double2 *>(roots), n, g, img);
+#define RD_SPLAT_D(KK) \
+    if (K == KK) splat_kernel<KK><<<splat_grid(n), 256, 0, st>>>(z, n, g, img);
+    RD_SPLAT_D(4) RD_SPLAT_D(7) RD_SPLAT_D(10) RD_SPLAT_D(13)
+#undef RD_SPLAT_D
     return rd_check_launch("splat_kernel");
 }
 
@@ -290,14 +313,20 @@ int launch_splat_backward(const double *roots, int64_t n, const rd_window &w, in
                           double scale, int precision, const double *G, double *grad, cudaStream_t st)
 {
     const SplatGeom g = splat_geom(w, W, H, sigma, scale);
+    const int K = splat_width(sigma);
+    auto z = reinterpret_cast<const double2 *>(roots);
+    auto gr = reinterpret_cast<double2 *>(grad);
     if (precision == RD_SPLAT_FP32) {
-        splat_backward_kernel_f32<<<splat_grid(n), 256, 0, st>>>(reinterpret_cast<const double2 *>(roots), n, g,
-                                                                 splat_geom_f(g), G,
-                                                                 reinterpret_cast<double2 *>(grad));
+#define RD_SPLAT_BF(KK) \
+    if (K == KK) splat_backward_kernel_f32<KK><<<splat_grid(n), 256, 0, st>>>(z, n, g, splat_geom_f(g), G, gr);
+        RD_SPLAT_BF(4) RD_SPLAT_BF(7) RD_SPLAT_BF(10) RD_SPLAT_BF(13)
+#undef RD_SPLAT_BF
         return rd_check_launch("splat_backward_kernel_f32");
     }
-    splat_backward_kernel<<<splat_grid(n), 256, 0, st>>>(reinterpret_cast<const double2 *>(roots), n, g, G,
-                                                         reinterpret_cast<double2 *>(grad));
+#define RD_SPLAT_BD(KK) \
+    if (K == KK) splat_backward_kernel<KK><<<splat_grid(n), 256, 0, st>>>(z, n, g, G, gr);
+    RD_SPLAT_BD(4) RD_SPLAT_BD(7) RD_SPLAT_BD(10) RD_SPLAT_BD(13)
+#undef RD_SPLAT_BD
     return rd_check_launch("splat_backward_kernel");
 }
 
