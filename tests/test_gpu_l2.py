@@ -35,11 +35,14 @@ def test_l2_worked_example(dev):
     assert np.abs(a - 0.3 ** np.arange(7)).max() <= 1e-14
 
 
-@pytest.mark.parametrize("degree,nr", [(0, 1), (3, 8), (12, 32)])
-def test_l2_degree_and_radial_order_range(dev, orc, degree, nr):
+# (16, 6) runs the build specialised for the pipeline's node count and
+# degree; every other pair the build with runtime bounds
+@pytest.mark.parametrize("degree,nr", [(0, 1), (3, 8), (12, 32), (6, 8), (5, 16), (6, 16)])
+@pytest.mark.parametrize("precision", ["fp64", "df"])
+def test_l2_degree_and_radial_order_range(dev, orc, degree, nr, precision):
     g = np.random.default_rng(degree)
     s = g.standard_normal((100, nr * 32)) + 1j * g.standard_normal((100, nr * 32))
-    got = api.l2_approx(torch.from_numpy(s).to(dev), nr, 32, degree).cpu().numpy().T
+    got = api.l2_approx(torch.from_numpy(s).to(dev), nr, 32, degree, precision=precision).cpu().numpy().T
     ref = orc.l2_approx(s, nr=nr, nt=32, degree=degree)
     assert np.abs(got - ref).max() <= 1e-12
 
