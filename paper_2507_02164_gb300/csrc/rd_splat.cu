@@ -25,6 +25,7 @@
 //     dL/du = scale sum G dw/du with dw/du = -(du / s^2) e(du) e(dv) where
 //     w > 0; dL/dx = (dL/du) / px, dL/dy = -(dL/dv) / py (PyTorch's
 //     convention for a complex root: dL/dRe + i dL/dIm).
+#include <atomic>
 #include <cmath>
 
 #include "rd_common.cuh"
@@ -111,28 +112,30 @@ __global__ void __launch_bounds__(256) splat_backward_kernel(const double2 *__re
         const int ny = nx ? splat_axis<K>(g, v, g.H, y0, ey, dy0) : 0;
         double gu = 0.0, gv = 0.0;
         if (ny) {
-            double dx[K];  // du of each column
+            // the Gaussian separates: sum G e(du) e(dv) du over a row is
+            // e(dv) sum G (e(du) du), so per pixel two FMAs on column factors
+            // fixed per root, and e(du) e(dv) only for the cut test
+            double edx[K];
 #pragma unroll
-            for (int kx = 0; kx < K; ++kx) dx[kx] = dx0 - kx;
+            for (int kx = 0; kx < K; ++kx) edx[kx] = ex[kx] * (dx0 - kx);
             const long long cut_bits = __double_as_longlong(g.cut);
 #pragma unroll
             for (int ky = 0; ky < K; ++ky) {
                 if (ky >= ny) break;
                 const double *row = G + (size_t)(y0 + ky) * g.W + x0;
-                const double dv = dy0 - ky;
                 double su = 0.0, sv = 0.0;
 #pragma unroll
                 for (int kx = 0; kx < K; ++kx) {
                     const double e = ex[kx] * ey[ky];
                     // e > cut for positive doubles, on the bits (integer pipe)
                     if (kx < nx && __double_as_longlong(e) > cut_bits) {
-                        const double ge = __ldg(row + kx) * e;
-                        su = fma(ge, dx[kx], su);
-                        sv += ge;
+                        const double gp = __ldg(row + kx);
+                        su = fma(gp, edx[kx], su);
+                        sv = fma(gp, ex[kx], sv);
                     }
                 }
-                gu += su;
-                gv = fma(sv, dv, gv);
+                gu = fma(ey[ky], su, gu);
+                gv = fma(ey[ky] * (dy0 - ky), sv, gv);
             }
         }
         // dw/du = -(du / s^2) e, dw/dv = -(dv / s^2) e
@@ -199,6 +202,49 @@ __global__ void __launch_bounds__(256) splat_kernel_f32(const double2 *__restric
                 if (kx < nx && __float_as_int(w) > 0) atomicAdd(row + kx, f2d(w));
             }
         }
+    }
+}
+
+// The same FP32 forward with the image accumulated per CTA in shared memory
+// (float, W x H <= SPLAT_SMEM_PIXELS): shared-memory atomic adds per root and
+// pixel, then one FP64 global atomic add per touched pixel per CTA instead
+// of one per root and pixel (at sigma 1.5 a root touches about 70 pixels).
+// The partial sums stay within the FP32 variant's 1e-6.
+constexpr int SPLAT_SMEM_PIXELS = 48 * 1024;  // 192 KB of floats
+
+template <int K>
+__global__ void __launch_bounds__(1024, 1) splat_kernel_f32_smem(const double2 *__restrict__ roots, int64_t n,
+                                                                 SplatGeom g, SplatGeomF gf, double *img)
+{
+    extern __shared__ float s_img[];
+    const int npix = g.W * g.H;
+    for (int p = threadIdx.x; p < npix; p += blockDim.x) s_img[p] = 0.0f;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const double2 z = __ldg(roots + j);
+        const double u = (z.x - g.xmin) / g.px, v = (g.ymax - z.y) / g.py;
+        float ex[K], ey[K], dx0, dy0;
+        int x0, y0;
+        const int nx = splat_axis_f<K>(gf, u, g.W, x0, ex, dx0);
+        const int ny = nx ? splat_axis_f<K>(gf, v, g.H, y0, ey, dy0) : 0;
+        if (!ny) continue;
+#pragma unroll
+        for (int ky = 0; ky < K; ++ky) {
+            if (ky >= ny) break;
+            float *row = s_img + (y0 + ky) * g.W + x0;
+            const float eys = ey[ky] * gf.scale;
+#pragma unroll
+            for (int kx = 0; kx < K; ++kx) {
+                const float w = fmaf(ex[kx], eys, -gf.cut_s);
+                if (kx < nx && __float_as_int(w) > 0) atomicAdd(row + kx, w);
+            }
+        }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < npix; p += blockDim.x) {
+        const float w = s_img[p];
+        if (w != 0.0f) atomicAdd(img + p, f2d(w));
     }
 }
 
@@ -289,6 +335,30 @@ static int splat_width(double sigma)
     return k <= 4 ? 4 : (k <= 7 ? 7 : (k <= 10 ? 10 : SPLAT_K));
 }
 
+// Shared memory above 48 KB for splat_kernel_f32_smem<K>: opted in per
+// device and width, once, to the largest size asked for.
+static int splat_allow_smem(int K, size_t bytes)
+{
+    static std::atomic<size_t> allowed[64][4];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return rd_check_launch("cudaGetDevice");
+    if (dev < 0 || dev >= 64) return rd_set_error(RD_EUNSUPPORTED, "device %d: at most 64 devices", dev);
+    const int w = K == 4 ? 0 : (K == 7 ? 1 : (K == 10 ? 2 : 3));
+    if (bytes <= 48 * 1024 || bytes <= allowed[dev][w].load()) return RD_OK;
+    cudaError_t e = cudaSuccess;
+    switch (w) {
+    case 0: e = cudaFuncSetAttribute(splat_kernel_f32_smem<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); break;
+    case 1: e = cudaFuncSetAttribute(splat_kernel_f32_smem<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); break;
+    case 2: e = cudaFuncSetAttribute(splat_kernel_f32_smem<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); break;
+    default: e = cudaFuncSetAttribute(splat_kernel_f32_smem<13>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    }
+    if (e != cudaSuccess) return rd_check_launch("cudaFuncSetAttribute(splat_kernel_f32_smem)");
+    size_t cur = allowed[dev][w].load();
+    while (cur < bytes && !allowed[dev][w].compare_exchange_weak(cur, bytes)) {
+    }
+    return RD_OK;
+}
+
 int launch_splat(const double *roots, int64_t n, const rd_window &w, int W, int H, double sigma, double scale,
                  int precision, double *img, cudaStream_t st)
 {
@@ -296,6 +366,20 @@ int launch_splat(const double *roots, int64_t n, const rd_window &w, int W, int 
     const int K = splat_width(sigma);
     auto z = reinterpret_cast<const double2 *>(roots);
     if (precision == RD_SPLAT_FP32) {
+        if ((int64_t)W * H <= SPLAT_SMEM_PIXELS) {
+            const size_t smem = (size_t)W * H * sizeof(float);
+            int rc = splat_allow_smem(K, smem);
+            if (rc) return rc;
+            int64_t ctas = (n + 1023) / 1024;
+            const int64_t cap = rd_sm_count_cached();
+            if (ctas > cap) ctas = cap;
+            if (ctas < 1) ctas = 1;
+#define RD_SPLAT_S(KK) \
+    if (K == KK) splat_kernel_f32_smem<KK><<<(unsigned)ctas, 1024, smem, st>>>(z, n, g, splat_geom_f(g), img);
+            RD_SPLAT_S(4) RD_SPLAT_S(7) RD_SPLAT_S(10) RD_SPLAT_S(13)
+#undef RD_SPLAT_S
+            return rd_check_launch("splat_kernel_f32_smem");
+        }
 #define RD_SPLAT_F(KK) \
     if (K == KK) splat_kernel_f32<KK><<<splat_grid(n), 256, 0, st>>>(z, n, g, splat_geom_f(g), img);
         RD_SPLAT_F(4) RD_SPLAT_F(7) RD_SPLAT_F(10) RD_SPLAT_F(13)
