@@ -287,6 +287,52 @@ __global__ void __launch_bounds__(256) splat_backward_kernel_f32(const double2 *
     }
 }
 
+// The same FP32 pull-back with dL/dimg staged once per CTA in shared memory
+// as float (W x H <= SPLAT_SMEM_PIXELS): the stencil then reads floats from
+// shared memory instead of converting an FP64 global value per pixel.
+template <int K>
+__global__ void __launch_bounds__(1024, 1) splat_backward_kernel_f32_smem(const double2 *__restrict__ roots,
+                                                                          int64_t n, SplatGeom g, SplatGeomF gf,
+                                                                          const double *__restrict__ G, double2 *grad)
+{
+    extern __shared__ float s_g[];
+    const int npix = g.W * g.H;
+    for (int p = threadIdx.x; p < npix; p += blockDim.x) s_g[p] = d2f(__ldg(G + p));
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const double2 z = __ldg(roots + j);
+        const double u = (z.x - g.xmin) / g.px, v = (g.ymax - z.y) / g.py;
+        float ex[K], ey[K], dx0, dy0;
+        int x0, y0;
+        const int nx = splat_axis_f<K>(gf, u, g.W, x0, ex, dx0);
+        const int ny = nx ? splat_axis_f<K>(gf, v, g.H, y0, ey, dy0) : 0;
+        float gu = 0.0f, gv = 0.0f;
+        if (ny) {
+            const int cut_bits = __float_as_int(gf.cut);
+#pragma unroll
+            for (int ky = 0; ky < K; ++ky) {
+                if (ky >= ny) break;
+                const float *row = s_g + (y0 + ky) * g.W + x0;
+                float su = 0.0f, sv = 0.0f;
+#pragma unroll
+                for (int kx = 0; kx < K; ++kx) {
+                    const float e = ex[kx] * ey[ky];
+                    if (kx < nx && __float_as_int(e) > cut_bits) {
+                        const float ge = row[kx] * e;
+                        su = fmaf(ge, dx0 - (float)kx, su);
+                        sv += ge;
+                    }
+                }
+                gu += su;
+                gv = fmaf(sv, dy0 - (float)ky, gv);
+            }
+        }
+        const float k = -gf.scale * gf.inv_s2;
+        grad[j] = make_double2(f2d(k * gu) / g.px, -f2d(k * gv) / g.py);
+    }
+}
+
 static SplatGeom splat_geom(const rd_window &w, int W, int H, double sigma, double scale)
 {
     SplatGeom g;
@@ -335,28 +381,33 @@ static int splat_width(double sigma)
     return k <= 4 ? 4 : (k <= 7 ? 7 : (k <= 10 ? 10 : SPLAT_K));
 }
 
-// Shared memory above 48 KB for splat_kernel_f32_smem<K>: opted in per
-// device and width, once, to the largest size asked for.
-static int splat_allow_smem(int K, size_t bytes)
+// Shared memory above 48 KB for the *_f32_smem kernels: opted in per
+// device, kernel and width, once, to the largest size asked for.
+template <typename Kern>
+static int splat_allow_smem(Kern kern, int slot, size_t bytes)
 {
-    static std::atomic<size_t> allowed[64][4];
+    static std::atomic<size_t> allowed[64][8];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return rd_check_launch("cudaGetDevice");
     if (dev < 0 || dev >= 64) return rd_set_error(RD_EUNSUPPORTED, "device %d: at most 64 devices", dev);
-    const int w = K == 4 ? 0 : (K == 7 ? 1 : (K == 10 ? 2 : 3));
-    if (bytes <= 48 * 1024 || bytes <= allowed[dev][w].load()) return RD_OK;
-    cudaError_t e = cudaSuccess;
-    switch (w) {
-    case 0: e = cudaFuncSetAttribute(splat_kernel_f32_smem<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); break;
-    case 1: e = cudaFuncSetAttribute(splat_kernel_f32_smem<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); break;
-    case 2: e = cudaFuncSetAttribute(splat_kernel_f32_smem<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); break;
-    default: e = cudaFuncSetAttribute(splat_kernel_f32_smem<13>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    }
-    if (e != cudaSuccess) return rd_check_launch("cudaFuncSetAttribute(splat_kernel_f32_smem)");
-    size_t cur = allowed[dev][w].load();
-    while (cur < bytes && !allowed[dev][w].compare_exchange_weak(cur, bytes)) {
+    if (bytes <= 48 * 1024 || bytes <= allowed[dev][slot].load()) return RD_OK;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+        return rd_check_launch("cudaFuncSetAttribute(splat smem kernel)");
+    size_t cur = allowed[dev][slot].load();
+    while (cur < bytes && !allowed[dev][slot].compare_exchange_weak(cur, bytes)) {
     }
     return RD_OK;
+}
+
+static int splat_slot(int K) { return K == 4 ? 0 : (K == 7 ? 1 : (K == 10 ? 2 : 3)); }
+
+// One CTA of 1024 threads per SM at most (the shared image).
+static unsigned splat_smem_grid(int64_t n)
+{
+    int64_t ctas = (n + 1023) / 1024;
+    const int64_t cap = rd_sm_count_cached();
+    if (ctas > cap) ctas = cap;
+    return (unsigned)(ctas < 1 ? 1 : ctas);
 }
 
 int launch_splat(const double *roots, int64_t n, const rd_window &w, int W, int H, double sigma, double scale,
@@ -368,14 +419,12 @@ int launch_splat(const double *roots, int64_t n, const rd_window &w, int W, int 
     if (precision == RD_SPLAT_FP32) {
         if ((int64_t)W * H <= SPLAT_SMEM_PIXELS) {
             const size_t smem = (size_t)W * H * sizeof(float);
-            int rc = splat_allow_smem(K, smem);
-            if (rc) return rc;
-            int64_t ctas = (n + 1023) / 1024;
-            const int64_t cap = rd_sm_count_cached();
-            if (ctas > cap) ctas = cap;
-            if (ctas < 1) ctas = 1;
-#define RD_SPLAT_S(KK) \
-    if (K == KK) splat_kernel_f32_smem<KK><<<(unsigned)ctas, 1024, smem, st>>>(z, n, g, splat_geom_f(g), img);
+#define RD_SPLAT_S(KK)                                                                                  \
+    if (K == KK) {                                                                                      \
+        int rc = splat_allow_smem(splat_kernel_f32_smem<KK>, splat_slot(KK), smem);                     \
+        if (rc) return rc;                                                                              \
+        splat_kernel_f32_smem<KK><<<splat_smem_grid(n), 1024, smem, st>>>(z, n, g, splat_geom_f(g), img); \
+    }
             RD_SPLAT_S(4) RD_SPLAT_S(7) RD_SPLAT_S(10) RD_SPLAT_S(13)
 #undef RD_SPLAT_S
             return rd_check_launch("splat_kernel_f32_smem");
@@ -401,6 +450,18 @@ int launch_splat_backward(const double *roots, int64_t n, const rd_window &w, in
     auto z = reinterpret_cast<const double2 *>(roots);
     auto gr = reinterpret_cast<double2 *>(grad);
     if (precision == RD_SPLAT_FP32) {
+        if ((int64_t)W * H <= SPLAT_SMEM_PIXELS) {
+            const size_t smem = (size_t)W * H * sizeof(float);
+#define RD_SPLAT_BS(KK)                                                                                       \
+    if (K == KK) {                                                                                            \
+        int rc = splat_allow_smem(splat_backward_kernel_f32_smem<KK>, 4 + splat_slot(KK), smem);              \
+        if (rc) return rc;                                                                                    \
+        splat_backward_kernel_f32_smem<KK><<<splat_smem_grid(n), 1024, smem, st>>>(z, n, g, splat_geom_f(g), G, gr); \
+    }
+            RD_SPLAT_BS(4) RD_SPLAT_BS(7) RD_SPLAT_BS(10) RD_SPLAT_BS(13)
+#undef RD_SPLAT_BS
+            return rd_check_launch("splat_backward_kernel_f32_smem");
+        }
 #define RD_SPLAT_BF(KK) \
     if (K == KK) splat_backward_kernel_f32<KK><<<splat_grid(n), 256, 0, st>>>(z, n, g, splat_geom_f(g), G, gr);
         RD_SPLAT_BF(4) RD_SPLAT_BF(7) RD_SPLAT_BF(10) RD_SPLAT_BF(13)
