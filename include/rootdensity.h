@@ -66,7 +66,8 @@ typedef struct {
     double residual_tol;   /* RD_MIXED: reject when |p(z)| > residual_tol * sum_k |a_k||z|^k;
                               <= 0 means 64 * d * 2^-53                                         */
     double collapse_tol;   /* RD_MIXED: reject when two roots lie within collapse_tol * max(1,|z|) */
-    int32_t block;         /* threads per CTA, multiple of 32 in [32, 256]; 0 = tuned default    */
+    int32_t block;         /* threads per CTA, multiple of 32 in [32, 256] (up to 512 with
+                              polish_warps > 0, see below); 0 = the default                  */
     int32_t ctas_per_sm;   /* grid = ctas_per_sm x SM count; 0 = tuned default                   */
     int32_t polish_extra;  /* RD_MIXED: further Newton steps, p and p' both in FP64, for a root
                               that fails the residual check after polish_steps (0..16)          */
