@@ -1192,7 +1192,10 @@ def small_batch_latency(api, WL, torch, dev, stream, reps=20, warmup=3):
     coeffs = torch.from_numpy(np.ascontiguousarray(co.T)).to(dev)
     hist = api.new_hist(W_PIX, H_PIX, dev)
     win = api.Window(-1.5, 1.5, -0.84375, 0.84375)
-    p = api.params("plain")
+    # the launch shape tuned at this batch size (complex128, degree 6, plain)
+    from paper_2507_02164_gb300 import autotune
+    shape = autotune.tune("plain", dtype=torch.complex128, degrees=[6], n=n)["degrees"]["6"]
+    p = autotune.degree_params({"degrees": {"6": shape}}, 6, "plain")
     api.roots_density(coeffs, win, hist, mode="plain", params_=p)  # loads the kernel, sizes the grid
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
@@ -1222,6 +1225,7 @@ def small_batch_latency(api, WL, torch, dev, stream, reps=20, warmup=3):
     err["reference"] = "the seeded roots each polynomial was expanded from (FP64)"
     return {"polys": n, "mode": "plain FP64 (tol 1e-13)", "median_ms": med, "min_ms": times[0],
             "polys_per_s": n / (med * 1e-3), "binned": int(hist.sum()), "root_error": err,
+            "launch_shape": {k: shape[k] for k in ("lanes", "block", "ctas_per_sm", "ms")},
             "note": "unit-disk roots (seed 1), complex128, one graph replay = histogram clear + fused solve"}
 
 

@@ -1,8 +1,8 @@
 """Launch-shape autotuner for the solve kernels.
 
 For each degree the candidates are the lanes per polynomial (one thread per
-matrix, or two lanes sharing it; degree >= 2), a threads-per-CTA size (64,
-128, 256) and a number of resident CTAs per SM (the occupancy maximum, or
+matrix, or two lanes sharing it; degree >= 2), a threads-per-CTA size (32,
+64, 128, 256; small CTAs spread a small batch over more SMs) and a number of resident CTAs per SM (the occupancy maximum, or
 fewer), all with every warp sweeping and then polishing its own polynomials;
 and, for the mixed mode, warp-specialised CTAs (params.polish_warps: some
 warps polish what the others sweep) of several sizes and splits. Each
@@ -23,8 +23,8 @@ import torch
 
 from . import api, workloads as WL
 
-BLOCKS = (64, 128, 256)
-CACHE_FORMAT = 3  # table rows [lanes, block, ctas_per_sm, polish_warps, ms]
+BLOCKS = (32, 64, 128, 256)
+CACHE_FORMAT = 4  # table rows [lanes, block, ctas_per_sm, polish_warps, ms]
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "rootdensity_tuning.json")
 
 
