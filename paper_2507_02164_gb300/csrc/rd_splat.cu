@@ -36,6 +36,7 @@ constexpr int SPLAT_K = 13;  // stencil width for sigma <= 2
 
 struct SplatGeom {
     double xmin, ymax, px, py;
+    double inv_px, inv_py;  // 1 / px, 1 / py: products instead of FP64 divisions per root
     int W, H;
     double sigma, inv_2s2, inv_s2, step, cut, scale, cut_s;  // cut_s = cut * scale
 };
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(256) splat_kernel(const double2 *__restrict__ 
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         const double2 z = __ldg(roots + j);
-        const double u = (z.x - g.xmin) / g.px, v = (g.ymax - z.y) / g.py;
+        const double u = (z.x - g.xmin) * g.inv_px, v = (g.ymax - z.y) * g.inv_py;
         double ex[K], ey[K], dx0, dy0;
         int x0, y0;
         const int nx = splat_axis<K>(g, u, g.W, x0, ex, dx0);
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(256) splat_backward_kernel(const double2 *__re
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         const double2 z = __ldg(roots + j);
-        const double u = (z.x - g.xmin) / g.px, v = (g.ymax - z.y) / g.py;
+        const double u = (z.x - g.xmin) * g.inv_px, v = (g.ymax - z.y) * g.inv_py;
         double ex[K], ey[K], dx0, dy0;
         int x0, y0;
         const int nx = splat_axis<K>(g, u, g.W, x0, ex, dx0);
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(256) splat_backward_kernel(const double2 *__re
         }
         // dw/du = -(du / s^2) e, dw/dv = -(dv / s^2) e
         const double k = -g.scale * g.inv_s2;
-        grad[j] = make_double2(k * gu / g.px, -k * gv / g.py);
+        grad[j] = make_double2(k * gu * g.inv_px, -k * gv * g.inv_py);
     }
 }
 
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(256) splat_kernel_f32(const double2 *__restric
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         const double2 z = __ldg(roots + j);
-        const double u = (z.x - g.xmin) / g.px, v = (g.ymax - z.y) / g.py;
+        const double u = (z.x - g.xmin) * g.inv_px, v = (g.ymax - z.y) * g.inv_py;
         float ex[K], ey[K], dx0, dy0;
         int x0, y0;
         const int nx = splat_axis_f<K>(gf, u, g.W, x0, ex, dx0);
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(1024, 1) splat_kernel_f32_smem(const double2 *
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         const double2 z = __ldg(roots + j);
-        const double u = (z.x - g.xmin) / g.px, v = (g.ymax - z.y) / g.py;
+        const double u = (z.x - g.xmin) * g.inv_px, v = (g.ymax - z.y) * g.inv_py;
         float ex[K], ey[K], dx0, dy0;
         int x0, y0;
         const int nx = splat_axis_f<K>(gf, u, g.W, x0, ex, dx0);
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(256) splat_backward_kernel_f32(const double2 *
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         const double2 z = __ldg(roots + j);
-        const double u = (z.x - g.xmin) / g.px, v = (g.ymax - z.y) / g.py;
+        const double u = (z.x - g.xmin) * g.inv_px, v = (g.ymax - z.y) * g.inv_py;
         float ex[K], ey[K], dx0, dy0;
         int x0, y0;
         const int nx = splat_axis_f<K>(gf, u, g.W, x0, ex, dx0);
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(256) splat_backward_kernel_f32(const double2 *
             }
         }
         const float k = -gf.scale * gf.inv_s2;
-        grad[j] = make_double2(f2d(k * gu) / g.px, -f2d(k * gv) / g.py);
+        grad[j] = make_double2(f2d(k * gu) * g.inv_px, -f2d(k * gv) * g.inv_py);
     }
 }
 
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(1024, 1) splat_backward_kernel_f32_smem(const 
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         const double2 z = __ldg(roots + j);
-        const double u = (z.x - g.xmin) / g.px, v = (g.ymax - z.y) / g.py;
+        const double u = (z.x - g.xmin) * g.inv_px, v = (g.ymax - z.y) * g.inv_py;
         float ex[K], ey[K], dx0, dy0;
         int x0, y0;
         const int nx = splat_axis_f<K>(gf, u, g.W, x0, ex, dx0);
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(1024, 1) splat_backward_kernel_f32_smem(const 
             }
         }
         const float k = -gf.scale * gf.inv_s2;
-        grad[j] = make_double2(f2d(k * gu) / g.px, -f2d(k * gv) / g.py);
+        grad[j] = make_double2(f2d(k * gu) * g.inv_px, -f2d(k * gv) * g.inv_py);
     }
 }
 
@@ -340,6 +341,8 @@ static SplatGeom splat_geom(const rd_window &w, int W, int H, double sigma, doub
     g.ymax = w.ymax;
     g.px = (w.xmax - w.xmin) / W;
     g.py = (w.ymax - w.ymin) / H;
+    g.inv_px = 1.0 / g.px;
+    g.inv_py = 1.0 / g.py;
     g.W = W;
     g.H = H;
     g.sigma = sigma;
