@@ -38,3 +38,26 @@ def test_root_error_summary_against_the_oracle(orc):
     gpu2[10, 0] += 1e-6
     s2 = bench.root_error_summary(gpu2, np.zeros(idx.size, np.uint8), ref, ref_st, co, 1e-9, 1e3)
     assert not s2["within_bar"] or s2["ill_conditioned_max_rel_err"] >= 1e-7
+
+
+def test_newton_move_of_kept_roots():
+    """The pipeline's accuracy check: a zero of sin(z^3) + z/2 placed in its
+    own tile moves by ~0 under one Newton step on f; a point off the zero
+    moves by about its distance; roots outside their tile are not counted."""
+    import torch
+
+    from paper_2507_02164_gb300 import workloads as WL
+    win = (-4.0, 4.0, -2.25, 2.25)
+    centres, rho, _, _ = WL.tiles(*win, 480, 270)
+    z = 1.0 + 0.5j
+    for _ in range(60):
+        z = z - (np.sin(z ** 3) + 0.5 * z) / (3 * z ** 2 * np.cos(z ** 3) + 0.5)
+    t = int(np.floor((win[3] - z.imag) * 270 / 4.5)) * 480 + int(np.floor((z.real - win[0]) * 480 / 8.0))
+    w = np.full((centres.size, 6), np.nan + 0j)
+    w[t, 0] = (z - centres[t]) / rho                     # the zero, in its own tile
+    w[t, 1] = (z + 2e-9 - centres[t]) / rho              # 2e-9 off it, same tile
+    w[t + 1, 0] = (z - centres[t + 1]) / rho             # the zero, but not in tile t + 1
+    out = bench.newton_move_of_kept(torch.from_numpy(np.ascontiguousarray(w.T)), torch.from_numpy(centres), rho,
+                                    win, 480, 270)
+    assert out["kept_roots"] == 2
+    assert 1e-9 <= out["max_newton_move"] <= 4e-9 and out["within_bar"]
