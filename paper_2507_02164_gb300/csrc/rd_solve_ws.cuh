@@ -85,7 +85,7 @@ __device__ __forceinline__ bool ws_wait(const volatile unsigned *state, unsigned
                 gave_up = true;
                 break;
             }
-            __nanosleep(512);
+            __nanosleep(2048);
             ok = *state == want;
             if (!ok && ((it & 63u) == 63u || it >= WS_MAX_POLLS) &&
                 (it >= WS_MAX_POLLS || ws_clock_ns() - t0 > WS_WAIT_NS)) {
