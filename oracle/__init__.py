@@ -146,7 +146,7 @@ def solve(coeffs, tol: float = 1e-13, max_its: int = 40, shift: int = SHIFT_RAYL
 
 
 def solve_fixed(coeffs, T: int = 10, shift: int = SHIFT_RAYLEIGH, exc_period: int = 0):
-    """Alg. 2's fixed schedule: T sweeps per eigenvalue, no deflation test.
+    """The paper's fixed schedule: T QR steps per eigenvalue, no deflation test.
     Returns (roots [n, d], status [n])."""
     coeffs = _c128(coeffs)
     if coeffs.ndim == 1:

@@ -9,12 +9,12 @@
  *   Sec. II-A   L2 approximation on the unit disk (G a = b)
  *   Sec. II-B   roots = eigenvalues of the Frobenius companion matrix; Alg. 1
  *   Sec. II-C   complex Givens rotation; A <- (Q_{n-1}..Q_1) A (Q_1^H..Q_{n-1}^H)
- *   Alg. 2      the row loop / column loop form of one shifted sweep
  *   Sec. III    roots converted to pixel coordinates and counted
  *
- * Everything is written out plainly: full m x m loops exactly as Alg. 2 states
- * them, C99 complex arithmetic, no blocking and no reordering. Readings where
- * the paper is silent:
+ * Everything is written out plainly, in C99 complex arithmetic: a QR step is
+ * the factorisation A - s I = Q R by Givens matrices followed by A <- R Q + s I,
+ * every product a full dense matrix product (no use of the Hessenberg
+ * structure, no blocking). Readings where the paper is silent:
  *   - Frobenius form: ones on the subdiagonal, last column -b_0..-b_{n-1}.
  *   - Givens: c = conj(a)/r, s = conj(b)/r, r = hypot(|a|,|b|); r = 0 -> (1,0).
  *   - Stopping: Alg. 1 runs a fixed number of sweeps per level; the oracle
@@ -86,30 +86,73 @@ void or_companion(const double *b, int n, double *A)
     for (int i = 0; i < n * n; ++i) st(A + 2 * i, AA[i]);
 }
 
-/* One sweep of Alg. 2 on the leading m x m block: subtract the shift, row
- * rotations r = 1..m-1 (each computed from the current (r-1,r-1), (r,r-1)
- * entries and applied to rows r-1, r over columns 0..m-1), then column
- * rotations r = 1..m-1 with the conjugate transposes over rows 0..m-1, then
- * add the shift back. */
+/* Small dense m x m matrices (row-major, m <= OR_MAX_DEGREE) for writing one
+ * QR step as the matrix products it is. */
+static void mat_identity(int m, cplx *X)
+{
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) X[i * m + j] = (i == j) ? 1.0 : 0.0;
+}
+
+/* Z = X Y (Z must not alias X or Y) */
+static void mat_mul(int m, const cplx *X, const cplx *Y, cplx *Z)
+{
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+            cplx acc = 0.0;
+            for (int k = 0; k < m; ++k) acc += X[i * m + k] * Y[k * m + j];
+            Z[i * m + j] = acc;
+        }
+}
+
+/* Y = X^H */
+static void mat_adjoint(int m, const cplx *X, cplx *Y)
+{
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) Y[j * m + i] = conj(X[i * m + j]);
+}
+
+/* Q_r of Sec. II-C embedded in the m x m identity: the 2 x 2 rotation
+ * [[c, s], [-conj(s), conj(c)]] acting on coordinates r-1 and r. */
+static void givens_matrix(int m, int r, cplx c, cplx s, cplx *G)
+{
+    mat_identity(m, G);
+    G[(r - 1) * m + (r - 1)] = c;
+    G[(r - 1) * m + r] = s;
+    G[r * m + (r - 1)] = -conj(s);
+    G[r * m + r] = conj(c);
+}
+
+/* One shifted QR step (Alg. 1, Sec. II-B/II-C) on the leading m x m block of
+ * the n x n matrix A, written as the factorisation it is:
+ *   B = A - s I;  Q_1 .. Q_{m-1}, each chosen (Sec. II-C) to zero entry
+ *   (r, r-1) of Q_{r-1} .. Q_1 B, give R = Q_{m-1} .. Q_1 B (upper triangular)
+ *   and Q^H = Q_{m-1} .. Q_1;  then A <- R Q + s I.
+ * Every product is a full dense m x m product; nothing uses the Hessenberg
+ * structure (Appendix A shows that the result stays Hessenberg; the tests
+ * check it instead of assuming it). */
 static void qr_sweep(cplx *A, int n, int m, cplx shift)
 {
-    cplx c[OR_MAX_DEGREE], s[OR_MAX_DEGREE];
-    for (int i = 0; i < m; ++i) AT(A, n, i, i) -= shift;
+    cplx B[OR_MAX_DEGREE * OR_MAX_DEGREE], Qh[OR_MAX_DEGREE * OR_MAX_DEGREE];
+    cplx G[OR_MAX_DEGREE * OR_MAX_DEGREE], T[OR_MAX_DEGREE * OR_MAX_DEGREE];
+    cplx Q[OR_MAX_DEGREE * OR_MAX_DEGREE];
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) B[i * m + j] = AT(A, n, i, j);
+    for (int i = 0; i < m; ++i) B[i * m + i] -= shift;
+    mat_identity(m, Qh);
     for (int r = 1; r < m; ++r) {
-        givens(AT(A, n, r - 1, r - 1), AT(A, n, r, r - 1), &c[r], &s[r]);
-        for (int j = 0; j < m; ++j) {
-            cplx x = AT(A, n, r - 1, j), y = AT(A, n, r, j);
-            AT(A, n, r - 1, j) = c[r] * x + s[r] * y;
-            AT(A, n, r, j) = -conj(s[r]) * x + conj(c[r]) * y;
-        }
+        cplx c, s;
+        givens(B[(r - 1) * m + (r - 1)], B[r * m + (r - 1)], &c, &s);
+        givens_matrix(m, r, c, s, G);
+        mat_mul(m, G, B, T); /* B <- Q_r B */
+        memcpy(B, T, sizeof(cplx) * m * m);
+        mat_mul(m, G, Qh, T); /* Q^H <- Q_r Q^H */
+        memcpy(Qh, T, sizeof(cplx) * m * m);
     }
-    for (int r = 1; r < m; ++r) {
-        for (int j = 0; j < m; ++j) {
-            cplx x = AT(A, n, j, r - 1), y = AT(A, n, j, r);
-            AT(A, n, j, r - 1) = conj(c[r]) * x + conj(s[r]) * y;
-            AT(A, n, j, r) = -s[r] * x + c[r] * y;
-        }
-    }
+    mat_adjoint(m, Qh, Q);
+    mat_mul(m, B, Q, T); /* R Q */
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) AT(A, n, i, j) = T[i * m + j];
     for (int i = 0; i < m; ++i) AT(A, n, i, i) += shift;
 }
 
@@ -196,10 +239,11 @@ int or_solve_one(const double *a, int d, double tol, int max_its, int shift_mode
     return status;
 }
 
-/* Alg. 2 exactly as printed: t = (n-1) T sweeps; sweep i works on the
- * leading m = n - floor(i / T) rows and columns with the shift of that
- * block; after each sweep eig[m-1] is the diagonal entry h[m-1][m-1] (the
- * last write for each m stands); eig[0] = h[0][0]. No deflation test. */
+/* The paper's fixed schedule (no deflation test): Alg. 1 with its iteration
+ * count T, i.e. T shifted QR steps on each active size m = d, d-1, .., 2, after
+ * which the diagonal entry h[m-1][m-1] is taken as an eigenvalue and the
+ * block shrinks; the last one is h[0][0]. The shift of step t on size m is
+ * chosen as in solve_one with t in place of the stagnation count. */
 int or_solve_fixed(const double *a_in, int d, int T, int shift_mode, int exc_period, double *roots)
 {
     cplx a[OR_MAX_DEGREE + 1], eig[OR_MAX_DEGREE];
@@ -215,19 +259,18 @@ int or_solve_fixed(const double *a_in, int d, int T, int shift_mode, int exc_per
     cplx b[OR_MAX_DEGREE], A[OR_MAX_DEGREE * OR_MAX_DEGREE];
     for (int k = 0; k < d; ++k) b[k] = a[k] / a[d];
     companion(b, d, A);
-    int n = d;
-    for (int i = 0; i < (n - 1) * T; ++i) {
-        int m = n - i / T;
-        int its = i % T;
-        cplx shift;
-        if (shift_mode == OR_SHIFT_WILKINSON || (its > 0 && exc_period > 0 && its % exc_period == 0))
-            shift = wilkinson(A, n, m);
-        else
-            shift = AT(A, n, m - 1, m - 1);
-        qr_sweep(A, n, m, shift);
-        eig[m - 1] = AT(A, n, m - 1, m - 1);
+    for (int m = d; m >= 2; --m) {
+        for (int t = 0; t < T; ++t) {
+            cplx shift;
+            if (shift_mode == OR_SHIFT_WILKINSON || (t > 0 && exc_period > 0 && t % exc_period == 0))
+                shift = wilkinson(A, d, m);
+            else
+                shift = AT(A, d, m - 1, m - 1);
+            qr_sweep(A, d, m, shift);
+        }
+        eig[m - 1] = AT(A, d, m - 1, m - 1);
     }
-    eig[0] = AT(A, n, 0, 0);
+    eig[0] = AT(A, d, 0, 0);
     for (int j = 0; j < d; ++j) st(roots + 2 * j, eig[j]);
     return OR_OK;
 }

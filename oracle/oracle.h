@@ -40,8 +40,9 @@ void or_givens(const double *a, const double *b, double *c, double *s);
  * low coefficients b_0..b_{n-1} into A (row-major n x n complex). */
 void or_companion(const double *b, int n, double *A);
 
-/* One shifted QR sweep on the leading m x m block of the n x n row-major
- * matrix A, with shift `shift` (Alg. 2 loop body, full j loops). */
+/* One shifted QR step on the leading m x m block of the n x n row-major
+ * matrix A, with shift `shift`: B = A - s I = Q R by Givens matrices
+ * (Sec. II-C), then A <- R Q + s I, as full dense matrix products. */
 void or_qr_sweep(double *A, int n, int m, const double *shift);
 
 /* Wilkinson shift of the trailing 2x2 of the leading m x m block of A. */
@@ -58,8 +59,9 @@ int or_solve_batch(const double *coef, int64_t n, int d, double tol, int max_its
                    int shift_mode, int exc_period, double *roots, uint8_t *status,
                    int32_t *sweeps, int threads);
 
-/* Alg. 2 as printed: (d-1) T sweeps, the active size dropping every T
- * sweeps, no deflation test. Returns the status (OK or DEGENERATE). */
+/* The paper's fixed schedule: T QR steps on each active size d, .., 2 (Alg. 1
+ * with its iteration count), no deflation test. Returns the status (OK or
+ * DEGENERATE). */
 int or_solve_fixed(const double *a, int d, int T, int shift_mode, int exc_period, double *roots);
 
 /* Root-density histogram: hist[iy*W + ix] += 1 for every root inside the

@@ -19,14 +19,16 @@ SRC = os.path.join(ROOT, "oracle", "oracle.c")
 
 MUTANTS = {
     "givens_s_not_conjugated": ("*s = conj(b) / r;", "*s = b / r;"),
-    "row_rotation_sign": ("AT(A, n, r, j) = -conj(s[r]) * x + conj(c[r]) * y;",
-                          "AT(A, n, r, j) = conj(s[r]) * x + conj(c[r]) * y;"),
-    "column_rotation_conjugate": ("AT(A, n, j, r - 1) = conj(c[r]) * x + conj(s[r]) * y;",
-                                  "AT(A, n, j, r - 1) = c[r] * x + conj(s[r]) * y;"),
-    "column_rotation_index": ("cplx x = AT(A, n, j, r - 1), y = AT(A, n, j, r);",
-                              "cplx x = AT(A, n, r - 1, j), y = AT(A, n, j, r);"),
+    "rotation_lower_sign": ("G[r * m + (r - 1)] = -conj(s);", "G[r * m + (r - 1)] = conj(s);"),
+    "rotation_diagonal_not_conjugated": ("G[r * m + r] = conj(c);", "G[r * m + r] = c;"),
+    "adjoint_not_conjugated_q": ("Y[j * m + i] = conj(X[i * m + j]);", "Y[j * m + i] = X[i * m + j];"),
+    "matmul_transposed_operand": ("acc += X[i * m + k] * Y[k * m + j];", "acc += X[k * m + i] * Y[k * m + j];"),
+    "q_accumulated_on_the_right": ("mat_mul(m, G, Qh, T); /* Q^H <- Q_r Q^H */",
+                                   "mat_mul(m, Qh, G, T); /* Q^H <- Q_r Q^H */"),
+    "rq_as_qr": ("mat_mul(m, B, Q, T); /* R Q */", "mat_mul(m, Q, B, T); /* R Q */"),
     "companion_sign": ("AT(A, n, i, n - 1) = -b[i];", "AT(A, n, i, n - 1) = b[i];"),
     "shift_not_restored": ("for (int i = 0; i < m; ++i) AT(A, n, i, i) += shift;", ""),
+    "fixed_schedule_wrong_level": ("eig[m - 1] = AT(A, d, m - 1, m - 1);", "eig[m - 1] = AT(A, d, m - 2, m - 2);"),
     "wilkinson_far_root": ("cabs(mu_plus - d) <= cabs(mu_minus - d) ? mu_plus : mu_minus",
                            "cabs(mu_plus - d) > cabs(mu_minus - d) ? mu_plus : mu_minus"),
     "hist_rows_flipped": ("double fy = (ymax - y) * sy;", "double fy = (y - ymin) * sy;"),
