@@ -20,6 +20,9 @@
  *   - Return value: RD_OK, or a negative error code. rd_last_error() gives a
  *     thread-local message for the most recent failure on the calling thread.
  *     On error nothing has been enqueued.
+ *   - rd_autotune is the one exception to "never allocates, never
+ *     synchronises": it allocates its own probe batch and times it with
+ *     events. Call it outside any stream capture.
  */
 #ifndef ROOTDENSITY_H
 #define ROOTDENSITY_H
@@ -31,7 +34,7 @@
 extern "C" {
 #endif
 
-#define RD_ABI_VERSION 1
+#define RD_ABI_VERSION 2
 
 /* ---- return codes ---------------------------------------------------- */
 #define RD_OK 0
@@ -125,7 +128,8 @@ typedef struct {
     uint64_t newton_steps;   /* RD_MIXED: Newton steps taken                             */
     uint64_t binned;         /* roots counted in the histogram                           */
     uint64_t out_of_window;  /* roots outside the window (NaN included)                  */
-    uint64_t clipped;        /* roots dropped by a tile clip                             */
+    uint64_t clipped;        /* roots dropped before binning: by a tile clip, or (standalone
+                                binning) because their polynomial's status is not OK     */
     uint64_t flops_fp32;     /* algorithmic FP32 flops of the solve (see below)          */
     uint64_t flops_fp64;     /* algorithmic FP64 flops of the solve                      */
     uint64_t wait_timeouts;  /* polynomials the warp-specialised solver abandoned after a
@@ -202,9 +206,23 @@ int rd_roots_density(const void *coeffs, rd_dtype dtype, int degree, int64_t n, 
 
 /* ---- standalone binning (Sec. III, Roots to Pixels) -------------------------
  * hist[iy*W + ix] += 1 for each of the n_roots roots (device rd_c128 array)
- * inside the window; others (NaN included) add to stats->out_of_window. */
-int rd_density_accumulate(const double *roots, int64_t n_roots, rd_window window, int W, int H,
-                          uint32_t *hist, rd_stats *stats, void *stream);
+ * inside the window; others (NaN included) add to stats->out_of_window.
+ *   n_polys  0: the roots stand alone (status and clip must be NULL).
+ *            n > 0: the roots are a solve's output for n polynomials, root r
+ *            belonging to polynomial r mod n (the [degree][n] layout of
+ *            rd_roots_batched); n_roots must be a multiple of n.
+ *   status   device uint8 [n_polys] or NULL: when given, only the roots of
+ *            polynomials with status RD_STATUS_OK are binned.
+ *   clip     host pointer or NULL: the roots are points w of their
+ *            polynomials' unit disks (Sec. II, subregions D_i); root r of
+ *            polynomial i is mapped to z = clip->centres[i] + clip->radius w
+ *            and binned only when z lies in polynomial i's own tile
+ *            (clip->tile_index[i], or i), as the fused solve's clip does.
+ * Roots dropped by the status mask or the clip add to stats->clipped. The
+ * pixel arithmetic is the fused solve's, operation for operation. */
+int rd_density_accumulate(const double *roots, const uint8_t *status, int64_t n_roots, int64_t n_polys,
+                          rd_window window, int W, int H, const rd_clip *clip, uint32_t *hist,
+                          rd_stats *stats, void *stream);
 
 /* Zero `words` 32-bit words of device memory (histogram or rd_stats). */
 int rd_hist_clear(uint32_t *hist, int64_t words, void *stream);
@@ -230,17 +248,27 @@ int rd_pointer_is_device_accessible(const void *p);
  * into the workspace, then solves every degree bin with a persistent kernel
  * that takes 32-polynomial tasks (16 with two lanes per polynomial) from the
  * bin's atomic queue, binning roots into hist when it is given.
- * A polynomial whose offsets do not hold degree+1 coefficients inside the
- * array, or whose degree is outside 1..12, gets RD_STATUS_DEGENERATE (NaN
- * roots when its offsets are consistent; nothing written otherwise).
+ * roots (when not NULL) holds n_coeffs - n elements.
+ * Polynomial i is solved when degrees[i] is 1..12 and its offsets are
+ * consistent: offsets[i+1] - offsets[i] = degrees[i] + 1, offsets[i] >= i and
+ * offsets[i+1] <= n_coeffs - (n - 1 - i) (its roots then lie inside the root
+ * array). An inconsistent polynomial gets RD_STATUS_DEGENERATE and nothing
+ * else is written for it; a consistent one of another degree gets
+ * RD_STATUS_DEGENERATE and NaN roots. If the solvable polynomials need more
+ * than n_coeffs coefficients in all (their ranges overlap: offsets that are
+ * not monotone), none of them is solved: each gets RD_STATUS_DEGENERATE and
+ * NaN roots. A well-formed batch (offsets[0] = 0, increasing, offsets[n] =
+ * n_coeffs) is always consistent.
  *   ws        device scratch of at least rd_uneven_workspace_bytes(n, n_coeffs,
  *             dtype) bytes, 256-byte aligned; overwritten; must not be shared
  *             by two calls in flight at once
  *   window    host pointer; NULL with hist NULL = no binning
  *   tuning    host pointer or NULL (params.block / ctas_per_sm / lanes for every
  *             degree); see rd_uneven_tuning
- * n < 2^32. Only enqueues kernels on `stream` (16 launches), so the whole
- * call can be captured in a CUDA graph. */
+ * n < 2^32 and n_coeffs <= 2^40 (RD_EINVAL otherwise;
+ * rd_uneven_workspace_bytes returns 0 outside these limits). Only enqueues
+ * kernels on `stream` (16 launches), so the whole call can be captured in a
+ * CUDA graph. */
 typedef struct {
     /* Launch shape of each degree bin's solve kernel, indexed by the degree
      * (entries 1..12; entries 0 and 13..15 are ignored). 0 = the default.   */
@@ -268,9 +296,12 @@ int rd_roots_uneven(const void *coeffs, rd_dtype dtype, const uint8_t *degrees, 
  *   - A batch whose rd_uneven_workspace_bytes(n, n_coeffs, dtype) exceeds
  *     RD_STATIC_SCRATCH_BYTES is rejected with RD_EINVAL and a message; split
  *     it, or use rd_roots_uneven.
- *   - The first call on each device looks up the scratch array's device
- *     address (cudaGetSymbolAddress) with that device current; make that
- *     first call before any stream capture begins.
+ *   - A call outside stream capture looks up the scratch array's device
+ *     address (cudaGetSymbolAddress) with its device current, so the
+ *     address stays right after a cudaDeviceReset; a call under capture uses
+ *     the address the last call outside capture found on that device. Make
+ *     the first call on each device before any stream capture begins (a
+ *     first call under capture returns RD_EINVAL).
  *   - All calls on a device share the one array and each leaves its contents
  *     behind (the next call clears what must start at zero). Two calls whose
  *     work overlaps on the GPU (different streams, or different host threads)
@@ -295,20 +326,42 @@ int rd_roots_backward(const void *coeffs, rd_dtype dtype, int degree, int64_t n,
                       const double *roots, const double *grad_roots, void *grad_coeffs,
                       uint8_t *status, void *stream);
 
+/* The same adjoint for a packed batch of uneven degrees (the layout of
+ * rd_roots_uneven): polynomial i has degree degrees[i] and coefficients
+ * coeffs[offsets[i] .. offsets[i+1]-1]; its roots and their gradients are
+ * roots[offsets[i] - i + j], grad_roots[offsets[i] - i + j] (rd_c128, n_coeffs
+ * - n elements each); grad_coeffs (n_coeffs elements of dtype) is written
+ * like coeffs. A polynomial is differentiated under the consistency rule of
+ * rd_roots_uneven; an inconsistent one gets RD_STATUS_DEGENERATE and nothing
+ * is written for it, a consistent one of degree 0 or above 12 gets
+ * RD_STATUS_DEGENERATE and zero gradients. n < 2^32, n_coeffs <= 2^40. */
+int rd_roots_backward_uneven(const void *coeffs, rd_dtype dtype, const uint8_t *degrees,
+                             const int64_t *offsets, int64_t n, int64_t n_coeffs, const double *roots,
+                             const double *grad_roots, void *grad_coeffs, uint8_t *status, void *stream);
+
 /* ---- L2 approximation on sub-disks (Sec. II-A) ------------------------------
  * Nodes of the quadrature on the unit disk: radii r_p (Gauss-Legendre on
- * [0,1], p < nr, ascending) with weights w_p, and angles theta_q = 2 pi q / nt.
- * Host function; r and w are host arrays of nr doubles. */
-int rd_l2_nodes(int nr, double *r, double *w);
+ * [0,1], p < nr, ascending) with weights w_p, and angles theta_q = 2 pi q / nt
+ * (q < nt), so that f is sampled at c + rho r_p e^{i theta_q}.
+ * Host function; r and w are host arrays of nr doubles, theta a host array of
+ * nt doubles or NULL. 1 <= nr <= 32, 1 <= nt <= 4096. */
+int rd_l2_nodes(int nr, int nt, double *r, double *theta, double *w);
 
 /* For each sub-disk s < n, samples[s][p*nt + q] = g_s(r_p e^{i theta_q})
  * (device rd_c128; g_s(w) = f(c_s + rho w)). Computes the degree-`degree`
  * least-squares polynomial of g_s on the unit disk for the inner product
  * <g, h> = integral g conj(h) dA, whose Gram matrix is diagonal:
  * a_j = (j+1)/pi <g, w^j>. coeffs: device rd_c128, coefficient-major
- * [degree+1][n] (ready for rd_roots_*). nt must be 32; nr <= 32; degree <= 12. */
-int rd_l2_approx(const double *samples, int64_t n, int nr, int nt, int degree, int precision, double *coeffs,
-                 void *stream);
+ * [degree+1][n] (ready for rd_roots_*). nt must be 32; nr <= 32; degree <= 12.
+ * The coefficients stay in the local variable w of each sub-disk (expanding
+ * them in z would scale a_j by rho^-j). centres (device rd_c128 [n], the
+ * sub-disk centres c_s) and radius (rho) describe that map z = c_s + rho w:
+ * when map is not NULL they are checked and written into map->centres and
+ * map->radius, which the caller completes with its tile grid and passes to
+ * rd_roots_density or rd_density_accumulate; the kernel does not read them.
+ * centres may be NULL only when map is NULL. */
+int rd_l2_approx(const double *samples, int64_t n, int nr, int nt, int degree, int precision,
+                 const double *centres, double radius, double *coeffs, rd_clip *map, void *stream);
 /* precision: RD_L2_FP64 sums in FP64 (the FP64 pipe bounds the kernel);
  * RD_L2_DF sums in double-float arithmetic on the FP32 pipe (about 2^-48
  * relative per term, ~1e-14 on the coefficients relative to the largest of a
@@ -383,6 +436,52 @@ typedef struct {
 int rd_field_density(rd_field f, const rd_field_spec *spec, rd_mode mode, const rd_params *params,
                      rd_window window, int W, int H, uint32_t *hist, double *coeffs, double *roots,
                      uint8_t *status, rd_stats *stats, void *stream);
+
+/* ---- launch-shape autotuner ---------------------------------------------------
+ * Times the launch shapes of rd_roots_density for one degree, mode and storage
+ * type on a probe batch of n_probe complex-Gaussian polynomials (real and
+ * imaginary parts N(0,1), drawn on the device from a fixed seed per degree)
+ * binned into a 1920 x 1080 histogram over [-3,3] x [-1.6875,1.6875], and
+ * returns the fastest. Candidates: lanes per polynomial (1; 2 from degree 2 on,
+ * with the FP64 polish), threads per CTA 32, 64, 128, 256, resident CTAs per
+ * SM (the occupancy maximum or fewer), each with every warp sweeping then
+ * polishing; and for RD_MIXED the warp-specialised shapes (polish_warps > 0).
+ * Each shape runs once untimed, then `reps` times (1..15) timed with CUDA
+ * events; its time is the median. A shape that cannot be launched (too many
+ * registers for the block) is recorded with ms < 0 and skipped. This is the
+ * one entry point that allocates (the probe batch and its histogram, freed
+ * before it returns) and synchronises: call it outside any stream capture.
+ *   out        host; the fastest shape, and the fastest with polish_warps = 0
+ *              (the form the uneven-degree bins run)
+ *   table      host array of table_cap entries or NULL; receives every timed
+ *              shape (at most table_cap), *table_len their number
+ * 1 <= degree <= 12, 1024 <= n_probe <= 2^24. */
+typedef struct {
+    int32_t lanes, block, ctas_per_sm, polish_warps;
+    float ms;      /* median milliseconds of one rd_roots_density call on the probe, < 0: not launchable */
+} rd_tune_entry;
+typedef struct {
+    rd_tune_entry best;      /* fastest shape overall                                      */
+    rd_tune_entry one_role;  /* fastest shape with polish_warps = 0                         */
+    int32_t n_candidates;    /* shapes timed (launchable or not)                           */
+    int32_t reserved;
+} rd_tuning;
+int rd_autotune(int degree, rd_mode mode, rd_dtype dtype, int64_t n_probe, int reps, rd_tuning *out,
+                rd_tune_entry *table, int table_cap, int *table_len);
+
+/* ---- ALU throughput probe ------------------------------------------------------
+ * Not part of the method: the denominator of its roofline. Enqueues one kernel
+ * of independent fused multiply-add chains, RD_PEAK_FP32 (FFMA on the FP32
+ * pipe) or RD_PEAK_FP64 (DFMA on the FP64 pipe): ctas_per_sm x SM count CTAs
+ * of 256 threads, each thread `iters` x 128 FMAs (16 steps of 8 independent
+ * chains per iteration). *flops (host) receives the
+ * flops the launch performs (2 per FMA); the caller times it with events on
+ * `stream`. sink: device, 8 bytes, written only if a chain ends on a value it
+ * cannot reach (it keeps the chains from being optimised away).
+ * 1 <= iters <= 2^24, 1 <= ctas_per_sm <= 32. */
+#define RD_PEAK_FP32 0
+#define RD_PEAK_FP64 1
+int rd_alu_peak(int kind, int64_t iters, int ctas_per_sm, double *sink, uint64_t *flops, void *stream);
 
 #ifdef __cplusplus
 }

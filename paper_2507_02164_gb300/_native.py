@@ -51,6 +51,18 @@ class FieldSpec(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("poly", ctypes.c_double * 26)]
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int32), ("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("polish_warps", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("best", TuneEntry), ("one_role", TuneEntry), ("n_candidates", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+ABI_VERSION = 2
+PEAK_FP32, PEAK_FP64 = 0, 1
 F_SIN_CUBE, F_POLY = 0, 1
 SPLAT_FP64, SPLAT_FP32 = 0, 1
 
@@ -72,16 +84,20 @@ SIGNATURES = {
     "rd_roots_batched": (I32, [P, I32, I32, I64, I32, ctypes.POINTER(Params), P, P, P, P]),
     "rd_roots_density": (I32, [P, I32, I32, I64, I32, ctypes.POINTER(Params), ctypes.POINTER(Clip), Window,
                                I32, I32, P, P, P, P, P]),
-    "rd_density_accumulate": (I32, [P, I64, Window, I32, I32, P, P, P]),
+    "rd_density_accumulate": (I32, [P, P, I64, I64, Window, I32, I32, ctypes.POINTER(Clip), P, P, P]),
     "rd_hist_clear": (I32, [P, I64, P]),
     "rd_roots_backward": (I32, [P, I32, I32, I64, P, P, P, P, P]),
+    "rd_roots_backward_uneven": (I32, [P, I32, P, P, I64, I64, P, P, P, P, P]),
+    "rd_autotune": (I32, [I32, I32, I32, I64, I32, ctypes.POINTER(Tuning), ctypes.POINTER(TuneEntry), I32,
+                          ctypes.POINTER(ctypes.c_int)]),
+    "rd_alu_peak": (I32, [I32, I64, I32, P, ctypes.POINTER(ctypes.c_uint64), P]),
     "rd_uneven_workspace_bytes": (SZ, [I64, I64, I32]),
     "rd_roots_uneven": (I32, [P, I32, P, P, I64, I64, I32, ctypes.POINTER(Params), ctypes.POINTER(UnevenTuning),
                               ctypes.POINTER(Window), I32, I32, P, P, P, P, P, SZ, P]),
     "rd_roots_uneven_static": (I32, [P, I32, P, P, I64, I64, I32, ctypes.POINTER(Params),
                                      ctypes.POINTER(UnevenTuning), ctypes.POINTER(Window), I32, I32, P, P, P, P, P]),
-    "rd_l2_nodes": (I32, [I32, P, P]),
-    "rd_l2_approx": (I32, [P, I64, I32, I32, I32, I32, P, P]),
+    "rd_l2_nodes": (I32, [I32, I32, P, P, P]),
+    "rd_l2_approx": (I32, [P, I64, I32, I32, I32, I32, P, F64, P, ctypes.POINTER(Clip), P]),
     "rd_splat": (I32, [P, I64, Window, I32, I32, F64, F64, I32, P, P]),
     "rd_splat_backward": (I32, [P, I64, Window, I32, I32, F64, F64, I32, P, P, P]),
     "rd_field_density": (I32, [I32, ctypes.POINTER(FieldSpec), I32, ctypes.POINTER(Params), Window, I32, I32, P, P,
@@ -117,8 +133,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                 f = getattr(L, name)
                 f.restype = res
                 f.argtypes = args
-            if L.rd_abi_version() != 1:
-                raise RuntimeError("libroots ABI version mismatch")
+            if L.rd_abi_version() != ABI_VERSION:
+                raise RuntimeError(f"libroots ABI version {L.rd_abi_version()}, binding expects {ABI_VERSION}")
             _lib = L
     return _lib
 

@@ -160,12 +160,30 @@ def roots_density(coeffs: torch.Tensor, window: Window, hist: torch.Tensor, mode
     return hist
 
 
-def density_accumulate(roots: torch.Tensor, window: Window, hist: torch.Tensor, stats=None, stream=None):
+def density_accumulate(roots: torch.Tensor, window: Window, hist: torch.Tensor, status=None, clip=None,
+                       stats=None, stream=None):
+    """Bin roots (complex128) into hist ([H, W] int32 viewed as uint32, accumulated).
+    roots [d, n] is a solve's output for n polynomials; a 1-D tensor stands
+    alone. status ([n] uint8) keeps only the roots of polynomials with status
+    OK; clip (make_clip) maps each root w of polynomial i to c_i + rho w and
+    keeps it only inside polynomial i's own tile."""
     _check_cuda("roots", roots, torch.complex128)
     _check_cuda("hist", hist)
+    if roots.dim() == 2:
+        n_polys = roots.shape[1]
+    elif roots.dim() == 1:
+        n_polys = 0
+    else:
+        raise ValueError("roots must be [d, n] or 1-D")
+    if status is not None:
+        _check_cuda("status", status, torch.uint8)
+        if n_polys == 0 or status.numel() != n_polys:
+            raise ValueError("status needs roots of shape [d, n] and n entries")
+    if clip is not None and n_polys == 0:
+        raise ValueError("clip needs roots of shape [d, n]")
     H, W = hist.shape
-    N.call("rd_density_accumulate", _ptr(roots), roots.numel(), window.c(), W, H, _ptr(hist), _ptr(stats),
-           _stream(stream))
+    N.call("rd_density_accumulate", _ptr(roots), _ptr(status), roots.numel(), n_polys, window.c(), W, H,
+           ctypes.byref(clip) if clip is not None else None, _ptr(hist), _ptr(stats), _stream(stream))
     return hist
 
 
@@ -234,35 +252,80 @@ def roots_backward(coeffs: torch.Tensor, roots: torch.Tensor, grad_roots: torch.
     return grad
 
 
-def l2_nodes(nr: int = 16):
-    """Gauss-Legendre radii and weights on [0, 1] (host lists), from the library."""
+def roots_backward_uneven(coeffs: torch.Tensor, degrees: torch.Tensor, offsets: torch.Tensor, roots: torch.Tensor,
+                          grad_roots: torch.Tensor, grad_coeffs=None, status=None, stream=None):
+    """Adjoint of a packed uneven-degree batch (the layout of roots_uneven):
+    grad_coeffs (packed like coeffs, same dtype) from grad_roots (packed like
+    roots, complex128)."""
+    _check_cuda("coeffs", coeffs)
+    if coeffs.dtype not in DTYPES or coeffs.dim() != 1:
+        raise ValueError("coeffs must be a 1-D complex64/complex128 tensor")
+    _check_cuda("degrees", degrees, torch.uint8)
+    _check_cuda("offsets", offsets, torch.int64)
+    n = degrees.numel()
+    if offsets.numel() != n + 1:
+        raise ValueError("offsets must have n+1 entries")
+    for name, t in (("roots", roots), ("grad_roots", grad_roots)):
+        _check_cuda(name, t, torch.complex128)
+        if t.numel() != coeffs.numel() - n:
+            raise ValueError(f"{name} must have n_coeffs - n entries")
+    if grad_coeffs is None:
+        grad_coeffs = torch.empty_like(coeffs)
+    _check_cuda("grad_coeffs", grad_coeffs, coeffs.dtype)
+    N.call("rd_roots_backward_uneven", _ptr(coeffs), DTYPES[coeffs.dtype], _ptr(degrees), _ptr(offsets), n,
+           coeffs.numel(), _ptr(roots), _ptr(grad_roots), _ptr(grad_coeffs), _ptr(status), _stream(stream))
+    return grad_coeffs
+
+
+def l2_nodes(nr: int = 16, nt: int = 32):
+    """Gauss-Legendre radii and weights on [0, 1] and the angles 2 pi q / nt
+    (host lists), from the library: (r, theta, w)."""
     r = (ctypes.c_double * nr)()
     w = (ctypes.c_double * nr)()
-    N.call("rd_l2_nodes", nr, ctypes.cast(r, ctypes.c_void_p), ctypes.cast(w, ctypes.c_void_p))
-    return list(r), list(w)
+    th = (ctypes.c_double * nt)()
+    N.call("rd_l2_nodes", nr, nt, ctypes.cast(r, ctypes.c_void_p), ctypes.cast(th, ctypes.c_void_p),
+           ctypes.cast(w, ctypes.c_void_p))
+    return list(r), list(th), list(w)
 
 
 def l2_sample_points(nr: int = 16, nt: int = 32, device="cuda") -> torch.Tensor:
-    """w_pq = r_p e^{i 2 pi q / nt} as a [nr*nt] complex128 tensor (index p*nt + q)."""
-    r, _ = l2_nodes(nr)
+    """w_pq = r_p e^{i theta_q} as a [nr*nt] complex128 tensor (index p*nt + q)."""
+    r, th, _ = l2_nodes(nr, nt)
     rr = torch.tensor(r, dtype=torch.float64, device=device)
-    th = 2.0 * torch.pi * torch.arange(nt, dtype=torch.float64, device=device) / nt
-    return (rr[:, None] * torch.exp(1j * th)[None, :]).reshape(-1)
+    tt = torch.tensor(th, dtype=torch.float64, device=device)
+    return (rr[:, None] * torch.exp(1j * tt)[None, :]).reshape(-1)
 
 
 def l2_approx(samples: torch.Tensor, nr: int = 16, nt: int = 32, degree: int = 6, coeffs=None, stream=None,
-              precision: str = "fp64"):
+              precision: str = "fp64", centres=None, radius: float = 0.0, clip=None):
     """samples [n, nr*nt] complex128 -> coeffs [degree+1, n] complex128 (local variable w).
-    precision "fp64" (FP64 sums) or "df" (double-float sums on the FP32 pipe)."""
+    precision "fp64" (FP64 sums) or "df" (double-float sums on the FP32 pipe).
+    With clip (an N.Clip whose tile grid the caller sets), centres [n]
+    complex128 and radius are checked and written into it: the map z = c + rho w
+    that rd_roots_density / density_accumulate apply to the roots."""
     _check_cuda("samples", samples, torch.complex128)
     n = samples.shape[0]
     if samples.shape[1] != nr * nt:
         raise ValueError("samples must have shape [n, nr*nt]")
     if coeffs is None:
         coeffs = torch.empty((degree + 1, n), dtype=torch.complex128, device=samples.device)
+    if centres is not None:
+        _check_cuda("centres", centres, torch.complex128)
     N.call("rd_l2_approx", _ptr(samples), n, nr, nt, degree, {"fp64": N.L2_FP64, "df": N.L2_DF}[precision],
-           _ptr(coeffs), _stream(stream))
+           _ptr(centres), float(radius), _ptr(coeffs), ctypes.byref(clip) if clip is not None else None,
+           _stream(stream))
     return coeffs
+
+
+def alu_peak(kind: str, iters: int, ctas_per_sm: int = 4, sink=None, stream=None) -> int:
+    """Enqueue the library's FMA throughput kernel ("fp32" or "fp64"); returns
+    the flops of the launch (the caller times it on `stream`)."""
+    if sink is None:
+        sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    fl = ctypes.c_uint64(0)
+    N.call("rd_alu_peak", {"fp32": N.PEAK_FP32, "fp64": N.PEAK_FP64}[kind], int(iters), int(ctas_per_sm),
+           _ptr(sink), ctypes.byref(fl), _stream(stream))
+    return int(fl.value)
 
 
 class RootsFn(torch.autograd.Function):

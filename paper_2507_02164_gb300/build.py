@@ -59,6 +59,19 @@ def _deps():
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
+def source_hash() -> str:
+    """Hash of every source the library is built from (16 hex digits): a
+    cached result that depends on the kernels (the autotuner's shapes) is
+    keyed on it, so a rebuilt library is measured again."""
+    import hashlib
+    h = hashlib.sha256()
+    for p in sorted(_deps()):
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def stale() -> bool:
     if not os.path.exists(LIB_PATH):
         return True

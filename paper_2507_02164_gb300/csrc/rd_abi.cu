@@ -18,8 +18,11 @@ int launch_solve_ws(int degree, rd_dtype dt, const SolveArgs &a, int block, int 
                     int ring_slots, cudaStream_t st);
 int launch_solve_ws_selftest(const SolveArgs &a, cudaStream_t st);
 int lanes_for(int degree, bool mixed, int polish_mode, int requested);
-int launch_density(const double *roots, int64_t n, const Binner &bin, uint32_t *hist, rd_stats *stats,
+int launch_density(const double *roots, int64_t n, const DensityArgs &D, uint32_t *hist, rd_stats *stats,
                    cudaStream_t st);
+int launch_backward_uneven(rd_dtype dt, const void *coeffs, const uint8_t *degrees, const int64_t *offsets,
+                           int64_t n, int64_t n_coeffs, const double *roots, const double *grad_roots,
+                           void *grad_coeffs, uint8_t *status, cudaStream_t st);
 int launch_clear(uint32_t *p, int64_t words, cudaStream_t st);
 int launch_backward(int degree, rd_dtype dt, const void *coeffs, const double *roots, const double *grad_roots,
                     void *grad_coeffs, uint8_t *status, int64_t n, cudaStream_t st);
@@ -123,6 +126,18 @@ int check_params(const rd_params &p)
     return RD_OK;
 }
 
+// Validate a tile clip (host struct, device arrays) for n polynomials.
+int check_clip(const rd_clip &c, int64_t n)
+{
+    if (!c.centres || !aligned(c.centres, 16)) return rd_set_error(RD_EINVAL, "clip.centres null or misaligned");
+    if (!(c.radius > 0) || !std::isfinite(c.radius)) return rd_set_error(RD_EINVAL, "clip.radius must be > 0");
+    if (c.nx < 1 || c.ny < 1 || !window_ok(c.tiles)) return rd_set_error(RD_EINVAL, "clip tile grid invalid");
+    if (c.tile_index && !aligned(c.tile_index, 8)) return rd_set_error(RD_EINVAL, "clip.tile_index misaligned");
+    if (!c.tile_index && n > (int64_t)c.nx * c.ny)
+        return rd_set_error(RD_EINVAL, "clip: n exceeds nx*ny without tile_index");
+    return RD_OK;
+}
+
 // Validate the arguments shared by every solve entry point and fill the
 // kernel argument block (everything except the coefficient layout).
 int build_solve_args(rd_dtype dtype, int degree_for_tol, rd_mode mode, const rd_params *params, const rd_clip *clip,
@@ -161,6 +176,7 @@ int build_solve_args(rd_dtype dtype, int degree_for_tol, rd_mode mode, const rd_
             if (!clip->centres || !aligned(clip->centres, 16)) return rd_set_error(RD_EINVAL, "clip.centres null or misaligned");
             if (!(clip->radius > 0) || !std::isfinite(clip->radius)) return rd_set_error(RD_EINVAL, "clip.radius must be > 0");
             if (clip->nx < 1 || clip->ny < 1 || !window_ok(clip->tiles)) return rd_set_error(RD_EINVAL, "clip tile grid invalid");
+            if (clip->tile_index && !aligned(clip->tile_index, 8)) return rd_set_error(RD_EINVAL, "clip.tile_index misaligned");
             a.clip_on = 1;
             a.centres = clip->centres;
             a.radius = clip->radius;
@@ -290,18 +306,36 @@ int rd_roots_density(const void *coeffs, rd_dtype dtype, int degree, int64_t n, 
                         stream);
 }
 
-int rd_density_accumulate(const double *roots, int64_t n_roots, rd_window window, int W, int H, uint32_t *hist,
-                          rd_stats *stats, void *stream)
+int rd_density_accumulate(const double *roots, const uint8_t *status, int64_t n_roots, int64_t n_polys,
+                          rd_window window, int W, int H, const rd_clip *clip, uint32_t *hist, rd_stats *stats,
+                          void *stream)
 {
-    if (n_roots < 0) return rd_set_error(RD_EINVAL, "n_roots < 0");
+    if (n_roots < 0 || n_polys < 0) return rd_set_error(RD_EINVAL, "n_roots and n_polys must be >= 0");
     if (!hist || !aligned(hist, 4)) return rd_set_error(RD_EINVAL, "hist null or misaligned");
     if (n_roots > 0 && (!roots || !aligned(roots, 16))) return rd_set_error(RD_EINVAL, "roots null or misaligned");
     if (!window_ok(window)) return rd_set_error(RD_EINVAL, "window must be finite with xmin < xmax, ymin < ymax");
     if (W < 1 || H < 1 || (int64_t)W * H > ((int64_t)1 << 31)) return rd_set_error(RD_EINVAL, "bad histogram size");
     if (stats && !aligned(stats, 8)) return rd_set_error(RD_EINVAL, "stats misaligned");
+    if ((status || clip) && n_polys == 0) return rd_set_error(RD_EINVAL, "status and clip need n_polys > 0");
+    if (n_polys > 0 && n_roots % n_polys != 0)
+        return rd_set_error(RD_EINVAL, "n_roots (%lld) must be a multiple of n_polys (%lld)", (long long)n_roots,
+                            (long long)n_polys);
+    rd::DensityArgs D;
+    std::memset(&D, 0, sizeof(D));
+    D.bin = make_binner(window, W, H);
+    D.status = status;
+    D.n_polys = n_polys;
+    if (clip) {
+        int rc = check_clip(*clip, n_polys);
+        if (rc) return rc;
+        D.clip_on = 1;
+        D.centres = clip->centres;
+        D.radius = clip->radius;
+        D.tile_index = clip->tile_index;
+        D.tiles = make_binner(clip->tiles, clip->nx, clip->ny);
+    }
     if (n_roots == 0) return RD_OK;
-    return rd::launch_density(roots, n_roots, make_binner(window, W, H), hist, stats,
-                              reinterpret_cast<cudaStream_t>(stream));
+    return rd::launch_density(roots, n_roots, D, hist, stats, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int rd_hist_clear(uint32_t *hist, int64_t words, void *stream)
@@ -314,8 +348,8 @@ int rd_hist_clear(uint32_t *hist, int64_t words, void *stream)
 
 size_t rd_uneven_workspace_bytes(int64_t n, int64_t n_coeffs, rd_dtype dtype)
 {
-    if (n < 0 || n_coeffs < 0 || (dtype != RD_C64 && dtype != RD_C128)) return 0;
-    return rd::uneven_workspace_bytes(n, n_coeffs, dtype);
+    if (dtype != RD_C64 && dtype != RD_C128) return 0;
+    return rd::uneven_workspace_bytes(n, n_coeffs, dtype);  // 0 outside n < 2^32, n_coeffs <= 2^40
 }
 
 int rd_roots_uneven(const void *coeffs, rd_dtype dtype, const uint8_t *degrees, const int64_t *offsets, int64_t n,
@@ -325,6 +359,7 @@ int rd_roots_uneven(const void *coeffs, rd_dtype dtype, const uint8_t *degrees, 
 {
     if (n < 0 || n_coeffs < 0) return rd_set_error(RD_EINVAL, "n and n_coeffs must be >= 0");
     if (n >= ((int64_t)1 << 32)) return rd_set_error(RD_EINVAL, "n must be below 2^32");
+    if (n_coeffs > ((int64_t)1 << 40)) return rd_set_error(RD_EINVAL, "n_coeffs must be at most 2^40");
     if ((hist == nullptr) != (window == nullptr)) return rd_set_error(RD_EINVAL, "hist and window go together");
     rd::SolveArgs a;
     rd_params p;
@@ -380,25 +415,61 @@ int rd_roots_backward(const void *coeffs, rd_dtype dtype, int degree, int64_t n,
                                reinterpret_cast<cudaStream_t>(stream));
 }
 
-int rd_l2_nodes(int nr, double *r, double *w)
+int rd_roots_backward_uneven(const void *coeffs, rd_dtype dtype, const uint8_t *degrees, const int64_t *offsets,
+                             int64_t n, int64_t n_coeffs, const double *roots, const double *grad_roots,
+                             void *grad_coeffs, uint8_t *status, void *stream)
 {
-    if (nr < 1 || nr > 32) return rd_set_error(RD_EINVAL, "nr must be in 1..32");
-    if (!r || !w) return rd_set_error(RD_EINVAL, "r / w null");
-    return rd::l2_nodes_host(nr, r, w);
+    if (dtype != RD_C64 && dtype != RD_C128) return rd_set_error(RD_EINVAL, "dtype must be RD_C64 or RD_C128");
+    if (n < 0 || n_coeffs < 0) return rd_set_error(RD_EINVAL, "n and n_coeffs must be >= 0");
+    if (n >= ((int64_t)1 << 32)) return rd_set_error(RD_EINVAL, "n must be below 2^32");
+    if (n_coeffs > ((int64_t)1 << 40)) return rd_set_error(RD_EINVAL, "n_coeffs must be at most 2^40");
+    if (n == 0) return RD_OK;
+    size_t el = dtype == RD_C64 ? 8 : 16;
+    if (!coeffs || !aligned(coeffs, el) || !grad_coeffs || !aligned(grad_coeffs, el))
+        return rd_set_error(RD_EINVAL, "coeffs / grad_coeffs null or misaligned");
+    if (!degrees || !offsets || !aligned(offsets, 8)) return rd_set_error(RD_EINVAL, "degrees / offsets null or misaligned");
+    if (!roots || !aligned(roots, 16) || !grad_roots || !aligned(grad_roots, 16))
+        return rd_set_error(RD_EINVAL, "roots / grad_roots null or misaligned");
+    return rd::launch_backward_uneven(dtype, coeffs, degrees, offsets, n, n_coeffs, roots, grad_roots, grad_coeffs,
+                                      status, reinterpret_cast<cudaStream_t>(stream));
 }
 
-int rd_l2_approx(const double *samples, int64_t n, int nr, int nt, int degree, int precision, double *coeffs,
-                 void *stream)
+int rd_l2_nodes(int nr, int nt, double *r, double *theta, double *w)
+{
+    if (nr < 1 || nr > 32) return rd_set_error(RD_EINVAL, "nr must be in 1..32");
+    if (nt < 1 || nt > 4096) return rd_set_error(RD_EINVAL, "nt must be in 1..4096");
+    if (!r || !w) return rd_set_error(RD_EINVAL, "r / w null");
+    int rc = rd::l2_nodes_host(nr, r, w);
+    if (rc) return rc;
+    const double pi = 3.14159265358979323846;
+    if (theta)
+        for (int q = 0; q < nt; ++q) theta[q] = 2.0 * pi * q / nt;
+    return RD_OK;
+}
+
+int rd_l2_approx(const double *samples, int64_t n, int nr, int nt, int degree, int precision, const double *centres,
+                 double radius, double *coeffs, rd_clip *map, void *stream)
 {
     if (precision != RD_L2_FP64 && precision != RD_L2_DF) return rd_set_error(RD_EINVAL, "precision must be RD_L2_FP64 or RD_L2_DF");
     if (nt != 32) return rd_set_error(RD_EUNSUPPORTED, "nt must be 32 (one angle per lane)");
     if (nr < 1 || nr > 32) return rd_set_error(RD_EINVAL, "nr must be in 1..32");
     if (degree < 0 || degree > 12) return rd_set_error(RD_EINVAL, "degree must be in 0..12");
     if (n < 0) return rd_set_error(RD_EINVAL, "n < 0");
-    if (n == 0) return RD_OK;
-    if (!samples || !aligned(samples, 16) || !coeffs || !aligned(coeffs, 16))
+    if (map) {
+        if (!centres || !aligned(centres, 16)) return rd_set_error(RD_EINVAL, "centres null or misaligned (16 B)");
+        if (!(radius > 0) || !std::isfinite(radius)) return rd_set_error(RD_EINVAL, "radius must be finite and > 0");
+    }
+    if (n > 0 && (!samples || !aligned(samples, 16) || !coeffs || !aligned(coeffs, 16)))
         return rd_set_error(RD_EINVAL, "samples / coeffs null or misaligned");
-    return rd::launch_l2(samples, n, nr, degree, coeffs, precision, reinterpret_cast<cudaStream_t>(stream));
+    if (n > 0) {
+        int rc = rd::launch_l2(samples, n, nr, degree, coeffs, precision, reinterpret_cast<cudaStream_t>(stream));
+        if (rc) return rc;
+    }
+    if (map) {
+        map->centres = centres;
+        map->radius = radius;
+    }
+    return RD_OK;
 }
 
 namespace {

@@ -106,6 +106,107 @@ static int launch_bw(int degree, const void *coeffs, const double *roots, const 
     return rd_check_launch("backward_kernel");
 }
 
+// Packed batch of uneven degrees (the layout of rd_roots_uneven): one thread
+// per polynomial with its degree d (1..12) a runtime value. The coefficient
+// and gradient arrays are sized for degree 12 and indexed only by unrolled
+// constants under k <= d predicates, so they stay in registers; the
+// arithmetic is the uniform kernel's operation for operation (p'(z) starts
+// from 0 z + d a_d = d a_d exactly), so a batch of one degree gives the same
+// bits either way. A polynomial is differentiated under rd_roots_uneven's
+// consistency rule, which keeps every read and write inside the arrays.
+template <typename T>
+__global__ void __launch_bounds__(128) backward_uneven_kernel(const void *coeffs, const uint8_t *__restrict__ degrees,
+                                                              const int64_t *__restrict__ offsets, int64_t n,
+                                                              int64_t n_coeffs, const double2 *__restrict__ roots,
+                                                              const double2 *__restrict__ grad_roots,
+                                                              void *grad_coeffs, uint8_t *status)
+{
+    constexpr int NMAX = 12;
+    using V = typename CLoad<T>::V;
+    const V *A = reinterpret_cast<const V *>(coeffs);
+    V *G = reinterpret_cast<V *>(grad_coeffs);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const T tiny = sizeof(T) == 8 ? (T)1e-300 : (T)0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int d = __ldg(degrees + i);
+        const int64_t o0 = __ldg(offsets + i), o1 = __ldg(offsets + i + 1);
+        const bool consistent = (o0 >= i) && (o1 >= o0) && (o1 <= n_coeffs - (n - 1 - i)) && (o1 - o0 == (int64_t)d + 1);
+        if (!consistent) {
+            if (status) status[i] = RD_STATUS_DEGENERATE;
+            continue;
+        }
+        if (d < 1 || d > NMAX) {
+            for (int k = 0; k <= d; ++k) G[o0 + k] = V{T(0), T(0)};
+            if (status) status[i] = RD_STATUS_DEGENERATE;
+            continue;
+        }
+        cx<T> a[NMAX + 1], g[NMAX + 1];
+#pragma unroll
+        for (int k = 0; k <= NMAX; ++k) {
+            V v = k <= d ? A[o0 + k] : V{T(0), T(0)};
+            a[k] = {v.x, v.y};
+            g[k] = {T(0), T(0)};
+        }
+        const int64_t r0 = o0 - i;
+        bool singular = false;
+        for (int j = 0; j < d; ++j) {
+            double2 zr = roots[r0 + j];
+            double2 gr = grad_roots[r0 + j];
+            cx<T> z = {(T)zr.x, (T)zr.y};
+            cx<T> gz = {(T)gr.x, (T)gr.y};
+            cx<T> dp = {T(0), T(0)};
+#pragma unroll
+            for (int k = NMAX; k >= 1; --k)
+                if (k <= d) dp = cfma(dp, z, scale((T)k, a[k]));
+            const T m = fmax(fabs(dp.re), fabs(dp.im));
+            bool big = m > tiny;
+            if (!big && m > tiny * (T)0.70710678118654752) big = hypot(dp.re, dp.im) > tiny;
+            bool bad = !(isfinite(dp.re) && isfinite(dp.im) && isfinite(z.re) && isfinite(z.im)) || !big;
+            singular |= bad;
+            if (bad) continue;
+            cx<T> inv = cdiv(cx<T>{T(1), T(0)}, dp);
+            cx<T> u = mul(cx<T>{-inv.re, inv.im}, gz);
+            cx<T> zc = {z.re, -z.im};
+            cx<T> pw = {T(1), T(0)};
+#pragma unroll
+            for (int k = 0; k <= NMAX; ++k)
+                if (k <= d) {
+                    g[k] = cfma(pw, u, g[k]);
+                    pw = mul(pw, zc);
+                }
+        }
+#pragma unroll
+        for (int k = 0; k <= NMAX; ++k)
+            if (k <= d) {
+                V v;
+                v.x = g[k].re;
+                v.y = g[k].im;
+                G[o0 + k] = v;
+            }
+        if (status) status[i] = singular ? RD_STATUS_REJECTED : RD_STATUS_OK;
+    }
+}
+
+int launch_backward_uneven(rd_dtype dt, const void *coeffs, const uint8_t *degrees, const int64_t *offsets,
+                           int64_t n, int64_t n_coeffs, const double *roots, const double *grad_roots,
+                           void *grad_coeffs, uint8_t *status, cudaStream_t st)
+{
+    const int block = 128;
+    int64_t ctas = (n + block - 1) / block;
+    int64_t cap = (int64_t)rd_sm_count_cached() * 16;
+    if (ctas > cap) ctas = cap;
+    if (ctas < 1) ctas = 1;
+    auto R = reinterpret_cast<const double2 *>(roots);
+    auto GR = reinterpret_cast<const double2 *>(grad_roots);
+    if (dt == RD_C64)
+        backward_uneven_kernel<float><<<(unsigned)ctas, block, 0, st>>>(coeffs, degrees, offsets, n, n_coeffs, R, GR,
+                                                                         grad_coeffs, status);
+    else
+        backward_uneven_kernel<double><<<(unsigned)ctas, block, 0, st>>>(coeffs, degrees, offsets, n, n_coeffs, R, GR,
+                                                                          grad_coeffs, status);
+    return rd_check_launch("backward_uneven_kernel");
+}
+
 int launch_backward(int degree, rd_dtype dt, const void *coeffs, const double *roots, const double *grad_roots,
                     void *grad_coeffs, uint8_t *status, int64_t n, cudaStream_t st)
 {

@@ -316,6 +316,18 @@ __device__ __forceinline__ int pixel_of(const Binner &b, double x, double y)
     return in ? iy * b.W + ix : -1;
 }
 
+// Arguments of the standalone binning kernel (rd_density.cu).
+struct DensityArgs {
+    Binner bin;
+    const uint8_t *status;  // [n_polys] or null
+    int64_t n_polys;        // 0: ungrouped (no status, no clip)
+    int clip_on;
+    const double *centres;  // rd_c128 [n_polys]
+    double radius;
+    const int64_t *tile_index;  // [n_polys] or null (= polynomial index)
+    Binner tiles;
+};
+
 // Warp-aggregated histogram increment: lanes holding the same pixel elect one
 // leader that adds the group size. Lanes with pix < 0 take no part.
 __device__ __forceinline__ void hist_add(uint32_t *hist, int pix)

@@ -29,13 +29,29 @@ struct UnevenArgs {
 };
 
 // A polynomial is solvable when its offsets hold exactly degree + 1
-// coefficients inside the array and its degree is 1..12.
+// coefficients, its degree is 1..12, and its roots fit the packed root array
+// of n_coeffs - n elements: o0 >= i keeps root 0 (at o0 - i) at or above 0,
+// o1 <= n_coeffs - (n - 1 - i) keeps its last root (at o1 - i - 2) below
+// n_coeffs - n. The comparisons are ordered so that no difference overflows.
+// These bounds hold for each polynomial alone; polynomials whose ranges
+// overlap (offsets that are not monotone) are caught by the total the scan
+// kernel checks.
 __device__ __forceinline__ int checked_degree(const UnevenArgs &U, int64_t i, bool &consistent)
 {
     int d = __ldg(U.degrees + i);
     int64_t o0 = __ldg(U.offsets + i), o1 = __ldg(U.offsets + i + 1);
-    consistent = (o0 >= 0) && (o1 <= U.n_coeffs) && (o1 - o0 == (int64_t)d + 1);
+    consistent = (o0 >= i) && (o1 >= o0) && (o1 <= U.n_coeffs - (U.n - 1 - i)) && (o1 - o0 == (int64_t)d + 1);
     return (consistent && d >= 1 && d <= UNEVEN_MAX_DEG) ? d : -1;
+}
+
+// NaN roots of polynomial i (its offsets passed checked_degree's bounds).
+__device__ __forceinline__ void nan_roots(const UnevenArgs &U, int64_t i, double *roots)
+{
+    if (!roots) return;
+    const int dd = __ldg(U.degrees + i);
+    const int64_t r0 = __ldg(U.offsets + i) - i;
+    const double q = __longlong_as_double(0x7ff8000000000000ll);
+    for (int j = 0; j < dd; ++j) reinterpret_cast<double2 *>(roots)[r0 + j] = make_double2(q, q);
 }
 
 // Count polynomials per degree; mark the unsolvable ones DEGENERATE (NaN
@@ -63,13 +79,7 @@ __global__ void __launch_bounds__(256) uneven_count_kernel(UnevenArgs U, UnevenH
                 invalid += 1;
                 bad += consistent ? 0u : 1u;
                 if (status) status[i] = RD_STATUS_DEGENERATE;
-                if (roots && consistent) {
-                    int dd = __ldg(U.degrees + i);
-                    int64_t r0 = __ldg(U.offsets + i) - i;
-                    for (int j = 0; j < dd; ++j)
-                        reinterpret_cast<double2 *>(roots)[r0 + j] =
-                            make_double2(__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
-                }
+                if (consistent) nan_roots(U, i, roots);
             }
         }
     }
@@ -83,8 +93,12 @@ __global__ void __launch_bounds__(256) uneven_count_kernel(UnevenArgs U, UnevenH
 }
 
 // Bin bases: poly_base[d] = sum of count[d'] for d' < d, coef_base[d] = sum
-// of count[d'] (d' + 1). One warp.
-__global__ void uneven_scan_kernel(UnevenHeader *hdr)
+// of count[d'] (d' + 1). One warp. When the solvable polynomials need more
+// than n_coeffs coefficients in all, their ranges overlap (offsets that are
+// not monotone) and the bins would not fit the workspace: the batch is then
+// not packed or solved (overflow = 1, every count 0), and the pack kernel
+// marks its solvable polynomials DEGENERATE instead.
+__global__ void uneven_scan_kernel(UnevenHeader *hdr, int64_t n_coeffs)
 {
     const int lane = threadIdx.x;
     unsigned c = lane < 16 ? hdr->count[lane] : 0u;
@@ -100,12 +114,16 @@ __global__ void uneven_scan_kernel(UnevenHeader *hdr)
             pe += oe;
         }
     }
+    const int64_t total = __shfl_sync(0xffffffffu, pe, 31);
+    const bool overflow = total > n_coeffs;
     if (lane < 16) {
         hdr->poly_base[lane] = pc - c;  // exclusive
         hdr->coef_base[lane] = pe - e;
         hdr->cursor[lane] = 0;
+        hdr->head[lane] = 0;
+        if (overflow) hdr->count[lane] = 0;
     }
-    if (lane < 16) hdr->head[lane] = 0;
+    if (lane == 0) hdr->overflow = overflow ? 1u : 0u;
 }
 
 // Scatter every solvable polynomial into its degree's bin: a slot from a
@@ -113,11 +131,32 @@ __global__ void uneven_scan_kernel(UnevenHeader *hdr)
 // coefficient-major at bins[coef_base[d] + k * count[d] + slot].
 template <typename E>
 __global__ void __launch_bounds__(256) uneven_pack_kernel(UnevenArgs U, const E *__restrict__ coeffs,
-                                                          UnevenHeader *hdr, uint32_t *perm, E *bins)
+                                                          UnevenHeader *hdr, uint32_t *perm, E *bins,
+                                                          double *roots, uint8_t *status, rd_stats *stats)
 {
     const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t warp_id = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
+    if (hdr->overflow) {
+        // overlapping ranges: nothing is packed; the solvable polynomials are
+        // reported DEGENERATE with NaN roots (their own bounds hold)
+        __shared__ unsigned long long acc[ST_WORDS];
+        const CtaStats S = stats_begin(acc, stats);
+        unsigned marked = 0;
+        for (int64_t base = warp_id * 32; base < U.n; base += warps_total * 32) {
+            int64_t i = base + lane;
+            bool consistent;
+            if (i < U.n && checked_degree(U, i, consistent) > 0) {
+                marked += 1;
+                if (status) status[i] = RD_STATUS_DEGENERATE;
+                nan_roots(U, i, roots);
+            }
+        }
+        S.add(ST_POLYS, marked);
+        S.add(ST_STATUS0 + RD_STATUS_DEGENERATE, marked);
+        stats_end(S, stats);
+        return;
+    }
     for (int64_t base = warp_id * 32; base < U.n; base += warps_total * 32) {
         int64_t i = base + lane;
         int d = -1;
@@ -145,6 +184,7 @@ __global__ void __launch_bounds__(256) uneven_pack_kernel(UnevenArgs U, const E 
 
 size_t uneven_workspace_bytes(int64_t n, int64_t n_coeffs, rd_dtype dt)
 {
+    if (!uneven_sizes_ok(n, n_coeffs)) return 0;
     return uneven_bytes(n, n_coeffs, dt == RD_C64 ? 8 : 16);
 }
 
@@ -163,14 +203,16 @@ int launch_uneven(const SolveArgs &a, rd_dtype dt, const uint8_t *degrees, const
     if (ctas < 1) ctas = 1;
     uneven_count_kernel<<<(unsigned)ctas, tb, 0, st>>>(U, L.hdr, a.roots, a.status, a.stats);
     if ((rc = rd_check_launch("uneven_count_kernel"))) return rc;
-    uneven_scan_kernel<<<1, 32, 0, st>>>(L.hdr);
+    uneven_scan_kernel<<<1, 32, 0, st>>>(L.hdr, n_coeffs);
     if ((rc = rd_check_launch("uneven_scan_kernel"))) return rc;
     if (dt == RD_C64)
         uneven_pack_kernel<float2><<<(unsigned)ctas, tb, 0, st>>>(U, reinterpret_cast<const float2 *>(a.coeffs), L.hdr,
-                                                                  L.perm, reinterpret_cast<float2 *>(L.bins));
+                                                                  L.perm, reinterpret_cast<float2 *>(L.bins), a.roots,
+                                                                  a.status, a.stats);
     else
         uneven_pack_kernel<double2><<<(unsigned)ctas, tb, 0, st>>>(U, reinterpret_cast<const double2 *>(a.coeffs),
-                                                                   L.hdr, L.perm, reinterpret_cast<double2 *>(L.bins));
+                                                                   L.hdr, L.perm, reinterpret_cast<double2 *>(L.bins),
+                                                                   a.roots, a.status, a.stats);
     if ((rc = rd_check_launch("uneven_pack_kernel"))) return rc;
     const int mode = !mixed ? MODE_PLAIN : (a.polish_mode == RD_POLISH_DF ? MODE_MIXED_DF : MODE_MIXED_FP64);
     if (dt == RD_C64) {

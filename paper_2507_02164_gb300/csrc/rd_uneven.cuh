@@ -17,7 +17,8 @@ struct UnevenHeader {
     uint32_t poly_base[16];  // first slot of each degree's bin in perm
     uint32_t head[16];       // task queue head of each degree's solve kernel
     uint32_t bad;            // polynomials whose offsets disagree with their degree
-    uint32_t pad[3];
+    uint32_t overflow;       // 1: the solvable polynomials overlap (sum of (d + 1) > n_coeffs)
+    uint32_t pad[2];
     int64_t coef_base[16];   // first element of each degree's bin in the bins region
 };
 static_assert(sizeof(UnevenHeader) <= 512, "header must fit its 512-byte slot");
@@ -31,6 +32,16 @@ struct UnevenLayout {
     uint32_t *perm;
     char *bins;
 };
+
+// Largest batch the uneven path takes: n < 2^32 polynomials (32-bit slots)
+// and n_coeffs <= 2^40 coefficients, so that no workspace size wraps.
+constexpr int64_t UNEVEN_MAX_N = (int64_t)1 << 32;
+constexpr int64_t UNEVEN_MAX_COEFFS = (int64_t)1 << 40;
+
+inline bool uneven_sizes_ok(int64_t n, int64_t n_coeffs)
+{
+    return n >= 0 && n < UNEVEN_MAX_N && n_coeffs >= 0 && n_coeffs <= UNEVEN_MAX_COEFFS;
+}
 
 inline size_t uneven_bytes(int64_t n, int64_t n_coeffs, size_t elem)
 {

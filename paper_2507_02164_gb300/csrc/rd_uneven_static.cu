@@ -23,9 +23,14 @@ static __device__ __align__(256) unsigned char g_uneven_scratch[RD_STATIC_SCRATC
 
 namespace {
 
-// Device address of g_uneven_scratch, looked up once per device with that
-// device current.
-int scratch_address(void **out)
+// Device address of g_uneven_scratch on the current device. A call whose
+// stream is not being captured looks it up again with that device current
+// (a cheap runtime query once the module is loaded), so the address follows
+// a cudaDeviceReset, after which the library's module, and with it the
+// array, is loaded anew; a call under stream capture takes the address the
+// last call outside capture found on this device (capture forbids module
+// loading), and fails if there was none.
+int scratch_address(cudaStream_t st, void **out)
 {
     static std::mutex mu;
     static void *addr[64] = {nullptr};
@@ -33,13 +38,19 @@ int scratch_address(void **out)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return rd_set_error(RD_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= 64) return rd_set_error(RD_EUNSUPPORTED, "device index %d above 63", dev);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return rd_set_error(RD_ECUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(e));
     std::lock_guard<std::mutex> lk(mu);
-    if (!addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_uneven_scratch);
         if (e != cudaSuccess || !p)
             return rd_set_error(RD_ECUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
         addr[dev] = p;
+    } else if (!addr[dev]) {
+        return rd_set_error(RD_EINVAL, "the first call on a device must come before any stream capture "
+                                       "(it looks up the static scratch)");
     }
     *out = addr[dev];
     return RD_OK;
@@ -54,15 +65,17 @@ extern "C" int rd_roots_uneven_static(const void *coeffs, rd_dtype dtype, const 
                                       uint8_t *status, rd_stats *stats, void *stream)
 {
     if (n < 0 || n_coeffs < 0) return rd_set_error(RD_EINVAL, "n and n_coeffs must be >= 0");
+    if (dtype != RD_C64 && dtype != RD_C128) return rd_set_error(RD_EINVAL, "dtype must be RD_C64 or RD_C128");
     size_t need = rd_uneven_workspace_bytes(n, n_coeffs, dtype);
-    if (need == 0) return rd_set_error(RD_EINVAL, "dtype must be RD_C64 or RD_C128");
+    if (need == 0)
+        return rd_set_error(RD_EINVAL, "batch too large for the uneven path (it takes n < 2^32 and n_coeffs <= 2^40), let alone the built-in scratch");
     if (need > (size_t)RD_STATIC_SCRATCH_BYTES)
         return rd_set_error(RD_EINVAL,
                             "batch needs %zu bytes of scratch; the built-in scratch holds %zu "
                             "(split the batch, or call rd_roots_uneven with your own workspace)",
                             need, (size_t)RD_STATIC_SCRATCH_BYTES);
     void *ws = nullptr;
-    int rc = scratch_address(&ws);
+    int rc = scratch_address(reinterpret_cast<cudaStream_t>(stream), &ws);
     if (rc) return rc;
     // the same launch sequence as rd_roots_uneven; its first launch clears the
     // scratch header, every other scratch byte is written before it is read

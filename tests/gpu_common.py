@@ -60,6 +60,22 @@ def compare_roots(gpu: np.ndarray, ref: np.ndarray, coeffs: np.ndarray, orc, tol
     return summary, g
 
 
+REJECTED_KAPPA_MIN = 100.0
+
+
+def check_rejected(coeffs: np.ndarray, status: np.ndarray, ref_roots: np.ndarray, orc,
+                   kappa_min: float = REJECTED_KAPPA_MIN):
+    """The mixed path may mark a polynomial REJECTED (status 2) only when its
+    roots are ill-conditioned: the largest condition number of its oracle
+    roots exceeds kappa_min. A polish bug that rejected well-conditioned
+    polynomials, which the parity comparisons leave out, fails here."""
+    rej = status == 2
+    if rej.any():
+        kap = orc.root_condition(coeffs[rej], ref_roots[rej]).max(axis=1)
+        assert kap.min() > kappa_min, (int(rej.sum()), float(kap.min()))
+    return int(rej.sum())
+
+
 def edge_distance(z: np.ndarray, window, W: int, H: int) -> np.ndarray:
     """Absolute distance in the plane from z to the nearest pixel edge line."""
     xmin, xmax, ymin, ymax = window

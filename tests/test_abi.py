@@ -23,7 +23,7 @@ def declared_functions():
 
 def test_library_builds_and_loads():
     L = N.load()
-    assert L.rd_abi_version() == 1
+    assert L.rd_abi_version() == N.ABI_VERSION == 2
 
 
 def test_every_declared_symbol_is_exported_and_bound():
@@ -37,6 +37,7 @@ def test_every_declared_symbol_is_exported_and_bound():
 
 
 def test_struct_sizes_match_header_layout():
+    assert ctypes.sizeof(N.TuneEntry) == 20 and ctypes.sizeof(N.Tuning) == 48
     assert ctypes.sizeof(N.Params) == 72
     assert ctypes.sizeof(N.Window) == 32
     assert ctypes.sizeof(N.Clip) == 64
@@ -57,7 +58,10 @@ def test_default_params():
 def test_library_gauss_legendre_matches_numpy(nr):
     r = (ctypes.c_double * nr)()
     w = (ctypes.c_double * nr)()
-    assert N.load().rd_l2_nodes(nr, ctypes.cast(r, ctypes.c_void_p), ctypes.cast(w, ctypes.c_void_p)) == 0
+    th = (ctypes.c_double * 32)()
+    assert N.load().rd_l2_nodes(nr, 32, ctypes.cast(r, ctypes.c_void_p), ctypes.cast(th, ctypes.c_void_p),
+                                ctypes.cast(w, ctypes.c_void_p)) == 0
+    assert np.array_equal(np.array(th), 2.0 * np.pi * np.arange(32) / 32)
     t, wt = np.polynomial.legendre.leggauss(nr)
     assert np.allclose(np.array(r), 0.5 * (t + 1), atol=2e-16, rtol=0)
     assert np.allclose(np.array(w), 0.5 * wt, atol=0, rtol=1e-13)
@@ -102,24 +106,77 @@ def test_argument_validation_without_gpu():
     # empty batch is a no-op
     assert L.rd_roots_batched(null, N.C64, 6, 0, N.MIXED, ctypes.byref(p), null, null, null, null) == 0
     # density: inverted window, bad size, null hist
+    h64 = ctypes.c_void_p(64)
+
+    def dens(roots, status, n_roots, n_polys, win, Wd, Hd, clip, hist):
+        return _err(L.rd_density_accumulate(roots, status, n_roots, n_polys, win, Wd, Hd, clip, hist, null, null))
+
     w_bad = N.Window(1.0, -1.0, -1.0, 1.0)
-    rc, _ = _err(L.rd_density_accumulate(ctypes.c_void_p(64), 4, w_bad, 16, 16, ctypes.c_void_p(64), null, null))
-    assert rc == N.RD_EINVAL
+    assert dens(h64, null, 4, 0, w_bad, 16, 16, None, h64)[0] == N.RD_EINVAL
     w = N.Window(-1.0, 1.0, -1.0, 1.0)
-    rc, _ = _err(L.rd_density_accumulate(ctypes.c_void_p(64), 4, w, 0, 16, ctypes.c_void_p(64), null, null))
-    assert rc == N.RD_EINVAL
-    rc, _ = _err(L.rd_density_accumulate(ctypes.c_void_p(64), 4, w, 16, 16, null, null, null))
-    assert rc == N.RD_EINVAL
+    assert dens(h64, null, 4, 0, w, 0, 16, None, h64)[0] == N.RD_EINVAL
+    assert dens(h64, null, 4, 0, w, 16, 16, None, null)[0] == N.RD_EINVAL
     nanw = N.Window(float("nan"), 1.0, -1.0, 1.0)
-    rc, _ = _err(L.rd_density_accumulate(ctypes.c_void_p(64), 4, nanw, 16, 16, ctypes.c_void_p(64), null, null))
-    assert rc == N.RD_EINVAL
+    assert dens(h64, null, 4, 0, nanw, 16, 16, None, h64)[0] == N.RD_EINVAL
+    # the status mask and the clip need the roots grouped by polynomial
+    rc, msg = dens(h64, h64, 4, 0, w, 16, 16, None, h64)
+    assert rc == N.RD_EINVAL and "n_polys" in msg
+    rc, msg = dens(h64, h64, 6, 4, w, 16, 16, None, h64)
+    assert rc == N.RD_EINVAL and "multiple" in msg
+    clip = N.Clip(centres=None, radius=0.1, tile_index=None, nx=4, ny=4, tiles=w)
+    rc, msg = dens(h64, null, 8, 4, w, 16, 16, ctypes.byref(clip), h64)
+    assert rc == N.RD_EINVAL and "centres" in msg
+    clip = N.Clip(centres=64, radius=0.1, tile_index=None, nx=2, ny=1, tiles=w)
+    rc, msg = dens(h64, null, 8, 4, w, 16, 16, ctypes.byref(clip), h64)
+    assert rc == N.RD_EINVAL and "nx*ny" in msg
+    assert dens(null, null, 0, 0, w, 16, 16, None, h64)[0] == 0  # nothing to bin
     # l2: nt must be 32, nr in 1..32
-    rc, _ = _err(L.rd_l2_approx(ctypes.c_void_p(64), 4, 16, 16, 6, 0, ctypes.c_void_p(64), null))
-    assert rc == N.RD_EUNSUPPORTED
-    rc, _ = _err(L.rd_l2_approx(ctypes.c_void_p(64), 4, 40, 32, 6, 0, ctypes.c_void_p(64), null))
+    def l2(s_, n, nr, nt, deg, prec, cen, rad, co, m):
+        return _err(L.rd_l2_approx(s_, n, nr, nt, deg, prec, cen, rad, co, m, null))
+
+    assert l2(h64, 4, 16, 16, 6, 0, null, 0.0, h64, None)[0] == N.RD_EUNSUPPORTED
+    assert l2(h64, 4, 40, 32, 6, 0, null, 0.0, h64, None)[0] == N.RD_EINVAL
+    assert l2(h64, 4, 16, 32, 6, 7, null, 0.0, h64, None)[0] == N.RD_EINVAL
+    # the affine map: centres and radius are checked, then written into the clip
+    m = N.Clip()
+    assert l2(h64, 4, 16, 32, 6, 0, null, 0.5, h64, ctypes.byref(m))[0] == N.RD_EINVAL
+    assert l2(h64, 4, 16, 32, 6, 0, h64, -1.0, h64, ctypes.byref(m))[0] == N.RD_EINVAL
+    assert l2(null, 0, 16, 32, 6, 0, ctypes.c_void_p(4096), 0.25, null, ctypes.byref(m))[0] == 0
+    assert m.centres == 4096 and m.radius == 0.25
+    # l2 nodes: bad sizes
+    buf = (ctypes.c_double * 64)()
+    b = ctypes.cast(buf, ctypes.c_void_p)
+    assert _err(L.rd_l2_nodes(16, 0, b, b, b))[0] == N.RD_EINVAL
+    assert _err(L.rd_l2_nodes(33, 32, b, b, b))[0] == N.RD_EINVAL
+    # uneven sizes beyond 2^32 polynomials or 2^40 coefficients
+    assert L.rd_uneven_workspace_bytes(10, (1 << 40) + 1, N.C64) == 0
+    assert L.rd_uneven_workspace_bytes(1 << 32, 10, N.C64) == 0
+    assert L.rd_uneven_workspace_bytes(10, 100, 7) == 0
+    rc, msg = _err(L.rd_roots_uneven(h64, N.C64, h64, h64, 10, (1 << 40) + 1, N.MIXED, None, None, None, 0, 0,
+                                     null, null, null, null, h64, 1 << 20, null))
+    assert rc == N.RD_EINVAL and "2^40" in msg
+    rc, msg = _err(L.rd_roots_uneven_static(h64, N.C64, h64, h64, 10, (1 << 40) + 1, N.MIXED, None, None, None,
+                                            0, 0, null, null, null, null, null))
     assert rc == N.RD_EINVAL
-    rc, _ = _err(L.rd_l2_approx(ctypes.c_void_p(64), 4, 16, 32, 6, 7, ctypes.c_void_p(64), null))
+    # packed adjoint
+    rc, _ = _err(L.rd_roots_backward_uneven(h64, 5, h64, h64, 4, 20, h64, h64, h64, null, null))
     assert rc == N.RD_EINVAL
+    rc, msg = _err(L.rd_roots_backward_uneven(h64, N.C128, h64, h64, 4, (1 << 40) + 1, h64, h64, h64, null, null))
+    assert rc == N.RD_EINVAL and "2^40" in msg
+    rc, msg = _err(L.rd_roots_backward_uneven(h64, N.C128, null, h64, 4, 20, h64, h64, h64, null, null))
+    assert rc == N.RD_EINVAL and "degrees" in msg
+    assert L.rd_roots_backward_uneven(null, N.C128, null, null, 0, 0, null, null, null, null, null) == 0
+    # autotuner and ALU probe: argument checks come before any device work
+    t = N.Tuning()
+    assert _err(L.rd_autotune(13, N.MIXED, N.C64, 1 << 16, 3, ctypes.byref(t), None, 0, None))[0] == \
+        N.RD_EUNSUPPORTED
+    assert _err(L.rd_autotune(6, N.MIXED, N.C64, 100, 3, ctypes.byref(t), None, 0, None))[0] == N.RD_EINVAL
+    assert _err(L.rd_autotune(6, N.MIXED, N.C64, 1 << 16, 0, ctypes.byref(t), None, 0, None))[0] == N.RD_EINVAL
+    assert _err(L.rd_autotune(6, N.MIXED, N.C64, 1 << 16, 3, None, None, 0, None))[0] == N.RD_EINVAL
+    fl = ctypes.c_uint64()
+    assert _err(L.rd_alu_peak(2, 10, 4, h64, ctypes.byref(fl), null))[0] == N.RD_EINVAL
+    assert _err(L.rd_alu_peak(0, 0, 4, h64, ctypes.byref(fl), null))[0] == N.RD_EINVAL
+    assert _err(L.rd_alu_peak(0, 10, 4, ctypes.c_void_p(65), ctypes.byref(fl), null))[0] == N.RD_EINVAL
     # backward: bad degree / null
     rc, _ = _err(L.rd_roots_backward(null, N.C128, 0, 4, null, null, null, null, null))
     assert rc == N.RD_EUNSUPPORTED

@@ -1,19 +1,11 @@
-"""Autotuner host logic (CPU) and one tuning pass on the GPU."""
+"""Autotuner host logic (CPU) and tuning passes through the C ABI on the GPU."""
+import ctypes
+import os
+
 import pytest
 
-from paper_2507_02164_gb300 import autotune
-
-
-def test_best_shape_takes_the_fastest_with_a_stable_tie_break():
-    table = {(1, 128, 0, 0): 2.0, (2, 64, 0, 0): 1.5, (2, 256, 1, 0): 1.5, (1, 64, 2, 0): 3.0}
-    assert autotune.best_shape(table) == (2, 64, 0, 0)
-
-
-def test_warp_specialised_candidates_fit_the_register_budget():
-    for d in range(1, 13):
-        for block, pw in autotune.ws_candidates(d):
-            assert block % 32 == 0 and 1 <= pw < block // 32
-            assert block <= (512 if d <= 6 else 256)
+from paper_2507_02164_gb300 import _native as N
+from paper_2507_02164_gb300 import autotune, build
 
 
 def test_uneven_tuning_takes_the_one_role_winner_and_uniform_params_the_overall_one():
@@ -23,11 +15,6 @@ def test_uneven_tuning_takes_the_one_role_winner_and_uniform_params_the_overall_
     assert list(t.block)[6] == 256 and list(t.ctas_per_sm)[6] == 2
     p = autotune.degree_params(res, 6)
     assert p.block == 512 and p.polish_warps == 10
-
-
-def test_lane_candidates():
-    assert autotune.lane_candidates(1) == (1,)
-    assert autotune.lane_candidates(2) == (1, 2) and autotune.lane_candidates(12) == (1, 2)
 
 
 def test_uneven_tuning_is_per_degree():
@@ -41,6 +28,52 @@ def test_uneven_tuning_is_per_degree():
         autotune.api.uneven_tuning(block={13: 64})
 
 
+def test_source_hash_follows_every_library_source(tmp_path, monkeypatch):
+    """A cached tuning is keyed on the library's sources: changing any kernel
+    source, header or the C ABI header gives another key."""
+    h0 = build.source_hash()
+    assert h0 == build.source_hash() and len(h0) == 16
+    deps = sorted(build._deps())
+    assert any(p.endswith("rootdensity.h") for p in deps) and any(p.endswith("rd_solve.cuh") for p in deps)
+    fake = tmp_path / "rd_extra.cu"
+    fake.write_text("// one more unit\n")
+    monkeypatch.setattr(build, "_deps", lambda: deps + [str(fake)])
+    assert build.source_hash() != h0
+
+
+@pytest.mark.gpu
+def test_c_autotuner_times_every_candidate_and_picks_the_fastest():
+    from tests.gpu_common import require_gpu
+    require_gpu()
+    L = N.load()
+    for degree, mode in ((6, N.MIXED), (9, N.MIXED), (6, N.PLAIN_FP64)):
+        t = N.Tuning()
+        tab = (N.TuneEntry * 64)()
+        used = ctypes.c_int(0)
+        rc = L.rd_autotune(degree, mode, N.C64 if mode == N.MIXED else N.C128, 1 << 14, 3, ctypes.byref(t), tab, 64,
+                           ctypes.byref(used))
+        assert rc == 0, L.rd_last_error()
+        rows = list(tab[:used.value])
+        assert used.value == t.n_candidates >= 24
+        ok = [r for r in rows if r.ms >= 0]
+        assert ok and all(r.ms > 0 for r in ok)
+        fastest = min(r.ms for r in ok)
+        assert t.best.ms == fastest
+        assert t.one_role.polish_warps == 0 and t.one_role.ms == min(r.ms for r in ok if r.polish_warps == 0)
+        ws = [r for r in rows if r.polish_warps > 0]
+        assert (len(ws) > 0) == (mode == N.MIXED)
+        for r in ws:
+            assert r.lanes == 1 and r.block % 32 == 0 and 1 <= r.polish_warps < r.block // 32
+            assert r.block <= (512 if degree <= 6 else 256)
+        assert {r.lanes for r in rows} == {1, 2}
+    # a table smaller than the candidate list keeps the first entries
+    t = N.Tuning()
+    tab = (N.TuneEntry * 4)()
+    used = ctypes.c_int(0)
+    assert L.rd_autotune(3, N.MIXED, N.C64, 1 << 12, 1, ctypes.byref(t), tab, 4, ctypes.byref(used)) == 0
+    assert used.value == 4 and t.n_candidates > 4
+
+
 @pytest.mark.gpu
 def test_tune_two_degrees_on_gpu(tmp_path):
     from tests.gpu_common import require_gpu
@@ -48,12 +81,13 @@ def test_tune_two_degrees_on_gpu(tmp_path):
     res = autotune.tune("mixed", degrees=(3, 6), n=1 << 14, cache_path=str(tmp_path / "t.json"))
     assert set(res["degrees"]) == {"3", "6"}
     for d, e in res["degrees"].items():
-        ws = {b for b, _ in autotune.ws_candidates(int(d))}
-        assert (e["block"] in autotune.BLOCKS or e["block"] in ws) and e["ms"] > 0
-        assert e["one_role"]["block"] in autotune.BLOCKS and e["one_role"]["ms"] >= e["ms"]
+        assert e["ms"] > 0 and e["one_role"]["ms"] >= e["ms"]
+        assert e["one_role"]["block"] in (32, 64, 128, 256)
+        assert [e["lanes"], e["block"], e["ctas_per_sm"], e["polish_warps"], e["ms"]] in e["table"]
     # a later request for more degrees measures only the new one
     more = autotune.tune("mixed", degrees=(3, 6, 9), n=1 << 14, cache_path=str(tmp_path / "t.json"))
     assert more["degrees"]["3"] == res["degrees"]["3"] and "9" in more["degrees"]
     again = autotune.tune("mixed", degrees=(3, 6, 9), n=1 << 14, cache_path=str(tmp_path / "t.json"))
     assert again["degrees"] == more["degrees"]
     assert {e["lanes"] for e in again["degrees"].values()} <= {1, 2}
+    assert os.path.exists(tmp_path / "t.json")

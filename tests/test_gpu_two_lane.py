@@ -14,7 +14,7 @@ import pytest
 import torch
 
 from paper_2507_02164_gb300 import api, workloads as WL
-from tests.gpu_common import compare_roots, hist_np, require_gpu, roots_poly_major, to_soa
+from tests.gpu_common import check_rejected, compare_roots, hist_np, require_gpu, roots_poly_major, to_soa
 
 pytestmark = pytest.mark.gpu
 
@@ -65,6 +65,8 @@ def test_two_lanes_match_one_lane_counters_and_oracle(dev, orc, degree, mode):
     assert (s1 == s2).mean() > 0.995, (np.bincount(s1, minlength=4), np.bincount(s2, minlength=4))
     ok = (s2 == 0) & (ref_st == 0)
     assert ok.mean() > 0.5, np.bincount(s2, minlength=4)
+    check_rejected(co, s1, ref, orc)
+    check_rejected(co, s2, ref, orc)
     compare_roots(r2[ok], ref[ok], co[ok], orc, tol, kcap)
     h_ref, oow = orc.hist(r2, WIN2.tuple(), W, H)
     assert np.array_equal(hist_np(h2), h_ref)
@@ -123,6 +125,7 @@ def test_two_lanes_rayleigh_shift_with_exceptional_shift(dev, orc):
     ref, ref_st, _, _ = orc.solve(co)
     ok = (status == 0) & (ref_st == 0)
     assert ok.mean() > 0.99
+    check_rejected(co, status, ref, orc)
     compare_roots(roots[ok], ref[ok], co[ok], orc, MIXED_TOL, KAPPA_MIXED)
 
 
@@ -166,6 +169,7 @@ def test_uneven_batch_two_lanes_matches_oracle(dev, orc, lanes):
         ref, ref_st, _, _ = orc.solve(rows)
         good = (s[idx] == 0) & (ref_st == 0)
         assert good.mean() > 0.99, (d, good.mean())
+        check_rejected(rows, s[idx], ref, orc)
         compare_roots(rg[good], ref[good], rows[good], orc, MIXED_TOL, KAPPA_MIXED)
     st = api.stats_dict(stats)
     assert st["polys"] == n and st["status_ok"] == int((s == 0).sum())

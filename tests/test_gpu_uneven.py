@@ -7,7 +7,7 @@ import pytest
 import torch
 
 from paper_2507_02164_gb300 import api, workloads as WL
-from tests.gpu_common import compare_roots, hist_np, require_gpu
+from tests.gpu_common import check_rejected, compare_roots, hist_np, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -38,6 +38,7 @@ def _check_against_oracle(orc, packed, deg, off, roots, status, tol, kcap, max_r
     for d, (idx, rows) in _split(packed, deg, off).items():
         r_gpu = np.stack([roots[off[i] - i: off[i] - i + d] for i in idx])
         ref, ref_st, _, _ = orc.solve(rows)
+        check_rejected(rows, status[idx], ref, orc)
         good = ok[idx] & (ref_st == 0)
         assert good.mean() > 0.99, (d, good.mean())
         compare_roots(r_gpu[good], ref[good], rows[good], orc, tol, kcap)
@@ -162,6 +163,7 @@ def test_full_size_batch_sampled(dev, orc):
         rows = np.stack([pk[off_h[i]:off_h[i + 1]] for i in idx])
         r_gpu = np.stack([r[off_h[i] - i: off_h[i] - i + d] for i in idx])
         ref, ref_st, _, _ = orc.solve(rows)
+        check_rejected(rows, s[idx], ref, orc)
         good = (s[idx] == 0) & (ref_st == 0)
         compare_roots(r_gpu[good], ref[good], rows[good], orc, 1e-9, 1e3)
 
@@ -182,3 +184,87 @@ def test_uneven_inputs_in_page_locked_host_memory(dev):
         torch.cuda.synchronize()
         out.append((r.cpu(), s.cpu(), hist.cpu()))
     assert all(torch.equal(a, b) for a, b in zip(out[0], out[1]))
+
+
+def _expected_uneven_status(n, n_coeffs, deg, off):
+    """The documented rule of rd_roots_uneven for malformed batches: per
+    polynomial (consistent offsets whose roots fit the n_coeffs - n root
+    array; degree 1..12), then the total of the solvable ones against n_coeffs.
+    Returns (status or -1 for "solved", NaN-root mask, overflow)."""
+    cons = np.array([(off[i] >= i) and (off[i + 1] >= off[i]) and (off[i + 1] <= n_coeffs - (n - 1 - i))
+                     and (off[i + 1] - off[i] == int(deg[i]) + 1) for i in range(n)])
+    solvable = cons & (deg >= 1) & (deg <= 12)
+    overflow = int(((deg.astype(np.int64) + 1) * solvable).sum()) > n_coeffs
+    status = np.where(solvable & ~overflow, -1, 3)
+    nan_roots = cons & (~solvable | overflow)
+    return status, nan_roots, overflow
+
+
+@pytest.mark.parametrize("case", ["overlapping", "repeated", "below_index", "tail_too_long", "random"])
+def test_malformed_offsets_stay_in_bounds(dev, case):
+    """Offsets that are not monotone, or whose ranges overlap, never make the
+    uneven path write outside its workspace or the root array: the workspace
+    and the root array each sit inside a larger buffer filled with a guard
+    pattern, which must come back untouched, and the statuses follow the
+    documented rule."""
+    rng = np.random.default_rng(["overlapping", "repeated", "below_index", "tail_too_long", "random"].index(case))
+    if case == "overlapping":   # polynomials 0, 2, 3 consistent alone, 21 coefficients > 20
+        deg, off, n_coeffs = np.array([6, 6, 6, 6]), np.array([0, 7, 3, 10, 17]), 20
+    elif case == "repeated":    # the same range again and again
+        deg, off, n_coeffs = np.array([6, 6, 6, 6]), np.array([0, 7, 0, 7, 0]), 28
+    elif case == "below_index":  # polynomial 2 starts at 1 < 2: its root 0 would be at -1
+        deg, off, n_coeffs = np.array([0, 0, 6, 3]), np.array([0, 1, 1, 8, 12]), 12
+    elif case == "tail_too_long":  # polynomial 0 fills the array, polynomial 1 has nothing
+        deg, off, n_coeffs = np.array([6, 0]), np.array([0, 7, 7]), 7
+    else:
+        n = 64
+        deg = rng.choice([1, 2, 3, 6, 12], size=n)
+        off = np.zeros(n + 1, np.int64)
+        off[1:] = np.cumsum(deg + 1)
+        n_coeffs = int(off[-1])
+        for _ in range(6):  # move a few ranges onto others
+            i = int(rng.integers(1, n))
+            off[i] = int(rng.integers(0, n_coeffs))
+    deg = deg.astype(np.uint8)
+    off = off.astype(np.int64)
+    n = deg.size
+    want, nan_mask, overflow = _expected_uneven_status(n, n_coeffs, deg, off)
+    assert overflow == (case in ("overlapping",)) or case == "random"
+    coeffs = (rng.standard_normal(n_coeffs) + 1j * rng.standard_normal(n_coeffs)).astype(np.complex64)
+    need = api.uneven_workspace_bytes(n, n_coeffs)
+    guard = 1 << 16
+    ws_buf = torch.full((need + guard,), 0xA5, dtype=torch.uint8, device=dev)
+    n_roots = n_coeffs - n
+    sentinel = complex(7.0, -7.0)
+    roots_buf = torch.full((max(n_roots, 0) + 4096,), sentinel, dtype=torch.complex128, device=dev)
+    status = torch.full((n,), 255, dtype=torch.uint8, device=dev)
+    stats = api.new_stats(dev)
+    hist = api.new_hist(W, H, dev)
+    L = api.N.load()
+    import ctypes
+    p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    c_t, d_t, o_t = (torch.from_numpy(x).to(dev) for x in (coeffs, deg, off))
+    prm = api.params("mixed")
+    win = WIN3.c()
+    rc = L.rd_roots_uneven(p(c_t), api.N.C64, p(d_t), p(o_t), n, n_coeffs, api.N.MIXED, ctypes.byref(prm), None,
+                           ctypes.byref(win), W, H, p(hist), p(roots_buf), p(status), p(stats), p(ws_buf), need,
+                           ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, L.rd_last_error()
+    torch.cuda.synchronize()
+    assert torch.all(ws_buf[need:] == 0xA5), "write past the workspace"
+    r = roots_buf.cpu().numpy()
+    assert np.all(r[max(n_roots, 0):] == sentinel), "write past the root array"
+    s = status.cpu().numpy()
+    assert np.all(s[want == 3] == 3), (s, want)
+    assert np.all(s[want == -1] <= 2), (s, want)
+    solved_slots = set()
+    for i in np.nonzero(want == -1)[0]:
+        solved_slots.update(range(off[i] - i, off[i] - i + int(deg[i])))
+    for i in range(n):
+        slots = list(range(off[i] - i, off[i] - i + int(deg[i])))
+        if nan_mask[i] and not solved_slots.intersection(slots):
+            assert np.all(np.isnan(r[slots])), i  # nothing solved writes there
+        if want[i] == -1:
+            assert np.all(np.isfinite(r[slots])), i
+    st = api.stats_dict(stats)
+    assert st["polys"] == n and st["status_degenerate"] == int((s == 3).sum())

@@ -14,7 +14,7 @@ import pytest
 import torch
 
 from paper_2507_02164_gb300 import api, workloads as WL
-from tests.gpu_common import compare_roots, require_gpu, to_soa
+from tests.gpu_common import check_rejected, compare_roots, require_gpu, to_soa
 
 pytestmark = pytest.mark.gpu
 
@@ -159,6 +159,7 @@ def test_littlewood_subsample_matches_oracle(dev, orc):
     s = status.cpu().numpy()
     ok = (s == 0) & (ref_status == 0)
     assert ok.mean() > 0.999
+    check_rejected(co.astype(np.complex128), s, ref, orc)
     r = roots.cpu().numpy().T
     compare_roots(r[ok], ref[ok], co[ok].astype(np.complex128), orc, 1e-9, 1e3)
     assert st["polys"] == idx.size and st["wait_timeouts"] == 0
