@@ -61,3 +61,56 @@ def test_newton_move_of_kept_roots():
                                     win, 480, 270)
     assert out["kept_roots"] == 2
     assert 1e-9 <= out["max_newton_move"] <= 4e-9 and out["within_bar"]
+
+
+def test_within_bar_needs_the_kappa_scaled_bound_and_a_small_excluded_share(orc):
+    """within_bar follows the parity tests' bar: the bar on well-conditioned
+    roots, 1e-11 max(1, kappa) on every root, and at most 6 % of the roots
+    left out as ill-conditioned."""
+    co, _ = WL.unit_disk_roots(1, 4000)  # seeded roots in the unit disk: some close pairs
+    ref, ref_st, _, _ = orc.solve(co, tol=1e-13)
+    ok = np.zeros(co.shape[0], np.uint8)
+    s = bench.root_error_summary(ref.copy(), ok, ref, ref_st, co, 1e-9, 1e3)
+    assert s["within_bar"] and s["kappa_scaled_ok"] and s["excluded_fraction"] <= 0.06
+    # an ill-conditioned root (left out of the bar) moved far beyond 1e-11 kappa fails the bound
+    kap = orc.root_condition(co, ref)
+    i, j = np.unravel_index(np.argmax(kap), kap.shape)
+    assert kap[i, j] > 1e3
+    bad = ref.copy()
+    bad[i, j] += 1e-11 * kap[i, j] * 100 * max(1.0, abs(ref[i, j]))
+    s2 = bench.root_error_summary(bad, ok, ref, ref_st, co, 1e-9, 1e3)
+    assert s2["max_rel_err"] <= 1e-9 and not s2["kappa_scaled_ok"] and not s2["within_bar"]
+    # a cap that leaves out more than 6 % of the roots fails too
+    s3 = bench.root_error_summary(ref.copy(), ok, ref, ref_st, co, 1e-9, 1.0)
+    assert s3["excluded_fraction"] > 0.06 and not s3["within_bar"]
+
+
+def test_launch_plan():
+    assert bench.launch_plan(1, {}, "ours") == ("run", 1)
+    assert bench.launch_plan(8, {}, "ours") == ("exec", 8)
+    assert bench.launch_plan(8, {}, "reference") == ("run", 1)
+    assert bench.launch_plan(4, {"WORLD_SIZE": "4"}, "ours") == ("run", 4)
+    kind, msg = bench.launch_plan(8, {"WORLD_SIZE": "1"}, "ours")
+    assert kind == "error" and "WORLD_SIZE" in msg
+    assert bench.launch_plan(0, {}, "ours")[0] == "error"
+    argv = bench.torchrun_argv(4, ["--gpus", "4", "--steps", "2"], 29512)
+    assert argv[1:4] == ["-m", "torch.distributed.run", "--nnodes=1"]
+    assert "--nproc-per-node=4" in argv and "--master-addr=127.0.0.1" in argv and "--master-port=29512" in argv
+    assert argv[-4:] == ["--gpus", "4", "--steps", "2"] and argv[-5].endswith("bench.py")
+
+
+def test_workload_config_labels_the_real_world_size():
+    args = bench.parse_args(["--gpus", "4"])
+    args.log2n = 26
+    assert bench.workload_config(args, 4)["parallelism"] == "dp4"
+    assert bench.workload_config(args, 1)["parallelism"] == "dp1"
+
+
+def test_mismatched_gpus_and_world_size_is_refused():
+    import os
+    import subprocess
+    import sys
+    env = dict(os.environ, WORLD_SIZE="1", RANK="0", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, "bench.py", "--gpus", "2", "--steps", "1"], cwd=bench.ROOT, env=env,
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 2 and "WORLD_SIZE" in r.stderr

@@ -195,7 +195,7 @@ def _expected_uneven_status(n, n_coeffs, deg, off):
                      and (off[i + 1] - off[i] == int(deg[i]) + 1) for i in range(n)])
     solvable = cons & (deg >= 1) & (deg <= 12)
     overflow = int(((deg.astype(np.int64) + 1) * solvable).sum()) > n_coeffs
-    status = np.where(solvable & ~overflow, -1, 3)
+    status = np.where(solvable & (not overflow), -1, 3)
     nan_roots = cons & (~solvable | overflow)
     return status, nan_roots, overflow
 
