@@ -439,7 +439,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     one = tuned["mixed"]["degrees"][str(DEGREE)]["one_role"]
     one_shape = dict(block=one["block"], ctas_per_sm=one["ctas_per_sm"], lanes=one["lanes"], polish_warps=0)
     elapsed_or, kern_or, st_or, clk_or = timed_leg("mixed", **one_shape)
-    elapsed_df, kern_df, st_df, clk_df = timed_leg("mixed", polish_mode=api.N.POLISH_DF, **one_shape)
+    # the FP32-pipe compensated polish (RD_POLISH_DF) in the launch shape the
+    # tuner picks for it (warp-specialised or not)
+    tuned_df = autotune.tune("mixed", degrees=[DEGREE], polish="df")
+    df_e = tuned_df["degrees"][str(DEGREE)]
+    df_shape = dict(block=df_e["block"], ctas_per_sm=df_e["ctas_per_sm"], lanes=df_e["lanes"],
+                    polish_warps=df_e.get("polish_warps", 0), polish_mode=api.N.POLISH_DF)
+    elapsed_df, kern_df, st_df, clk_df = timed_leg("mixed", **df_shape)
 
     plain = None
     if not args.no_plain:
@@ -463,6 +469,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         for mode in tuned:
             r, stt = api.roots_batched(sub, mode=mode, params_=autotune.degree_params(tuned[mode], DEGREE, mode))
             sub_roots[mode] = (r.cpu().numpy().T, stt.cpu().numpy())
+        r, stt = api.roots_batched(sub, mode="mixed", params_=autotune.degree_params(tuned_df, DEGREE, "mixed", "df"))
+        sub_roots["mixed_df"] = (r.cpu().numpy().T, stt.cpu().numpy())
 
     # one exchange step: sum the per-rank images (after the timed region)
     reduce_ms = None
@@ -525,8 +533,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     line["mixed_df_polish"] = {
         "value": polys_total / (elapsed_df * 1e-3), "unit": UNIT, "ms_per_step": elapsed_df / args.steps,
         "kernel_ms": kern_df, "fp32_frac": g32 / p32 / t_df, "fp64_frac": g64 / p64 / t_df,
+        "frac": g32 / p32 / t_df + g64 / p64 / t_df,
+        "fp32_tflops": g32 / t_df / 1e12, "fp64_tflops": g64 / t_df / 1e12,
+        "shape": {k: v for k, v in df_shape.items() if k != "polish_mode"}, "tuned_ms": df_e["ms"],
         "status": {k: st_df[k] for k in ("status_ok", "status_not_converged", "status_rejected", "status_degenerate")},
-        "note": "Newton steps in double-float arithmetic on the FP32 pipe, FP64 final residual check",
+        "newton_steps_per_poly": st_df["newton_steps"] / max(1, st_df["polys"]),
+        "over_fp64_polish": kern_mx / kern_df,
+        "note": "RD_POLISH_DF: 3 Newton steps on the FP32 pipe (z as a float pair, p(z) by the compensated "
+                "Horner scheme), FP64 final residual check; sweep warps and polish warps as the tuner picked",
         "clocks": clk_df}
     if plain is not None:
         pv = polys_total / (plain["elapsed_ms"] * 1e-3)
@@ -562,6 +576,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             if "plain" in sub_roots:
                 line["root_error"]["plain_fp64"] = root_error_summary(sub_roots["plain"][0], sub_roots["plain"][1],
                                                                       ref_s, ref_st, co_s, 1e-11, 1e2)
+            line["root_error"]["mixed_df_polish"] = root_error_summary(
+                sub_roots["mixed_df"][0], sub_roots["mixed_df"][1], ref_s, ref_st, co_s, 1e-9, 1e3)
     if world == 1 and not args.no_configs:
         line["configs"] = other_configs(args, rank, world, local_rank)
     print(json.dumps(line), flush=True)

@@ -82,24 +82,26 @@ typedef struct {
                               exchanged by warp shuffles; degree >= 2 and RD_POLISH_FP64
                               only, degree 1 always runs one lane). Two lanes measured
                               slower on GB300 at degrees 6..12; the autotuner times both   */
-    int32_t polish_warps;  /* RD_MIXED, RD_POLISH_FP64, one lane, rd_roots_batched and
+    int32_t polish_warps;  /* RD_MIXED (either polish mode), one lane, rd_roots_batched and
                               rd_roots_density: 0 = every warp sweeps and then polishes its
                               own 32 polynomials; P > 0 = warp-specialised CTAs, P warps of
                               each polish, check, store and bin what the other block/32 - P
                               warps sweep, handed over through a shared-memory ring, so the
-                              FP64 pipe (polish) and the FP32 pipe (sweeps) work at the same
-                              time. block may then be up to 512 (degrees <= 6) or 256
+                              polish (FP64 pipe, or FP32 pipe with RD_POLISH_DF) and the
+                              sweeps (FP32 pipe) work at the same time. block may then be up to 512 (degrees <= 6) or 256
                               (degrees >= 7). Same roots bit for bit                       */
     int32_t ring_slots;    /* polish_warps > 0: ring slots of 32 polynomials per CTA (2..64);
                               0 = 2 x block/32                                             */
 } rd_params;
 
 /* RD_POLISH_FP64: every Newton step evaluates p(z) by FP64 Horner.
- * RD_POLISH_DF: the Newton steps evaluate p(z) in double-float arithmetic
- * (pairs of FP32 numbers with error-free products and sums, about 2^-48
- * relative precision) on the FP32 pipe, which GB300 runs 64x faster than its
- * FP64 pipe; the final residual check is still an FP64 Horner evaluation and
- * a root that fails it still gets polish_extra FP64 Newton steps. */
+ * RD_POLISH_DF: the Newton steps run on the FP32 pipe, which GB300 runs
+ * about 70x faster than its FP64 pipe: z is carried as a pair zh + zl of
+ * floats (about 2^-48 relative), p(zh) is evaluated by the compensated
+ * Horner scheme (error-free products and sums, as accurate as Horner in
+ * twice the working precision) and p(z) = p(zh) + p'(zh) zl + p''(zh)/2 zl^2;
+ * the final residual check is still an FP64 Horner evaluation and a root
+ * that fails it still gets polish_extra FP64 Newton steps. */
 typedef enum { RD_POLISH_FP64 = 0, RD_POLISH_DF = 1 } rd_polish;
 
 /* Defaults: plain tol 1e-13, mixed tol 4 * 2^-24, max_iters 40, Wilkinson
@@ -142,8 +144,9 @@ typedef struct {
  * Wilkinson shift and deflation test, in the sweep precision. RD_MIXED adds
  * per Newton step 8d + 2 FP64 (p(z)) and 8d + 3 FP32 (p'(z), step size), and
  * per root 8d + 4 FP64 (final residual, binning) and 2d + 4 FP32 (denominator);
- * with RD_POLISH_DF a Newton step costs 116d + 3 FP32 (double-float Horner:
- * 108 FP32 operations per coefficient) and a root 8d + 6 FP64;
+ * with RD_POLISH_DF a Newton step costs 66d + 50 FP32 (compensated Horner
+ * and its derivative recurrences: 66 FP32 flops per coefficient) and a root
+ * 8d + 6 FP64;
  * RD_PLAIN_FP64 adds 4 FP64 per root (binning). */
 
 /* Optional per-polynomial tile clip of the full pipeline (Sec. II, domain
@@ -438,14 +441,15 @@ int rd_field_density(rd_field f, const rd_field_spec *spec, rd_mode mode, const 
                      uint8_t *status, rd_stats *stats, void *stream);
 
 /* ---- launch-shape autotuner ---------------------------------------------------
- * Times the launch shapes of rd_roots_density for one degree, mode and storage
- * type on a probe batch of n_probe complex-Gaussian polynomials (real and
+ * Times the launch shapes of rd_roots_density for one degree, mode, polish
+ * mode (rd_polish; RD_MIXED only, else ignored) and storage type on a probe batch of n_probe complex-Gaussian polynomials (real and
  * imaginary parts N(0,1), drawn on the device from a fixed seed per degree)
  * binned into a 1920 x 1080 histogram over [-3,3] x [-1.6875,1.6875], and
  * returns the fastest. Candidates: lanes per polynomial (1; 2 from degree 2 on,
  * with the FP64 polish), threads per CTA 32, 64, 128, 256, resident CTAs per
  * SM (the occupancy maximum or fewer), each with every warp sweeping then
- * polishing; and for RD_MIXED the warp-specialised shapes (polish_warps > 0).
+ * polishing; and for RD_MIXED the warp-specialised shapes (polish_warps > 0),
+ * a set for each polish mode. Two lanes are not a candidate with RD_POLISH_DF.
  * Each shape runs once untimed, then `reps` times (1..15) timed with CUDA
  * events; its time is the median. A shape that cannot be launched (too many
  * registers for the block) is recorded with ms < 0 and skipped. This is the
@@ -466,8 +470,8 @@ typedef struct {
     int32_t n_candidates;    /* shapes timed (launchable or not)                           */
     int32_t reserved;
 } rd_tuning;
-int rd_autotune(int degree, rd_mode mode, rd_dtype dtype, int64_t n_probe, int reps, rd_tuning *out,
-                rd_tune_entry *table, int table_cap, int *table_len);
+int rd_autotune(int degree, rd_mode mode, int polish_mode, rd_dtype dtype, int64_t n_probe, int reps,
+                rd_tuning *out, rd_tune_entry *table, int table_cap, int *table_len);
 
 /* ---- ALU throughput probe ------------------------------------------------------
  * Not part of the method: the denominator of its roofline. Enqueues one kernel

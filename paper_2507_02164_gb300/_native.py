@@ -88,7 +88,7 @@ SIGNATURES = {
     "rd_hist_clear": (I32, [P, I64, P]),
     "rd_roots_backward": (I32, [P, I32, I32, I64, P, P, P, P, P]),
     "rd_roots_backward_uneven": (I32, [P, I32, P, P, I64, I64, P, P, P, P, P]),
-    "rd_autotune": (I32, [I32, I32, I32, I64, I32, ctypes.POINTER(Tuning), ctypes.POINTER(TuneEntry), I32,
+    "rd_autotune": (I32, [I32, I32, I32, I32, I64, I32, ctypes.POINTER(Tuning), ctypes.POINTER(TuneEntry), I32,
                           ctypes.POINTER(ctypes.c_int)]),
     "rd_alu_peak": (I32, [I32, I64, I32, P, ctypes.POINTER(ctypes.c_uint64), P]),
     "rd_uneven_workspace_bytes": (SZ, [I64, I64, I32]),

@@ -33,22 +33,28 @@ def _entry(e) -> tuple:
     return (int(e.lanes), int(e.block), int(e.ctas_per_sm), int(e.polish_warps))
 
 
-def tune_degree(degree: int, mode: str = "mixed", dtype=torch.complex64, n: int = 1 << 18, reps: int = 3):
+POLISH = {"fp64": N.POLISH_FP64, "df": N.POLISH_DF}
+
+
+def tune_degree(degree: int, mode: str = "mixed", dtype=torch.complex64, n: int = 1 << 18, reps: int = 3,
+                polish: str = "fp64"):
     """One rd_autotune call: ({(lanes, block, cps, polish_warps): ms}, the best
-    shape, the best shape with polish_warps = 0). ms < 0: not launchable."""
+    shape, the best shape with polish_warps = 0). ms < 0: not launchable.
+    polish: "fp64" or "df" (the mixed mode's polish, rd_polish)."""
     t = N.Tuning()
     table = (N.TuneEntry * TABLE_CAP)()
     used = ctypes.c_int(0)
-    N.call("rd_autotune", degree, api._mode(mode), api.DTYPES[dtype], n, reps, ctypes.byref(t), table, TABLE_CAP,
-           ctypes.byref(used))
+    N.call("rd_autotune", degree, api._mode(mode), POLISH[polish], api.DTYPES[dtype], n, reps, ctypes.byref(t), table,
+           TABLE_CAP, ctypes.byref(used))
     res = {_entry(e): float(e.ms) for e in table[:used.value]}
     return res, (_entry(t.best), float(t.best.ms)), (_entry(t.one_role), float(t.one_role.ms))
 
 
-def cache_key(mode: str, dtype, n: int) -> str:
+def cache_key(mode: str, dtype, n: int, polish: str = "fp64") -> str:
     name = torch.cuda.get_device_name()
     kind = "c64" if dtype == torch.complex64 else "c128"
-    return f"{name}|{mode}|{kind}|n={n}|lib={build.source_hash()}|v{CACHE_FORMAT}"
+    m = f"{mode}-{polish}" if mode == "mixed" else mode
+    return f"{name}|{m}|{kind}|n={n}|lib={build.source_hash()}|v{CACHE_FORMAT}"
 
 
 def load(cache_path: str = DEFAULT_CACHE) -> dict:
@@ -60,20 +66,21 @@ def load(cache_path: str = DEFAULT_CACHE) -> dict:
 
 
 def tune(mode: str = "mixed", dtype=torch.complex64, degrees=range(1, 13), n: int = 1 << 20,
-         cache_path: str | None = DEFAULT_CACHE, force: bool = False) -> dict:
+         cache_path: str | None = DEFAULT_CACHE, force: bool = False, polish: str = "fp64") -> dict:
     """Tune every requested degree; degrees already in the cache (same GPU,
-    mode, storage type, probe size and library sources) are not re-measured.
+    mode and polish, storage type, probe size and library sources) are not
+    re-measured.
     Returns {"degrees": {d: {"lanes", "block", "ctas_per_sm", "polish_warps",
     "ms", "one_role": {"lanes", "block", "ctas_per_sm", "ms"}, "table"}},
     "seconds": time spent measuring, "probe_polys": n}."""
-    key = cache_key(mode, dtype, n)
+    key = cache_key(mode, dtype, n, polish)
     cache = load(cache_path) if cache_path else {}
     entry = cache.get(key, {}) if not force else {}
     t0 = time.perf_counter()
     for d in degrees:
         if str(d) in entry:
             continue
-        res, (best, ms), (one, one_ms) = tune_degree(d, mode, dtype, n)
+        res, (best, ms), (one, one_ms) = tune_degree(d, mode, dtype, n, polish=polish)
         entry[str(d)] = {"lanes": best[0], "block": best[1], "ctas_per_sm": best[2], "polish_warps": best[3],
                          "ms": ms,
                          "one_role": {"lanes": one[0], "block": one[1], "ctas_per_sm": one[2], "ms": one_ms},
@@ -99,8 +106,10 @@ def uneven_tuning(result: dict):
                              lanes={int(d): e["lanes"] for d, e in deg.items()})
 
 
-def degree_params(result: dict, degree: int, mode: str = "mixed"):
-    """rd_params for a uniform batch of `degree` from a tune() result."""
+def degree_params(result: dict, degree: int, mode: str = "mixed", polish: str = "fp64"):
+    """rd_params for a uniform batch of `degree` from a tune() result (made
+    with the same polish)."""
     e = result["degrees"][str(degree)]
+    extra = {"polish_mode": POLISH[polish]} if mode == "mixed" else {}
     return api.params(mode, block=e["block"], ctas_per_sm=e["ctas_per_sm"], lanes=e["lanes"],
-                      polish_warps=e.get("polish_warps", 0))
+                      polish_warps=e.get("polish_warps", 0), **extra)

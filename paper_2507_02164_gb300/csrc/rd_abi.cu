@@ -121,8 +121,8 @@ int check_params(const rd_params &p)
         return rd_set_error(RD_EINVAL, "params.lanes = 2 needs polish_mode RD_POLISH_FP64");
     if (p.fixed_sweeps < 0 || p.fixed_sweeps > p.max_iters)
         return rd_set_error(RD_EINVAL, "params.fixed_sweeps must be in [0, max_iters]");
-    if (p.polish_warps > 0 && (p.polish_mode != RD_POLISH_FP64 || p.lanes == 2))
-        return rd_set_error(RD_EINVAL, "params.polish_warps > 0 needs polish_mode RD_POLISH_FP64 and one lane");
+    if (p.polish_warps > 0 && p.lanes == 2)
+        return rd_set_error(RD_EINVAL, "params.polish_warps > 0 needs one lane per polynomial");
     return RD_OK;
 }
 

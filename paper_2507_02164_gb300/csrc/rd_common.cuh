@@ -250,16 +250,47 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b)
     return fast_two_sum(p, e);
 }
 
-struct dfc {
-    dfl re, im;
-};
-
-// acc * z + a in double-float complex arithmetic (one Horner step)
-__device__ __forceinline__ dfc dfc_fma(dfc acc, dfc z, dfc a)
+// Error-free product: a b = p + e exactly (p = fl(a b), e from one FMA).
+__device__ __forceinline__ dfl two_prod(float a, float b)
 {
-    dfl re = df_add(df_add(df_mul(acc.re, z.re), df_neg(df_mul(acc.im, z.im))), a.re);
-    dfl im = df_add(df_add(df_mul(acc.re, z.im), df_mul(acc.im, z.re)), a.im);
-    return {re, im};
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+// Compensated Horner scheme (Graillat, Langlois, Louvet, "Compensated Horner
+// scheme", 2005; the complex form: Graillat and Menissier-Morain, 2012) at the
+// FP32 point x for coefficients a_k = hi_k + lo_k (lo only when LO). Each
+// Horner step's product acc * x and sum with hi_k are split error-free into
+// a float and its rounding error (four TwoProducts, four TwoSums); the errors
+// run through a second Horner recurrence. On return p + err equals p(x) as
+// if evaluated in twice the working precision, and d1 = p'(x), d2 = p''(x)/2
+// in FP32 (plain Horner on the FP32 iterates).
+template <int N, bool LO>
+__device__ __forceinline__ void comp_horner(const cx<float> (&hi)[N + 1], const cx<float> (&lo)[LO ? N + 1 : 1],
+                                            cx<float> x, cx<float> &p, cx<float> &err, cx<float> &d1,
+                                            cx<float> &d2)
+{
+    p = hi[N];
+    err = LO ? lo[LO ? N : 0] : cx<float>{0.0f, 0.0f};
+    d1 = {0.0f, 0.0f};
+    d2 = {0.0f, 0.0f};
+#pragma unroll
+    for (int k = N - 1; k >= 0; --k) {
+        d2 = cfma(d2, x, d1);
+        d1 = cfma(d1, x, p);
+        const dfl t1 = two_prod(p.re, x.re), t2 = two_prod(p.im, x.im);
+        const dfl t3 = two_prod(p.re, x.im), t4 = two_prod(p.im, x.re);
+        const dfl s1 = two_sum(t1.hi, -t2.hi), s2 = two_sum(t3.hi, t4.hi);
+        const dfl u1 = two_sum(s1.hi, hi[k].re), u2 = two_sum(s2.hi, hi[k].im);
+        p = {u1.hi, u2.hi};
+        float er = __fadd_rn(__fadd_rn(__fsub_rn(t1.lo, t2.lo), s1.lo), u1.lo);
+        float ei = __fadd_rn(__fadd_rn(__fadd_rn(t3.lo, t4.lo), s2.lo), u2.lo);
+        if constexpr (LO) {
+            er = __fadd_rn(er, lo[k].re);
+            ei = __fadd_rn(ei, lo[k].im);
+        }
+        err = cfma(err, x, cx<float>{er, ei});
+    }
 }
 
 // Split d * 2^-shift into hi + lo floats (|d * 2^-shift| <= 2): hi = d's

@@ -419,19 +419,15 @@ __device__ __forceinline__ void finish_lane(const SolveArgs &A, const void *coef
                     af[N] = {1.0f, 0.0f};
                 }
                 // residual_tol <= 0: the default 64 d 2^-53 for this degree
-                // double-float coefficients for MODE_MIXED_DF: hi = the FP32 rounding,
-                // lo = the FP32 rounding of the remainder (zero for complex64 input)
-                dfc adf[MODE == MODE_MIXED_DF ? N + 1 : 1];
-                if constexpr (MODE == MODE_MIXED_DF) {
+                // MODE_MIXED_DF with complex128 input: the FP32 rounding of each
+                // coefficient's remainder (a_k = af_k + alo_k to about 2^-48);
+                // complex64 coefficients are exact in FP32 and have none
+                constexpr bool LO = MODE == MODE_MIXED_DF && !std::is_same<In, float2>::value;
+                cx<float> alo[LO ? N + 1 : 1];
+                if constexpr (LO) {
 #pragma unroll
-                    for (int k = 0; k <= N; ++k) {
-                        if constexpr (std::is_same<In, float2>::value) {
-                            adf[k] = {{af[k].re, 0.0f}, {af[k].im, 0.0f}};
-                        } else {
-                            adf[k] = {{af[k].re, d2f(ad[k].re - f2d(af[k].re))},
-                                      {af[k].im, d2f(ad[k].im - f2d(af[k].im))}};
-                        }
-                    }
+                    for (int k = 0; k <= N; ++k)
+                        alo[k] = {d2f(ad[k].re - f2d(af[k].re)), d2f(ad[k].im - f2d(af[k].im))};
                 }
                 const float rtol = A.residual_tol > 0 ? (float)A.residual_tol : (float)(64.0 * N * 0x1p-53);
                 // residual test |p(z)| <= residual_tol * sum_k |a_k|_1 |z|^k (1-norms
@@ -451,30 +447,30 @@ __device__ __forceinline__ void finish_lane(const SolveArgs &A, const void *coef
                     for (int k = 0; k + 1 < N; ++k) zq[k] = zq[k + 1];
                     cx<double> zj;
                     if constexpr (MODE == MODE_MIXED_DF) {
-                        // Newton steps with p(z) in double-float arithmetic on the FP32
-                        // pipe (coefficients split into hi + lo floats), z kept as a
-                        // double-float pair; p'(z) and the step size in FP32
-                        dfc zd = {{zf.re, 0.0f}, {zf.im, 0.0f}};
+                        // Newton steps on the FP32 pipe: z kept as a pair zh + zl of
+                        // floats; p(z) = p(zh) + p'(zh) zl + p''(zh)/2 zl^2 (the next
+                        // term is below 2^-72), p(zh) by the compensated Horner scheme
+                        // (twice the working precision), the derivative terms and
+                        // the step size in FP32
+                        cx<float> zl = {0.0f, 0.0f};
                         for (int step = 0; step < A.polish_steps; ++step) {
-                            dfc p = adf[N];
-#pragma unroll
-                            for (int k = N - 1; k >= 0; --k) p = dfc_fma(p, zd, adf[k]);
-                            cx<float> pf = af[N], dp = {0.0f, 0.0f};
-#pragma unroll
-                            for (int k = N - 1; k >= 0; --k) {
-                                dp = cfma(dp, zf, pf);
-                                pf = cfma(pf, zf, af[k]);
-                            }
-                            cx<float> r = {__fadd_rn(p.re.hi, p.re.lo), __fadd_rn(p.im.hi, p.im.lo)};
-                            cx<float> dz = cdiv(r, dp);
+                            cx<float> p, err, d1, d2;
+                            comp_horner<N, LO>(af, alo, zf, p, err, d1, d2);
+                            const cx<float> corr = mul(cfma(d2, zl, d1), zl);
+                            const cx<float> r = {__fadd_rn(p.re, __fadd_rn(err.re, corr.re)),
+                                                 __fadd_rn(p.im, __fadd_rn(err.im, corr.im))};
+                            const cx<float> dz = cdiv(r, d1);
                             if (!finite_c(dz)) break;
-                            zd.re = df_add(zd.re, dfl{-dz.re, 0.0f});
-                            zd.im = df_add(zd.im, dfl{-dz.im, 0.0f});
-                            zf = {zd.re.hi, zd.im.hi};
+                            // z <- z - dz: TwoSum on the high parts, then renormalise
+                            const dfl sr = two_sum(zf.re, -dz.re), si = two_sum(zf.im, -dz.im);
+                            const dfl nr = fast_two_sum(sr.hi, __fadd_rn(sr.lo, zl.re));
+                            const dfl ni = fast_two_sum(si.hi, __fadd_rn(si.lo, zl.im));
+                            zf = {nr.hi, ni.hi};
+                            zl = {nr.lo, ni.lo};
                             newton += 1;
                         }
-                        // the pair hi + lo is exact in FP64
-                        zj = {f2d(zd.re.hi) + f2d(zd.re.lo), f2d(zd.im.hi) + f2d(zd.im.lo)};
+                        // zh + zl rounded once to FP64
+                        zj = {f2d(zf.re) + f2d(zl.re), f2d(zf.im) + f2d(zl.im)};
                     } else {
                         zj = f2d(zf);
                         // Newton steps: p(z) by FP64 Horner on the original coefficients,
@@ -568,11 +564,13 @@ __device__ __forceinline__ void finish_lane(const SolveArgs &A, const void *coef
             S.add(ST_NEWTON, degenerate ? 0u : newton);
             const unsigned nw = degenerate ? 0u : newton, nr = (degenerate || !polish) ? 0u : (unsigned)N;
             if constexpr (MODE == MODE_MIXED_DF) {
-                // double-float Horner: per coefficient 4 products (7 FP32 ops) and
-                // 4 sums (20) = 108 FP32 ops; FP64 only for the hi + lo assembly,
-                // the final residual and the binning
+                // compensated Horner per coefficient: 4 TwoProducts (3 flops each),
+                // 4 TwoSums (6), 3 error sums, the error recurrence (8) and the
+                // derivative recurrences (16) = 66 FP32 flops; per step 50 more
+                // (Taylor correction, step size, double-float update). FP64 only for
+                // the zh + zl assembly, the final residual and the binning
                 S.add(ST_F64, (8u * N + 6u) * nr);
-                S.add(ST_F32, (116u * N + 3u) * nw + (2u * N + 4u) * nr);
+                S.add(ST_F32, (66u * N + 50u) * nw + (2u * N + 4u) * nr);
             } else {
                 S.add(ST_F64, (8u * N + 2u) * nw + (8u * N + 4u) * nr);
                 S.add(ST_F32, (8u * N + 3u) * nw + (2u * N + 4u) * nr);

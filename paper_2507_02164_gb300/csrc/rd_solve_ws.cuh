@@ -114,10 +114,10 @@ __device__ __forceinline__ void ws_publish(volatile unsigned *state, unsigned va
 // CTA (at most MAXB = ws_max_block(N) threads), the first polish_warps of them
 // (1 .. blockDim.x / 32 - 1) polishing; `slots` (2 .. WS_MAX_SLOTS) ring
 // slots in the dynamic shared memory (ws_smem_bytes(N, slots)).
-template <int N, typename In, int MAXB>
+template <int N, typename In, int MAXB, int MODE>
 __global__ void __launch_bounds__(MAXB, 1) solve_ws_kernel(SolveArgs A, int polish_warps, int slots)
 {
-    constexpr int MODE = MODE_MIXED_FP64;
+    static_assert(MODE == MODE_MIXED_FP64 || MODE == MODE_MIXED_DF, "the warp-specialised solver is mixed-mode");
     extern __shared__ __align__(16) unsigned char ws_smem[];
     WsCtl *ctl = reinterpret_cast<WsCtl *>(ws_smem);
     WsSlot<N> *ring = reinterpret_cast<WsSlot<N> *>(ws_smem + sizeof(WsCtl));

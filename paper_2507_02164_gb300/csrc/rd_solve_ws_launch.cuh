@@ -12,7 +12,7 @@ namespace rd {
 // per device; it is raised once per device to the largest size asked for
 // (host calls, outside any stream order), so a graph capture that follows
 // the first launch on a device makes none.
-template <int N, typename In, int MAXB>
+template <int N, typename In, int MAXB, int MODE>
 static int ws_allow_smem(size_t bytes)
 {
     static std::atomic<size_t> allowed[64];
@@ -20,7 +20,7 @@ static int ws_allow_smem(size_t bytes)
     if (cudaGetDevice(&dev) != cudaSuccess) return rd_check_launch("cudaGetDevice");
     if (dev < 0 || dev >= 64) return rd_set_error(RD_EUNSUPPORTED, "device %d: at most 64 devices", dev);
     if (bytes <= 48 * 1024 || bytes <= allowed[dev].load()) return RD_OK;
-    if (cudaFuncSetAttribute(solve_ws_kernel<N, In, MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+    if (cudaFuncSetAttribute(solve_ws_kernel<N, In, MAXB, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
         cudaSuccess)
         return rd_check_launch("cudaFuncSetAttribute(solve_ws_kernel)");
     size_t cur = allowed[dev].load();
@@ -29,13 +29,13 @@ static int ws_allow_smem(size_t bytes)
     return RD_OK;
 }
 
-template <int N, typename In, int MAXB>
+template <int N, typename In, int MAXB, int MODE>
 static int launch_ws_build(const SolveArgs &a, int block, int ctas_per_sm, int polish_warps, int slots, cudaStream_t st)
 {
     const size_t smem = ws_smem_bytes(N, slots);
-    int rc = ws_allow_smem<N, In, MAXB>(smem);
+    int rc = ws_allow_smem<N, In, MAXB, MODE>(smem);
     if (rc) return rc;
-    auto kern = solve_ws_kernel<N, In, MAXB>;
+    auto kern = solve_ws_kernel<N, In, MAXB, MODE>;
     int per_sm = ctas_per_sm;
     if (per_sm <= 0) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem) != cudaSuccess || per_sm < 1)
@@ -52,7 +52,7 @@ static int launch_ws_build(const SolveArgs &a, int block, int ctas_per_sm, int p
 // Validate the shape and launch.
 // no_sweep_warps: the self-test of the bounded waits (every warp polishes, so
 // no slot is ever filled); otherwise 1 <= polish_warps < block / 32.
-template <int N, typename In>
+template <int N, typename In, int MODE>
 static int launch_ws_n(const SolveArgs &a, int block, int ctas_per_sm, int polish_warps, int slots, cudaStream_t st,
                        bool no_sweep_warps = false)
 {
@@ -68,25 +68,25 @@ static int launch_ws_n(const SolveArgs &a, int block, int ctas_per_sm, int polis
     if (slots <= 0) slots = 2 * warps < WS_MAX_SLOTS ? 2 * warps : WS_MAX_SLOTS;
     if (slots < 2 || slots > WS_MAX_SLOTS)
         return rd_set_error(RD_EINVAL, "params.ring_slots must be 0 or in [2, %d]", WS_MAX_SLOTS);
-    return launch_ws_build<N, In, ws_max_block(N)>(a, block, ctas_per_sm, polish_warps, slots, st);
+    return launch_ws_build<N, In, ws_max_block(N), MODE>(a, block, ctas_per_sm, polish_warps, slots, st);
 }
 
-template <typename In>
+template <typename In, int MODE>
 static int launch_ws_degree(int degree, const SolveArgs &a, int block, int cps, int pw, int slots, cudaStream_t st)
 {
     switch (degree) {
-    case 1: return launch_ws_n<1, In>(a, block, cps, pw, slots, st);
-    case 2: return launch_ws_n<2, In>(a, block, cps, pw, slots, st);
-    case 3: return launch_ws_n<3, In>(a, block, cps, pw, slots, st);
-    case 4: return launch_ws_n<4, In>(a, block, cps, pw, slots, st);
-    case 5: return launch_ws_n<5, In>(a, block, cps, pw, slots, st);
-    case 6: return launch_ws_n<6, In>(a, block, cps, pw, slots, st);
-    case 7: return launch_ws_n<7, In>(a, block, cps, pw, slots, st);
-    case 8: return launch_ws_n<8, In>(a, block, cps, pw, slots, st);
-    case 9: return launch_ws_n<9, In>(a, block, cps, pw, slots, st);
-    case 10: return launch_ws_n<10, In>(a, block, cps, pw, slots, st);
-    case 11: return launch_ws_n<11, In>(a, block, cps, pw, slots, st);
-    case 12: return launch_ws_n<12, In>(a, block, cps, pw, slots, st);
+    case 1: return launch_ws_n<1, In, MODE>(a, block, cps, pw, slots, st);
+    case 2: return launch_ws_n<2, In, MODE>(a, block, cps, pw, slots, st);
+    case 3: return launch_ws_n<3, In, MODE>(a, block, cps, pw, slots, st);
+    case 4: return launch_ws_n<4, In, MODE>(a, block, cps, pw, slots, st);
+    case 5: return launch_ws_n<5, In, MODE>(a, block, cps, pw, slots, st);
+    case 6: return launch_ws_n<6, In, MODE>(a, block, cps, pw, slots, st);
+    case 7: return launch_ws_n<7, In, MODE>(a, block, cps, pw, slots, st);
+    case 8: return launch_ws_n<8, In, MODE>(a, block, cps, pw, slots, st);
+    case 9: return launch_ws_n<9, In, MODE>(a, block, cps, pw, slots, st);
+    case 10: return launch_ws_n<10, In, MODE>(a, block, cps, pw, slots, st);
+    case 11: return launch_ws_n<11, In, MODE>(a, block, cps, pw, slots, st);
+    case 12: return launch_ws_n<12, In, MODE>(a, block, cps, pw, slots, st);
     default: return rd_set_error(RD_EUNSUPPORTED, "degree %d not built (1..12)", degree);
     }
 }

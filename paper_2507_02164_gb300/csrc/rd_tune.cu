@@ -90,24 +90,41 @@ struct Shape {
 // warp-specialised shapes: up to 16 warps per CTA at degrees <= 6 (about 128
 // registers), up to 8 above (255). A polish warp keeps about one FP64
 // instruction in flight, so the FP64 pipe wants about ten polish warps per SM.
-std::vector<Shape> candidates(int degree, rd_mode mode)
+std::vector<Shape> candidates(int degree, rd_mode mode, int polish_mode)
 {
     std::vector<Shape> v;
     const int blocks[4] = {32, 64, 128, 256};
-    for (int lanes = 1; lanes <= (degree >= 2 ? 2 : 1); ++lanes)
+    // two lanes per polynomial only with the FP64 polish (or no polish: plain)
+    const int max_lanes = (degree >= 2 && (mode == RD_PLAIN_FP64 || polish_mode == RD_POLISH_FP64)) ? 2 : 1;
+    for (int lanes = 1; lanes <= max_lanes; ++lanes)
         for (int b : blocks) {
             const int cps_big[3] = {0, 1, 2}, cps_small[3] = {0, 2, 4};
             const int *cps = b >= 128 ? cps_big : cps_small;
             for (int k = 0; k < 3; ++k) v.push_back({lanes, b, cps[k], 0});
         }
     if (mode == RD_MIXED) {
+        // the FP64 polish wants about ten polish warps (one FP64 instruction in
+        // flight per warp); the compensated polish is FP32 work of about the
+        // sweeps' size and wants an even split
         static const int ws_small[][2] = {{512, 8}, {512, 9}, {512, 10}, {512, 11}, {256, 4}, {256, 5}, {192, 3}, {192, 4}};
         static const int ws_large[][2] = {{96, 1}, {96, 2}, {128, 1}, {128, 2}, {192, 2}, {192, 3}, {192, 4},
                                           {256, 3}, {256, 4}};
-        if (degree <= 6)
-            for (auto &s : ws_small) v.push_back({1, s[0], 0, s[1]});
-        else
-            for (auto &s : ws_large) v.push_back({1, s[0], 0, s[1]});
+        static const int df_small[][2] = {{512, 6}, {512, 7}, {512, 8}, {512, 9}, {512, 10}, {384, 5}, {384, 6},
+                                          {384, 7}, {256, 3}, {256, 4}, {256, 5}};
+        static const int df_large[][2] = {{128, 1}, {128, 2}, {192, 2}, {192, 3}, {256, 2}, {256, 3}, {256, 4},
+                                          {256, 5}};
+        const bool df = polish_mode == RD_POLISH_DF;
+        if (degree <= 6) {
+            if (df)
+                for (auto &s : df_small) v.push_back({1, s[0], 0, s[1]});
+            else
+                for (auto &s : ws_small) v.push_back({1, s[0], 0, s[1]});
+        } else {
+            if (df)
+                for (auto &s : df_large) v.push_back({1, s[0], 0, s[1]});
+            else
+                for (auto &s : ws_large) v.push_back({1, s[0], 0, s[1]});
+        }
     }
     return v;
 }
@@ -134,11 +151,13 @@ int cuda_fail(const char *what, cudaError_t e)
 
 }  // namespace
 
-extern "C" int rd_autotune(int degree, rd_mode mode, rd_dtype dtype, int64_t n_probe, int reps, rd_tuning *out,
-                           rd_tune_entry *table, int table_cap, int *table_len)
+extern "C" int rd_autotune(int degree, rd_mode mode, int polish_mode, rd_dtype dtype, int64_t n_probe, int reps,
+                           rd_tuning *out, rd_tune_entry *table, int table_cap, int *table_len)
 {
     if (degree < 1 || degree > 12) return rd_set_error(RD_EUNSUPPORTED, "degree %d outside 1..12", degree);
     if (mode != RD_PLAIN_FP64 && mode != RD_MIXED) return rd_set_error(RD_EINVAL, "mode must be RD_PLAIN_FP64 or RD_MIXED");
+    if (polish_mode != RD_POLISH_FP64 && polish_mode != RD_POLISH_DF)
+        return rd_set_error(RD_EINVAL, "polish_mode must be RD_POLISH_FP64 or RD_POLISH_DF");
     if (dtype != RD_C64 && dtype != RD_C128) return rd_set_error(RD_EINVAL, "dtype must be RD_C64 or RD_C128");
     if (n_probe < 1024 || n_probe > ((int64_t)1 << 24)) return rd_set_error(RD_EINVAL, "n_probe must be in [1024, 2^24]");
     if (reps < 1 || reps > 15) return rd_set_error(RD_EINVAL, "reps must be in 1..15");
@@ -167,12 +186,13 @@ extern "C" int rd_autotune(int degree, rd_mode mode, rd_dtype dtype, int64_t n_p
     if (rc) return rc;
     if ((rc = rd_hist_clear(S.hist, (int64_t)W * H, S.st))) return rc;
 
-    const std::vector<Shape> cand = candidates(degree, mode);
+    const std::vector<Shape> cand = candidates(degree, mode, polish_mode);
     rd_tune_entry best = {0, 0, 0, 0, -1.0f}, one = {0, 0, 0, 0, -1.0f};
     int stored = 0;
     for (const Shape &sh : cand) {
         rd_params p;
         rd_default_params(mode, &p);
+        if (mode == RD_MIXED) p.polish_mode = polish_mode;
         p.lanes = sh.lanes;
         p.block = sh.block;
         p.ctas_per_sm = sh.cps;

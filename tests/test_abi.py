@@ -168,11 +168,13 @@ def test_argument_validation_without_gpu():
     assert L.rd_roots_backward_uneven(null, N.C128, null, null, 0, 0, null, null, null, null, null) == 0
     # autotuner and ALU probe: argument checks come before any device work
     t = N.Tuning()
-    assert _err(L.rd_autotune(13, N.MIXED, N.C64, 1 << 16, 3, ctypes.byref(t), None, 0, None))[0] == \
+    F = N.POLISH_FP64
+    assert _err(L.rd_autotune(13, N.MIXED, F, N.C64, 1 << 16, 3, ctypes.byref(t), None, 0, None))[0] == \
         N.RD_EUNSUPPORTED
-    assert _err(L.rd_autotune(6, N.MIXED, N.C64, 100, 3, ctypes.byref(t), None, 0, None))[0] == N.RD_EINVAL
-    assert _err(L.rd_autotune(6, N.MIXED, N.C64, 1 << 16, 0, ctypes.byref(t), None, 0, None))[0] == N.RD_EINVAL
-    assert _err(L.rd_autotune(6, N.MIXED, N.C64, 1 << 16, 3, None, None, 0, None))[0] == N.RD_EINVAL
+    assert _err(L.rd_autotune(6, N.MIXED, F, N.C64, 100, 3, ctypes.byref(t), None, 0, None))[0] == N.RD_EINVAL
+    assert _err(L.rd_autotune(6, N.MIXED, F, N.C64, 1 << 16, 0, ctypes.byref(t), None, 0, None))[0] == N.RD_EINVAL
+    assert _err(L.rd_autotune(6, N.MIXED, F, N.C64, 1 << 16, 3, None, None, 0, None))[0] == N.RD_EINVAL
+    assert _err(L.rd_autotune(6, N.MIXED, 5, N.C64, 1 << 16, 3, ctypes.byref(t), None, 0, None))[0] == N.RD_EINVAL
     fl = ctypes.c_uint64()
     assert _err(L.rd_alu_peak(2, 10, 4, h64, ctypes.byref(fl), null))[0] == N.RD_EINVAL
     assert _err(L.rd_alu_peak(0, 0, 4, h64, ctypes.byref(fl), null))[0] == N.RD_EINVAL
@@ -214,7 +216,6 @@ def test_warp_specialised_argument_validation_without_gpu():
                      (dict(polish_warps=2, ring_slots=1), "ring_slots"),
                      (dict(polish_warps=2, ring_slots=65), "ring_slots"),
                      (dict(polish_warps=2, block=544), "block"), (dict(block=512), "block"),
-                     (dict(polish_warps=2, polish_mode=N.POLISH_DF), "polish_warps"),
                      (dict(polish_warps=2, lanes=2), "polish_warps"),
                      (dict(polish_warps=4, block=128), "polish_warps"),  # no sweep warp left
                      (dict(polish_warps=1, block=512), "block")]:  # degree 8: at most 256 threads

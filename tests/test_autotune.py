@@ -46,15 +46,16 @@ def test_c_autotuner_times_every_candidate_and_picks_the_fastest():
     from tests.gpu_common import require_gpu
     require_gpu()
     L = N.load()
-    for degree, mode in ((6, N.MIXED), (9, N.MIXED), (6, N.PLAIN_FP64)):
+    for degree, mode, polish in ((6, N.MIXED, N.POLISH_FP64), (9, N.MIXED, N.POLISH_FP64), (6, N.PLAIN_FP64, 0),
+                                 (6, N.MIXED, N.POLISH_DF)):
         t = N.Tuning()
         tab = (N.TuneEntry * 64)()
         used = ctypes.c_int(0)
-        rc = L.rd_autotune(degree, mode, N.C64 if mode == N.MIXED else N.C128, 1 << 14, 3, ctypes.byref(t), tab, 64,
-                           ctypes.byref(used))
+        rc = L.rd_autotune(degree, mode, polish, N.C64 if mode == N.MIXED else N.C128, 1 << 14, 3, ctypes.byref(t),
+                           tab, 64, ctypes.byref(used))
         assert rc == 0, L.rd_last_error()
         rows = list(tab[:used.value])
-        assert used.value == t.n_candidates >= 24
+        assert used.value == t.n_candidates >= 12
         ok = [r for r in rows if r.ms >= 0]
         assert ok and all(r.ms > 0 for r in ok)
         fastest = min(r.ms for r in ok)
@@ -65,12 +66,13 @@ def test_c_autotuner_times_every_candidate_and_picks_the_fastest():
         for r in ws:
             assert r.lanes == 1 and r.block % 32 == 0 and 1 <= r.polish_warps < r.block // 32
             assert r.block <= (512 if degree <= 6 else 256)
-        assert {r.lanes for r in rows} == {1, 2}
+        assert {r.lanes for r in rows} == ({1} if polish == N.POLISH_DF else {1, 2})
     # a table smaller than the candidate list keeps the first entries
     t = N.Tuning()
     tab = (N.TuneEntry * 4)()
     used = ctypes.c_int(0)
-    assert L.rd_autotune(3, N.MIXED, N.C64, 1 << 12, 1, ctypes.byref(t), tab, 4, ctypes.byref(used)) == 0
+    assert L.rd_autotune(3, N.MIXED, N.POLISH_FP64, N.C64, 1 << 12, 1, ctypes.byref(t), tab, 4,
+                         ctypes.byref(used)) == 0
     assert used.value == 4 and t.n_candidates > 4
 
 

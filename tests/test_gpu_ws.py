@@ -77,6 +77,35 @@ def test_every_degree_bit_identical(dev, degree, dtype):
         _same(_run(co, degree, WIN3, block=block, polish_warps=pw, ring_slots=slots), ref)
 
 
+@pytest.mark.parametrize("degree", [2, 6, 9, 12])
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+def test_compensated_polish_bit_identical_to_one_role_kernel(dev, degree, dtype):
+    """The FP32-pipe compensated polish (RD_POLISH_DF) in the warp-specialised
+    form: the same bits as its one-role form, for both storage types."""
+    n = 4000 + 13 * degree
+    co = to_soa(WL.gaussian(300 + degree, n, degree), dev, dtype)
+    ref = _run(co, degree, WIN3, polish_mode="df")
+    shapes = [(512, 6, 0), (256, 3, 4), (64, 1, 2)] if degree <= 6 else [(256, 3, 0), (128, 1, 2)]
+    for block, pw, slots in shapes:
+        _same(_run(co, degree, WIN3, polish_mode="df", block=block, polish_warps=pw, ring_slots=slots), ref)
+
+
+def test_compensated_polish_littlewood_subsample_matches_oracle(dev, orc):
+    """2^14 polynomials i = 4096 k of the 2^26 Littlewood batch through the
+    warp-specialised compensated polish against the FP64 oracle at 1e-9."""
+    idx = np.arange(1 << 14, dtype=np.uint64) * np.uint64(4096)
+    co = WL.littlewood(2, idx)
+    roots, status, _, st = _run(to_soa(co, dev, torch.complex64), 6, WIN2, block=512, polish_warps=6,
+                                polish_mode="df")
+    ref, ref_status, _, _ = orc.solve(co.astype(np.complex128), tol=1e-13)
+    s = status.cpu().numpy()
+    ok = (s == 0) & (ref_status == 0)
+    assert ok.mean() > 0.999
+    check_rejected(co.astype(np.complex128), s, ref, orc)
+    compare_roots(roots.cpu().numpy().T[ok], ref[ok], co[ok].astype(np.complex128), orc, 1e-9, 1e3)
+    assert st["wait_timeouts"] == 0
+
+
 @pytest.mark.parametrize("ctas_per_sm", [1, 2])
 def test_grid_smaller_than_the_sm_count_and_explicit_ctas(dev, ctas_per_sm):
     """ctas_per_sm fixed, and batches with fewer tasks than CTAs."""
