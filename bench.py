@@ -173,7 +173,7 @@ def measured_alu_peaks(torch, dev, local_rank: int):
     stream = torch.cuda.current_stream()
     res = {}
     with ClockSampler(local_rank) as clk:
-        for kind, iters in (("fp32", 100000), ("fp64", 1500)):
+        for kind, iters in (("fp32", 50000), ("fp64", 1500)):
             api.alu_peak(kind, iters // 10, sink=sink)  # warm-up
             rates = []
             for _ in range(5):
@@ -194,8 +194,9 @@ def measured_alu_peaks(torch, dev, local_rank: int):
         "derived_fp64_tflops": sms * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12,
         "flops_per_launch": {"fp32": res["fp32"][2], "fp64": res["fp64"][2]},
         "clocks": c,
-        "how": "rd_alu_peak: 4 CTAs x 256 threads per SM, 8 independent FMA chains per thread, best of 5 "
-               "launches of ~50 ms (CUDA events); derived = SMs x lanes x 2 flop x max SM clock",
+        "how": "rd_alu_peak: 4 CTAs x 256 threads per SM, 8 independent FMA chains per thread (FP32: packed "
+               "fma.rn.f32x2 pairs), best of 5 launches of ~50 ms (CUDA events); derived = SMs x lanes x 2 flop "
+               "x max SM clock",
     }
     return _PEAKS["v"]
 
@@ -601,6 +602,7 @@ def other_configs(args, rank, world, local_rank) -> dict:
     sub = copy.copy(args)
     sub.steps, sub.warmup = min(args.steps, 5), 3
     sub.cpu_seconds, sub.no_e2e = min(args.cpu_seconds, 4.0), True
+    sub.min_timed_s = 0.5  # at least 0.5 s of timed work, so the clock sampler sees it
     t0 = time.perf_counter()
     out = {}
     u = copy.copy(sub)
@@ -1071,8 +1073,12 @@ def run_uneven(args, rank: int, world: int, local_rank: int, emit: bool = True):
 
 def _timed(step, args, dev, world, local_rank):
     """W warm-up steps, then K timed steps between CUDA events on the current
-    stream (barrier + synchronize on both sides); returns (max-over-ranks ms,
-    clock summary)."""
+    stream (barrier + synchronize on both sides); returns (max-over-ranks ms
+    for the K steps, clock summary, K). K is args.steps, raised when
+    args.min_timed_s is set so that the timed region lasts at least that long
+    (the clock sampler reads every 200 ms)."""
+    import math
+
     import torch
 
     from paper_2507_02164_gb300 import dist as D
@@ -1083,15 +1089,24 @@ def _timed(step, args, dev, world, local_rank):
         dist.barrier()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
+    steps = args.steps
+    min_s = getattr(args, "min_timed_s", 0.0) or 0.0
+    if min_s > 0:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        steps = max(steps, math.ceil(min_s * 1e3 / max(e0.elapsed_time(e1), 1e-3)))
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local_rank) as clk:
         t0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             step()
         t1.record(stream)
         torch.cuda.synchronize()
-    return D.max_over_ranks(t0.elapsed_time(t1), device=dev), clk.summary()
+    return D.max_over_ranks(t0.elapsed_time(t1), device=dev), clk.summary(), steps
 
 
 PAPER_METRIC = "deg-6 complex polys rooted+binned/s with the paper's schedule (FP32, T=10 sweeps per root, Rayleigh shift)"
@@ -1119,18 +1134,18 @@ def run_paper(args, rank, world, local_rank):
         api.hist_clear(stats)
         api.roots_density(coeffs, win, hist, mode="mixed", params_=p, stats=stats)
 
-    ms, clk = _timed(step, args, dev, world, local_rank)
+    ms, clk, steps = _timed(step, args, dev, world, local_rank)
     if rank != 0:
         return
     st = api.stats_dict(stats)
-    value = n * world * args.steps / (ms * 1e-3)
+    value = n * world * steps / (ms * 1e-3)
     p32, p64, peak_src = roofline_peaks(torch, dev, local_rank)
     f32, f64 = algorithmic_flops(st)
-    t = ms * 1e-3 / args.steps
+    t = ms * 1e-3 / steps
     qr_per_s = value * st["sweeps"] / max(1, st["polys"])
     print(json.dumps({
-        "metric": PAPER_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "metric": PAPER_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32",
         "data": "synthetic: seeded Littlewood {1,-1,i,-i} degree-6 polynomials (SplitMix64 seed 2), generated on device",
         "config": {"workload": f"littlewood-deg6-2^{args.log2n}, fixed schedule T=10 (Alg. 2), Rayleigh shift, FP32 "
@@ -1139,7 +1154,7 @@ def run_paper(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "kernel": "rd::solve_kernel<6, float, float2, MIXED> (fixed schedule)",
                      "achieved": (f32 + f64 * p32 / p64) / t / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
                      "frac": f32 / p32 / t + f64 / p64 / t, "traffic": None, "peak_source": peak_src},
-        "gpu_launches": 3 * args.steps, "clocks": clk,
+        "gpu_launches": 3 * steps, "clocks": clk,
         "equiv_qr_decompositions_per_s": qr_per_s,
         "paper_context": {"fpga_qr_per_s": 16.5e6, "fpga_polys_per_s": 3.33e5, "rtx3060m_polys_per_s": 2.79e7,
                           "note": "paper's inputs unspecified; other hardware"},
@@ -1270,16 +1285,16 @@ def run_pipeline(args, rank, world, local_rank, emit: bool = True):
         api.field_density(spec, win, hist, mode="mixed", stats=stats)
         e_f[1].record(stream)
 
-    ms_fused, clk_fused = _timed(fused_step, args, dev, world, local_rank)
+    ms_fused, clk_fused, k_fused = _timed(fused_step, args, dev, world, local_rank)
     fused_kernel_ms = e_f[0].elapsed_time(e_f[1])
     st_fused = api.stats_dict(stats)
     frames = render_frames(api, torch, dev, stream)
 
     # the FP64 L2 sums (RD_L2_FP64), for reference
-    ms_fp64, _ = _timed(make_step("fp64"), args, dev, world, local_rank)
+    ms_fp64, _, k_fp64 = _timed(make_step("fp64"), args, dev, world, local_rank)
     l2_fp64_ms = e[0].elapsed_time(e[1])
     # the main leg: double-float L2 sums on the FP32 pipe (RD_L2_DF), same 1e-13 parity bar
-    ms, clk = _timed(make_step("df"), args, dev, world, local_rank)
+    ms, clk, steps = _timed(make_step("df"), args, dev, world, local_rank)
     l2_ms = e[0].elapsed_time(e[1])
     solve_ms = e[1].elapsed_time(e[2])
     if rank != 0:
@@ -1307,8 +1322,8 @@ def run_pipeline(args, rank, world, local_rank, emit: bool = True):
                "sample": f"{done} sub-disks (blocks of 4096 consecutive tiles): f at the nodes, FP64 oracle L2 fit, "
                          f"solve, map, own-tile clip and histogram, ~{args.cpu_seconds:.0f} s"}
     line = {
-        "metric": PIPELINE_METRIC, "value": n * world * args.steps / (ms * 1e-3), "unit": "sub-disks/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "metric": PIPELINE_METRIC, "value": n * world * steps / (ms * 1e-3), "unit": "sub-disks/s",
+        "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": ms / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
         "data": "synthetic: f(z) = sin(z^3) + 0.5 z sampled on the device at the quadrature nodes of every sub-disk",
         "config": {"workload": "480x270 tiles of 1/60 on [-4,4]x[-2.25,2.25], rho = tile half-diagonal, 16x32 polar "
@@ -1328,22 +1343,22 @@ def run_pipeline(args, rank, world, local_rank, emit: bool = True):
                            "frac": f32r / p32 / t_roots + f64r / p64 / t_roots,
                            "fp32_frac": f32r / p32 / t_roots, "fp64_frac": f64r / p64 / t_roots,
                            "peak_source": peak_src},
-        "l2_fp64": {"value": n * world * args.steps / (ms_fp64 * 1e-3), "ms_per_step": ms_fp64 / args.steps,
+        "l2_fp64": {"value": n * world * k_fp64 / (ms_fp64 * 1e-3), "ms_per_step": ms_fp64 / k_fp64,
                     "l2_approx_ms": l2_fp64_ms, "fp64_tflops": l2_flops / (l2_fp64_ms * 1e-3) / 1e12,
                     "fp64_frac": l2_flops / (l2_fp64_ms * 1e-3) / p64},
-        "fused": {"value": n * world * args.steps / (ms_fused * 1e-3), "unit": "sub-disks/s",
-                  "ms_per_step": ms_fused / args.steps, "field_kernel_ms": fused_kernel_ms,
+        "fused": {"value": n * world * k_fused / (ms_fused * 1e-3), "unit": "sub-disks/s",
+                  "ms_per_step": ms_fused / k_fused, "field_kernel_ms": fused_kernel_ms,
                   "samples_per_s": n * 512 / (fused_kernel_ms * 1e-3), "kept_roots": st_fused["binned"],
                   "note": "rd_field_density: f evaluated in FP64 at the 16x32 nodes inside the kernel, L2, roots, "
                           "clip and histogram in one launch; no 1.06 GB sample array",
                   "clocks": clk_fused},
         "frames": frames,
-        "split_end_to_end": {"sampling_ms": sampling_ms, "l2_plus_roots_ms": ms / args.steps,
-                             "value": n / ((sampling_ms + ms / args.steps) * 1e-3),
+        "split_end_to_end": {"sampling_ms": sampling_ms, "l2_plus_roots_ms": ms / steps,
+                             "value": n / ((sampling_ms + ms / steps) * 1e-3),
                              "note": "torch evaluates f at every node into a 1.06 GB array, then the timed step"},
         "kept_roots": st["binned"], "clipped": st["clipped"],
         "status": {k: st[k] for k in ("status_ok", "status_not_converged", "status_rejected", "status_degenerate")},
-        "gpu_launches": 4 * args.steps, "clocks": clk,
+        "gpu_launches": 4 * steps, "clocks": clk,
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
@@ -1512,9 +1527,9 @@ def run_adjoint(args, rank, world, local_rank, emit: bool = True):
             api.roots_backward(coeffs, roots, 2.0 * roots)
             ev[2].record(stream)
 
-        ms, clk = _timed(step, args, dev, world, local_rank)
-        out[name] = {"ms_per_step": ms / args.steps, "forward_ms": ev[0].elapsed_time(ev[1]),
-                     "backward_ms": ev[1].elapsed_time(ev[2]), "value": n * args.steps / (ms * 1e-3),
+        ms, clk, k = _timed(step, args, dev, world, local_rank)
+        out[name] = {"ms_per_step": ms / k, "steps": k, "forward_ms": ev[0].elapsed_time(ev[1]),
+                     "backward_ms": ev[1].elapsed_time(ev[2]), "value": n * world * k / (ms * 1e-3),
                      "clocks": clk}
 
         # the whole differentiation step through autograd: roots, soft-density
@@ -1530,9 +1545,9 @@ def run_adjoint(args, rank, world, local_rank, emit: bool = True):
             L = SP.loss(z, target, precision=precision)
             L.backward()
 
-        ms_l, _ = _timed(loss_step, args, dev, world, local_rank)
-        out[name]["loss_step_ms"] = ms_l / args.steps
-        out[name]["loss_step_value"] = n * args.steps / (ms_l * 1e-3)
+        ms_l, _, k_l = _timed(loss_step, args, dev, world, local_rank)
+        out[name]["loss_step_ms"] = ms_l / k_l
+        out[name]["loss_step_value"] = n * world * k_l / (ms_l * 1e-3)
         out[name]["splat_precision"] = precision
     if rank != 0:
         return None
@@ -1564,7 +1579,8 @@ def run_adjoint(args, rank, world, local_rank, emit: bool = True):
                "sample": f"first {done} polynomials of the same stream: FP64 oracle solve + adjoint of "
                          f"L = sum |z|^2, ~{args.cpu_seconds:.0f} s"}
     line = {
-        "metric": ADJOINT_METRIC, "value": out["c128"]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": ADJOINT_METRIC, "value": out["c128"]["value"], "unit": UNIT, "n_gpus": world,
+        "steps": out["c128"]["steps"],
         "warmup": args.warmup, "ms_per_step": out["c128"]["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 (c128) / f32 (c64)",
         "data": "synthetic: seeded complex-Gaussian degree-6 polynomials (SplitMix64 seed 4)",
@@ -1574,7 +1590,8 @@ def run_adjoint(args, rank, world, local_rank, emit: bool = True):
                    "l2_flush": "none (inputs 112 MB c128, 56 MB c64)", "parallelism": f"dp{world}",
                    "launch_shapes": {k: {x: v[x] for x in ("lanes", "block", "ctas_per_sm", "polish_warps", "ms")}
                                      for k, v in shapes.items()}},
-        "c128": out["c128"], "c64": out["c64"], "gpu_launches": 2 * args.steps, "clocks": out["c128"]["clocks"],
+        "c128": out["c128"], "c64": out["c64"], "gpu_launches": 2 * out["c128"]["steps"],
+        "clocks": out["c128"]["clocks"],
         "roofline": out["c128"]["backward_roofline"],
         "grad_error": {"sample": "4096 polynomials spread over the batch (complex128): GPU adjoint of L = sum |z|^2 "
                                  "at the GPU roots vs the oracle's adjoint at the same roots, relative to each "

@@ -475,10 +475,11 @@ int rd_autotune(int degree, rd_mode mode, int polish_mode, rd_dtype dtype, int64
 
 /* ---- ALU throughput probe ------------------------------------------------------
  * Not part of the method: the denominator of its roofline. Enqueues one kernel
- * of independent fused multiply-add chains, RD_PEAK_FP32 (FFMA on the FP32
- * pipe) or RD_PEAK_FP64 (DFMA on the FP64 pipe): ctas_per_sm x SM count CTAs
- * of 256 threads, each thread `iters` x 128 FMAs (16 steps of 8 independent
- * chains per iteration). *flops (host) receives the
+ * of independent fused multiply-add chains, RD_PEAK_FP32 (packed FP32 pairs,
+ * fma.rn.f32x2, on the FP32 pipe) or RD_PEAK_FP64 (DFMA on the FP64 pipe):
+ * ctas_per_sm x SM count CTAs of 256 threads, each thread `iters` x 16 steps
+ * of 8 independent chains, i.e. iters x 256 FP32 or iters x 128 FP64 FMAs.
+ * *flops (host) receives the
  * flops the launch performs (2 per FMA); the caller times it with events on
  * `stream`. sink: device, 8 bytes, written only if a chain ends on a value it
  * cannot reach (it keeps the chains from being optimised away).

@@ -52,28 +52,63 @@ __global__ void __launch_bounds__(256) probe_kernel(V *out, int64_t count, uint6
 }
 
 // ---- ALU throughput probe ------------------------------------------------------
-// Eight independent FMA chains per thread, 16 steps unrolled per iteration
-// (128 FMAs against two loop instructions). b and c are kernel arguments, so
-// nothing folds; the sink is written only if the sum hits a value the chains
-// never reach, so the chains stay live.
+// Eight independent FMA chains per thread, 16 steps unrolled per iteration.
+// FP64: DFMA, 128 FMAs per iteration. FP32: each chain is a pair of floats
+// stepped by one packed fma.rn.f32x2 (two FMAs per instruction, so the loop
+// and issue overhead cannot hide the FMA pipe's limit), 256 FMAs per
+// iteration. b and c are kernel arguments, so nothing folds; the sink is
+// written only if the sum hits a value the chains never reach, so the chains
+// stay live.
 constexpr int PEAK_STEPS = 16;
 constexpr int PEAK_CHAINS = 8;
 
-template <typename T>
-__global__ void __launch_bounds__(256) alu_peak_kernel(int64_t iters, T b, T c, T never, double *sink)
+__global__ void __launch_bounds__(256) alu_peak_f64_kernel(int iters, double b, double c, double never,
+                                                           double *sink)
 {
-    T a[PEAK_CHAINS];
+    double a[PEAK_CHAINS];
 #pragma unroll
-    for (int k = 0; k < PEAK_CHAINS; ++k) a[k] = (T)(threadIdx.x + k) * (T)1e-3;
-    for (int64_t it = 0; it < iters; ++it) {
+    for (int k = 0; k < PEAK_CHAINS; ++k) a[k] = (double)(threadIdx.x + k) * 1e-3;
+    for (int it = 0; it < iters; ++it) {
 #pragma unroll
         for (int s = 0; s < PEAK_STEPS; ++s)
 #pragma unroll
             for (int k = 0; k < PEAK_CHAINS; ++k) a[k] = fma(a[k], b, c);
     }
-    T sum = T(0);
+    double sum = 0.0;
 #pragma unroll
     for (int k = 0; k < PEAK_CHAINS; ++k) sum += a[k];
+    if (sum == never) *sink = sum;
+}
+
+__device__ __forceinline__ unsigned long long fma_f32x2(unsigned long long a, unsigned long long b,
+                                                        unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long pack_f32x2(float x, float y)
+{
+    return ((unsigned long long)__float_as_uint(y) << 32) | __float_as_uint(x);
+}
+
+__global__ void __launch_bounds__(256) alu_peak_f32_kernel(int iters, float b, float c, float never, double *sink)
+{
+    unsigned long long a[PEAK_CHAINS];
+    const unsigned long long B = pack_f32x2(b, b), C = pack_f32x2(c, c);
+#pragma unroll
+    for (int k = 0; k < PEAK_CHAINS; ++k) a[k] = pack_f32x2((threadIdx.x + 2 * k) * 1e-3f, (threadIdx.x + 2 * k + 1) * 1e-3f);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int s = 0; s < PEAK_STEPS; ++s)
+#pragma unroll
+            for (int k = 0; k < PEAK_CHAINS; ++k) a[k] = fma_f32x2(a[k], B, C);
+    }
+    float sum = 0.0f;
+#pragma unroll
+    for (int k = 0; k < PEAK_CHAINS; ++k)
+        sum += __uint_as_float((unsigned)a[k]) + __uint_as_float((unsigned)(a[k] >> 32));
     if (sum == never) *sink = (double)sum;
 }
 
@@ -245,12 +280,12 @@ extern "C" int rd_alu_peak(int kind, int64_t iters, int ctas_per_sm, double *sin
     const int grid = ctas_per_sm * rd_sm_count_cached(), block = 256;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (kind == RD_PEAK_FP32)
-        rd::alu_peak_kernel<float><<<grid, block, 0, st>>>(iters, 0.999999f, 1e-7f, -1.2345e-33f, sink);
+        rd::alu_peak_f32_kernel<<<grid, block, 0, st>>>((int)iters, 0.999999f, 1e-7f, -1.2345e-33f, sink);
     else
-        rd::alu_peak_kernel<double><<<grid, block, 0, st>>>(iters, 0.999999999, 1e-12, -1.2345e-300, sink);
+        rd::alu_peak_f64_kernel<<<grid, block, 0, st>>>((int)iters, 0.999999999, 1e-12, -1.2345e-300, sink);
     int rc = rd_check_launch("alu_peak_kernel");
     if (rc) return rc;
-    if (flops)
-        *flops = (uint64_t)grid * block * (uint64_t)iters * rd::PEAK_STEPS * rd::PEAK_CHAINS * 2ull;
+    const uint64_t fma_per_iter = (uint64_t)rd::PEAK_STEPS * rd::PEAK_CHAINS * (kind == RD_PEAK_FP32 ? 2u : 1u);
+    if (flops) *flops = (uint64_t)grid * block * (uint64_t)iters * fma_per_iter * 2ull;
     return RD_OK;
 }
