@@ -607,7 +607,8 @@ def other_configs(args, rank, world, local_rank) -> dict:
     out = {}
     u = copy.copy(sub)
     u.log2n = 24
-    out["batching"] = _compact(run_uneven(u, rank, world, local_rank, emit=False), ("status", "sweeps_per_poly"))
+    out["batching"] = _compact(run_uneven(u, rank, world, local_rank, emit=False),
+                               ("status", "sweeps_per_poly", "mixed_df_polish"))
     out["differentiation"] = _compact(run_adjoint(sub, rank, world, local_rank, emit=False),
                                       ("c128", "c64", "grad_error"))
     out["full_pipeline"] = _compact(run_pipeline(sub, rank, world, local_rank, emit=False),
@@ -892,6 +893,41 @@ def run_uneven(args, rank: int, world: int, local_rank: int, emit: bool = True):
     if world > 1:
         D.reduce_images(hist, dst=0)
 
+    # the same batch and graph with the FP32-pipe compensated polish
+    # (RD_POLISH_DF), each bin in the one-role shape the tuner picks for it
+    tuned_df = autotune.tune("mixed", degrees=range(2, 13), polish="df")
+    tuning_df = autotune.uneven_tuning(tuned_df)
+    p_df = api.params("mixed", polish_mode="df")
+    hist_df = api.new_hist(W_PIX, H_PIX, dev)
+    stats_df = api.new_stats(dev)
+
+    def step_df():
+        api.hist_clear(hist_df)
+        api.hist_clear(stats_df)
+        api.roots_uneven(packed, deg, off, ws, mode="mixed", params_=p_df, tuning=tuning_df, window=win,
+                         hist=hist_df, stats=stats_df, want_roots=False, want_status=False)
+
+    step_df()
+    torch.cuda.synchronize()
+    graph_df = torch.cuda.CUDAGraph()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph_df, stream=side):
+            step_df()
+    torch.cuda.current_stream().wait_stream(side)
+    for _ in range(args.warmup):
+        graph_df.replay()
+    torch.cuda.synchronize()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk_df:
+        d0.record(stream)
+        for _ in range(args.steps):
+            graph_df.replay()
+        d1.record(stream)
+        torch.cuda.synchronize()
+    ms_df = D.max_over_ranks(d0.elapsed_time(d1), device=dev)
+    st_df = api.stats_dict(stats_df)
+
     # end to end: inputs in page-locked host memory. Main: the graph's own
     # kernels (count, pack) read them across the host link (zero copy);
     # beside it: explicit copies into the device buffers before each replay
@@ -1030,6 +1066,16 @@ def run_uneven(args, rank: int, world: int, local_rank: int, emit: bool = True):
         "status": {k: st[k] for k in ("status_ok", "status_not_converged", "status_rejected", "status_degenerate")},
         "sweeps_per_poly": st["sweeps"] / max(1, st["polys"]),
     }
+    g32, g64 = algorithmic_flops(st_df)
+    t_df = ms_df * 1e-3 / args.steps
+    line["mixed_df_polish"] = {
+        "value": n * world * args.steps / (ms_df * 1e-3), "unit": UNIT, "ms_per_step": ms_df / args.steps,
+        "fp32_frac": g32 / p32 / t_df, "fp64_frac": g64 / p64 / t_df, "frac": g32 / p32 / t_df + g64 / p64 / t_df,
+        "status": {k: st_df[k] for k in ("status_ok", "status_not_converged", "status_rejected",
+                                         "status_degenerate")},
+        "identical_image": bool(torch.equal(hist_df, hist)) if world == 1 else None,
+        "note": "RD_POLISH_DF (Newton steps on the FP32 pipe, compensated Horner; FP64 final residual), one "
+                "graph replay per step, each bin in its tuned one-role shape", "clocks": clk_df.summary()}
     if e2e is not None:
         line["e2e"] = e2e
     # the oracle's first chunk (polynomials 0..32767 of the stream), solved again

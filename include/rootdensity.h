@@ -270,8 +270,12 @@ int rd_pointer_is_device_accessible(const void *p);
  *             degree); see rd_uneven_tuning
  * n < 2^32 and n_coeffs <= 2^40 (RD_EINVAL otherwise;
  * rd_uneven_workspace_bytes returns 0 outside these limits). Only enqueues
- * kernels on `stream` (16 launches), so the whole call can be captured in a
- * CUDA graph. */
+ * work (16 kernel launches): the degree bins run as two chains, one on
+ * `stream` and one on a helper stream of the calling host thread, forked from
+ * and joined back to `stream` with events, so the whole call can be captured
+ * in a CUDA graph (as two parallel branches) and `stream` orders everything
+ * before and after it. The first call on a device from a host thread creates
+ * the helper stream and its two events; make that call outside capture. */
 typedef struct {
     /* Launch shape of each degree bin's solve kernel, indexed by the degree
      * (entries 1..12; entries 0 and 13..15 are ignored). 0 = the default.   */

@@ -182,6 +182,47 @@ __global__ void __launch_bounds__(256) uneven_pack_kernel(UnevenArgs U, const E 
     }
 }
 
+namespace {
+struct ForkState {
+    int device = -1;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+thread_local ForkState g_fork[64];
+}  // namespace
+
+int uneven_fork(cudaStream_t st, cudaStream_t *side, cudaEvent_t *fork, cudaEvent_t *join)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return rd_set_error(RD_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64) return rd_set_error(RD_EUNSUPPORTED, "device index %d above 63", dev);
+    ForkState &f = g_fork[dev];
+    if (!f.side) {
+        if ((e = cudaStreamCreateWithFlags(&f.side, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&f.join, cudaEventDisableTiming)) != cudaSuccess)
+            return rd_set_error(RD_ECUDA, "uneven helper stream: %s (the first call on a device from a host thread "
+                                          "creates it; make that call outside stream capture)",
+                                cudaGetErrorString(e));
+        f.device = dev;
+    }
+    if ((e = cudaEventRecord(f.fork, st)) != cudaSuccess || (e = cudaStreamWaitEvent(f.side, f.fork, 0)) != cudaSuccess)
+        return rd_set_error(RD_ECUDA, "uneven fork: %s", cudaGetErrorString(e));
+    *side = f.side;
+    *fork = f.fork;
+    *join = f.join;
+    return RD_OK;
+}
+
+int uneven_join(cudaStream_t st, cudaStream_t side, cudaEvent_t join)
+{
+    cudaError_t e;
+    if ((e = cudaEventRecord(join, side)) != cudaSuccess || (e = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess)
+        return rd_set_error(RD_ECUDA, "uneven join: %s", cudaGetErrorString(e));
+    return RD_OK;
+}
+
 size_t uneven_workspace_bytes(int64_t n, int64_t n_coeffs, rd_dtype dt)
 {
     if (!uneven_sizes_ok(n, n_coeffs)) return 0;

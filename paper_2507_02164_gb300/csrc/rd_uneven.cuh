@@ -58,6 +58,13 @@ inline UnevenLayout uneven_layout(void *ws, int64_t n)
     return L;
 }
 
+// Fork: a helper stream of the calling host thread on the current device
+// (created on its first use, non-blocking) made to wait for `st`; join:
+// `st` made to wait for the helper. Both only record and wait on events, so
+// they can be captured into a CUDA graph (as two parallel branches).
+int uneven_fork(cudaStream_t st, cudaStream_t *side, cudaEvent_t *fork, cudaEvent_t *join);
+int uneven_join(cudaStream_t st, cudaStream_t side, cudaEvent_t join);
+
 // Solve every degree bin of a packed batch (one persistent kernel per
 // degree, largest degree first) with the per-degree launch shapes
 // block[d], cps[d] and lanes per polynomial lanes[d].

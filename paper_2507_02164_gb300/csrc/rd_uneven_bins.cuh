@@ -87,18 +87,28 @@ static int launch_degree_bin(const SolveArgs &a, const UnevenLayout &L, const in
                              "uneven_solve_kernel");
 }
 
-// Degree bins largest first: the most expensive work starts first.
+// The twelve degree bins run as two chains of persistent kernels, forked from
+// the caller's stream onto a helper stream and joined back (under stream
+// capture: two parallel graph branches), so that one chain's kernels take
+// over the SMs the other chain's kernel leaves while its queue drains. Work
+// per bin grows about as d^2.5; the chains hold about equal shares, each
+// largest first: 12, 9, 8, 5, 2, 1 on the caller's stream and 11, 10, 7, 6, 4,
+// 3 on the helper.
 template <typename In, int MODE>
 int launch_uneven_bins(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, const int *block,
                        const int *cps, const int *lanes, cudaStream_t st)
 {
-    int rc = 0;
-#define RD_BIN(D) \
-    if (!rc) rc = launch_degree_bin<D, In, MODE>(a, L, offsets, block[D], cps[D], lanes[D], st);
-    RD_BIN(12) RD_BIN(11) RD_BIN(10) RD_BIN(9) RD_BIN(8) RD_BIN(7)
-    RD_BIN(6) RD_BIN(5) RD_BIN(4) RD_BIN(3) RD_BIN(2) RD_BIN(1)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    int rc = uneven_fork(st, &side, &fork, &join);
+    if (rc) return rc;
+#define RD_BIN(D, S) \
+    if (!rc) rc = launch_degree_bin<D, In, MODE>(a, L, offsets, block[D], cps[D], lanes[D], S);
+    RD_BIN(11, side) RD_BIN(12, st) RD_BIN(10, side) RD_BIN(9, st) RD_BIN(7, side) RD_BIN(8, st)
+    RD_BIN(6, side) RD_BIN(5, st) RD_BIN(4, side) RD_BIN(2, st) RD_BIN(3, side) RD_BIN(1, st)
 #undef RD_BIN
-    return rc;
+    const int rj = uneven_join(st, side, join);
+    return rc ? rc : rj;
 }
 
 }  // namespace rd
