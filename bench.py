@@ -1050,11 +1050,14 @@ def run_uneven(args, rank: int, world: int, local_rank: int, emit: bool = True):
                                f"over [-3,3]x[-1.6875,1.6875]", "polys_per_gpu": n,
                    "coefficients": int(packed.numel()), "l2_flush": "inputs larger than L2 (0.94 GB per step)",
                    "parallelism": f"dp{world}",
-                   "launch_shapes": {"per_degree": {d: {k: e.get("one_role", e)[k]
-                                                        for k in ("lanes", "block", "ctas_per_sm", "ms")}
-                                                    for d, e in tuned["degrees"].items()},
-                                     "note": "each degree bin's fastest one-role shape (the bins have no "
-                                             "warp-specialised form)",
+                   "launch_shapes": {"per_degree": {str(d): {"block": int(tuning.block[d]),
+                                                             "ctas_per_sm": int(tuning.ctas_per_sm[d]),
+                                                             "lanes": int(tuning.lanes[d]),
+                                                             "polish_warps": int(tuning.polish_warps[d])}
+                                                    for d in range(2, 13)},
+                                     "note": "each degree bin's fastest shape: warp-specialised (polish_warps > 0) "
+                                             "where the tuner picked it and the bins have it (degrees <= 8), else "
+                                             "its fastest one-role shape",
                                      "tuning_seconds": tuned["seconds"]}},
         "roofline": {"bound": "alu", "kernel": "whole step (pack + 12 uneven_solve_kernel launches)",
                      "achieved": (f32 + f64 * p32 / p64) / t / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",

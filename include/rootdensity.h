@@ -282,6 +282,12 @@ typedef struct {
     int32_t block[16];        /* threads per CTA, a multiple of 32 in [32, 256]                  */
     int32_t ctas_per_sm[16];  /* resident CTAs per SM (0 = the occupancy maximum)                 */
     int32_t lanes[16];        /* lanes per polynomial, 1 or 2 (0 = params.lanes)                  */
+    int32_t polish_warps[16]; /* RD_MIXED, degrees 1..8: P > 0 runs the bin in warp-specialised
+                                 CTAs of block[d] threads (a multiple of 32 up to 512 at degrees
+                                 <= 6, 256 at 7 and 8; 0 = the largest), P warps of each polishing
+                                 what the others sweep (see rd_params.polish_warps), one lane per
+                                 polynomial, ctas_per_sm ignored; 0 = every warp sweeps and then
+                                 polishes. The same roots either way                                */
 } rd_uneven_tuning;
 
 size_t rd_uneven_workspace_bytes(int64_t n, int64_t n_coeffs, rd_dtype dtype);

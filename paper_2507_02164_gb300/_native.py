@@ -42,7 +42,8 @@ class Clip(ctypes.Structure):
 
 class UnevenTuning(ctypes.Structure):
     # indexed by degree (1..12 used)
-    _fields_ = [("block", ctypes.c_int32 * 16), ("ctas_per_sm", ctypes.c_int32 * 16), ("lanes", ctypes.c_int32 * 16)]
+    _fields_ = [("block", ctypes.c_int32 * 16), ("ctas_per_sm", ctypes.c_int32 * 16), ("lanes", ctypes.c_int32 * 16),
+                ("polish_warps", ctypes.c_int32 * 16)]
 
 
 class FieldSpec(ctypes.Structure):

@@ -196,10 +196,12 @@ def new_uneven_workspace(n: int, n_coeffs: int, dtype=torch.complex64, device="c
     return torch.empty(uneven_workspace_bytes(n, n_coeffs, dtype), dtype=torch.uint8, device=device)
 
 
-def uneven_tuning(block=None, ctas_per_sm=None, lanes=None) -> N.UnevenTuning:
-    """rd_uneven_tuning from {degree: value} dicts (missing degrees: defaults)."""
+def uneven_tuning(block=None, ctas_per_sm=None, lanes=None, polish_warps=None) -> N.UnevenTuning:
+    """rd_uneven_tuning from {degree: value} dicts (missing degrees: defaults;
+    polish_warps > 0 runs that degree's bin warp-specialised, degrees <= 8)."""
     t = N.UnevenTuning()
-    for arr, vals in ((t.block, block), (t.ctas_per_sm, ctas_per_sm), (t.lanes, lanes)):
+    for arr, vals in ((t.block, block), (t.ctas_per_sm, ctas_per_sm), (t.lanes, lanes),
+                      (t.polish_warps, polish_warps)):
         for d, v in (vals or {}).items():
             if not 1 <= int(d) <= 12:
                 raise ValueError(f"tuning degree {d} outside 1..12")

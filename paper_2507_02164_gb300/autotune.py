@@ -97,13 +97,24 @@ def tune(mode: str = "mixed", dtype=torch.complex64, degrees=range(1, 13), n: in
     return {"degrees": per_deg, "seconds": spent, "probe_polys": n}
 
 
+UNEVEN_WS_MAX_DEG = 8  # the uneven bins have a warp-specialised form up to this degree
+
+
 def uneven_tuning(result: dict):
     """rd_uneven_tuning (per degree) from a tune() result: each degree's
-    fastest one-role shape (the uneven bins have no warp-specialised form)."""
-    deg = {d: e.get("one_role", e) for d, e in result["degrees"].items()}
+    fastest shape where the bins have it (the warp-specialised form up to
+    degree 8), else its fastest one-role shape."""
+    deg = {}
+    for d, e in result["degrees"].items():
+        if int(d) <= UNEVEN_WS_MAX_DEG and e.get("polish_warps", 0) > 0:
+            deg[d] = {"block": e["block"], "ctas_per_sm": 0, "lanes": 1, "polish_warps": e["polish_warps"]}
+        else:
+            o = e.get("one_role", e)
+            deg[d] = {"block": o["block"], "ctas_per_sm": o["ctas_per_sm"], "lanes": o["lanes"], "polish_warps": 0}
     return api.uneven_tuning(block={int(d): e["block"] for d, e in deg.items()},
                              ctas_per_sm={int(d): e["ctas_per_sm"] for d, e in deg.items()},
-                             lanes={int(d): e["lanes"] for d, e in deg.items()})
+                             lanes={int(d): e["lanes"] for d, e in deg.items()},
+                             polish_warps={int(d): e["polish_warps"] for d, e in deg.items()})
 
 
 def degree_params(result: dict, degree: int, mode: str = "mixed", polish: str = "fp64"):

@@ -30,7 +30,7 @@ int l2_nodes_host(int nr, double *r, double *w);
 size_t uneven_workspace_bytes(int64_t n, int64_t n_coeffs, rd_dtype dt);
 int launch_uneven(const SolveArgs &a, rd_dtype dt, const uint8_t *degrees, const int64_t *offsets, int64_t n,
                   int64_t n_coeffs, bool mixed, void *ws, const int *block, const int *cps, const int *lanes,
-                  cudaStream_t st);
+                  const int *pw, cudaStream_t st);
 int launch_l2(const double *samples, int64_t n, int nr, int degree, double *coeffs, int precision,
               cudaStream_t st);
 int launch_field(const SolveArgs &a, const rd_field_spec &spec, int func, double rho, bool mixed, double *coeffs,
@@ -374,11 +374,29 @@ int rd_roots_uneven(const void *coeffs, rd_dtype dtype, const uint8_t *degrees, 
     if (!ws || !aligned(ws, 256)) return rd_set_error(RD_EINVAL, "workspace null or not 256-byte aligned");
     size_t need = rd::uneven_workspace_bytes(n, n_coeffs, dtype);
     if (ws_bytes < need) return rd_set_error(RD_EINVAL, "workspace too small: %zu < %zu bytes", ws_bytes, need);
-    int block[16], cps[16], lanes[16];
+    int block[16], cps[16], lanes[16], pw[16];
     for (int d = 0; d < 16; ++d) {
         block[d] = p.block ? p.block : 128;
         cps[d] = p.ctas_per_sm;
         lanes[d] = p.lanes;
+        pw[d] = 0;
+        if (tuning && d >= 1 && d <= 12 && tuning->polish_warps[d] != 0) {
+            // the warp-specialised form of this bin
+            const int P = tuning->polish_warps[d];
+            const int maxb = d <= 6 ? 512 : 256;
+            const int b = tuning->block[d] ? tuning->block[d] : maxb;
+            if (d > 8) return rd_set_error(RD_EINVAL, "tuning.polish_warps[%d]: built for degrees up to 8", d);
+            if (mode != RD_MIXED) return rd_set_error(RD_EINVAL, "tuning.polish_warps[%d] needs RD_MIXED", d);
+            if (b < 64 || b > maxb || b % 32)
+                return rd_set_error(RD_EINVAL, "tuning.block[%d] must be a multiple of 32 in [64, %d] with polish warps",
+                                    d, maxb);
+            if (P < 1 || P >= b / 32)
+                return rd_set_error(RD_EINVAL, "tuning.polish_warps[%d] must be in [1, %d]", d, b / 32 - 1);
+            if (tuning->lanes[d] == 2) return rd_set_error(RD_EINVAL, "tuning.polish_warps[%d] needs one lane", d);
+            block[d] = b;
+            pw[d] = P;
+            continue;
+        }
         if (tuning && d >= 1 && d <= 12) {
             if (tuning->block[d] != 0 && (tuning->block[d] < 32 || tuning->block[d] > 256 || tuning->block[d] % 32))
                 return rd_set_error(RD_EINVAL, "tuning.block[%d] must be 0 or a multiple of 32 in [32, 256]", d);
@@ -395,7 +413,7 @@ int rd_roots_uneven(const void *coeffs, rd_dtype dtype, const uint8_t *degrees, 
     }
     a.coeffs = coeffs;
     a.n = n;
-    return rd::launch_uneven(a, dtype, degrees, offsets, n, n_coeffs, mode == RD_MIXED, ws, block, cps, lanes,
+    return rd::launch_uneven(a, dtype, degrees, offsets, n, n_coeffs, mode == RD_MIXED, ws, block, cps, lanes, pw,
                              reinterpret_cast<cudaStream_t>(stream));
 }
 

@@ -110,12 +110,16 @@ __device__ __forceinline__ void ws_publish(volatile unsigned *state, unsigned va
     }
 }
 
-// Uniform batch of A.n polynomials of degree N; blockDim.x / 32 warps per
-// CTA (at most MAXB = ws_max_block(N) threads), the first polish_warps of them
-// (1 .. blockDim.x / 32 - 1) polishing; `slots` (2 .. WS_MAX_SLOTS) ring
-// slots in the dynamic shared memory (ws_smem_bytes(N, slots)).
-template <int N, typename In, int MAXB, int MODE>
-__global__ void __launch_bounds__(MAXB, 1) solve_ws_kernel(SolveArgs A, int polish_warps, int slots)
+// One warp-specialised CTA over a coefficient-major batch `coeffs` of n
+// polynomials of degree N whose results go where `map` says (a uniform batch,
+// or one degree bin of a packed batch): blockDim.x / 32 warps, the first
+// polish_warps of them (1 .. blockDim.x / 32 - 1) polishing; `slots`
+// (2 .. WS_MAX_SLOTS) ring slots in the dynamic shared memory
+// (ws_smem_bytes(N, slots)). CTA b of the grid's G takes the tasks
+// (32 polynomials each) b, b + G, b + 2G, ...
+template <int N, typename In, int MODE, class Map>
+__device__ __forceinline__ void ws_cta(const SolveArgs &A, const void *coeffs, int64_t n, const Map &map,
+                                       int polish_warps, int slots)
 {
     static_assert(MODE == MODE_MIXED_FP64 || MODE == MODE_MIXED_DF, "the warp-specialised solver is mixed-mode");
     extern __shared__ __align__(16) unsigned char ws_smem[];
@@ -131,10 +135,9 @@ __global__ void __launch_bounds__(MAXB, 1) solve_ws_kernel(SolveArgs A, int poli
     __syncthreads();
     const CtaStats S = stats_begin(acc, A.stats);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t tasks = (A.n + 31) / 32;
+    const int64_t tasks = (n + 31) / 32;
     const int64_t G = gridDim.x, b = blockIdx.x;
     const unsigned my_tasks = b < tasks ? (unsigned)((tasks - b + G - 1) / G) : 0u;
-    const UniformMap map{{}, A.n};
     volatile unsigned *abort_flag = &ctl->abort;
 
     if (warp >= polish_warps) {
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(MAXB, 1) solve_ws_kernel(SolveArgs A, int poli
             const int64_t i = (b + (int64_t)k * G) * 32 + lane;
             cx<float> d[N];
             bool degenerate, not_conv;
-            sweep_lane<N, float, In, MODE>(A, A.coeffs, A.n, i, S, d, degenerate, not_conv);
+            sweep_lane<N, float, In, MODE>(A, coeffs, n, i, S, d, degenerate, not_conv);
             const unsigned slot = k % (unsigned)slots, round = k / (unsigned)slots;
             if (!ws_wait(&ctl->state[slot], 2u * round, abort_flag)) break;
             WsSlot<N> &w = ring[slot];
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(MAXB, 1) solve_ws_kernel(SolveArgs A, int poli
             const unsigned slot = k % (unsigned)slots, round = k / (unsigned)slots;
             if (!ws_wait(&ctl->state[slot], 2u * round + 1u, abort_flag)) {
                 // abandoned: its polynomials are reported, not solved
-                const bool valid = i < A.n;
+                const bool valid = i < n;
                 if (valid && A.status) A.status[map.poly(i)] = RD_STATUS_REJECTED;
                 S.add(ST_POLYS, valid ? 1u : 0u);
                 S.add(ST_STATUS0 + RD_STATUS_REJECTED, valid ? 1u : 0u);
@@ -188,10 +191,18 @@ __global__ void __launch_bounds__(MAXB, 1) solve_ws_kernel(SolveArgs A, int poli
             const bool degenerate = (w.degenerate >> lane) & 1u;
             const bool not_conv = (w.not_conv >> lane) & 1u;
             ws_publish(&ctl->state[slot], 2u * round + 2u);
-            finish_lane<N, float, In, MODE>(A, A.coeffs, A.n, i, map, S, d, degenerate, not_conv);
+            finish_lane<N, float, In, MODE>(A, coeffs, n, i, map, S, d, degenerate, not_conv);
         }
     }
     stats_end(S, A.stats);
+}
+
+// Uniform batch of A.n polynomials of degree N, at most MAXB = ws_max_block(N)
+// threads per CTA.
+template <int N, typename In, int MAXB, int MODE>
+__global__ void __launch_bounds__(MAXB, 1) solve_ws_kernel(SolveArgs A, int polish_warps, int slots)
+{
+    ws_cta<N, In, MODE>(A, A.coeffs, A.n, UniformMap{{}, A.n}, polish_warps, slots);
 }
 
 }  // namespace rd

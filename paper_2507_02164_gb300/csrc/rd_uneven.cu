@@ -183,10 +183,19 @@ __global__ void __launch_bounds__(256) uneven_pack_kernel(UnevenArgs U, const E 
 }
 
 namespace {
+// The helper stream and its two events, per device, owned by one host thread
+// and released when that thread exits (errors ignored: at process exit the
+// runtime may already be gone).
 struct ForkState {
     int device = -1;
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    ~ForkState()
+    {
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (side) cudaStreamDestroy(side);
+    }
 };
 thread_local ForkState g_fork[64];
 }  // namespace
@@ -199,12 +208,21 @@ int uneven_fork(cudaStream_t st, cudaStream_t *side, cudaEvent_t *fork, cudaEven
     if (dev < 0 || dev >= 64) return rd_set_error(RD_EUNSUPPORTED, "device index %d above 63", dev);
     ForkState &f = g_fork[dev];
     if (!f.side) {
-        if ((e = cudaStreamCreateWithFlags(&f.side, cudaStreamNonBlocking)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&f.join, cudaEventDisableTiming)) != cudaSuccess)
+        // all three or none: a partial failure releases what it made
+        cudaStream_t s = nullptr;
+        cudaEvent_t a = nullptr, b = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&a, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&b, cudaEventDisableTiming)) != cudaSuccess) {
+            if (a) cudaEventDestroy(a);
+            if (s) cudaStreamDestroy(s);
             return rd_set_error(RD_ECUDA, "uneven helper stream: %s (the first call on a device from a host thread "
                                           "creates it; make that call outside stream capture)",
                                 cudaGetErrorString(e));
+        }
+        f.side = s;
+        f.fork = a;
+        f.join = b;
         f.device = dev;
     }
     if ((e = cudaEventRecord(f.fork, st)) != cudaSuccess || (e = cudaStreamWaitEvent(f.side, f.fork, 0)) != cudaSuccess)
@@ -231,7 +249,7 @@ size_t uneven_workspace_bytes(int64_t n, int64_t n_coeffs, rd_dtype dt)
 
 int launch_uneven(const SolveArgs &a, rd_dtype dt, const uint8_t *degrees, const int64_t *offsets, int64_t n,
                   int64_t n_coeffs, bool mixed, void *ws, const int *block, const int *cps, const int *lanes,
-                  cudaStream_t st)
+                  const int *pw, cudaStream_t st)
 {
     UnevenLayout L = uneven_layout(ws, n);
     UnevenArgs U{degrees, offsets, n, n_coeffs};
@@ -257,13 +275,13 @@ int launch_uneven(const SolveArgs &a, rd_dtype dt, const uint8_t *degrees, const
     if ((rc = rd_check_launch("uneven_pack_kernel"))) return rc;
     const int mode = !mixed ? MODE_PLAIN : (a.polish_mode == RD_POLISH_DF ? MODE_MIXED_DF : MODE_MIXED_FP64);
     if (dt == RD_C64) {
-        if (mode == MODE_PLAIN) return launch_uneven_bins<float2, MODE_PLAIN>(a, L, offsets, block, cps, lanes, st);
-        if (mode == MODE_MIXED_DF) return launch_uneven_bins<float2, MODE_MIXED_DF>(a, L, offsets, block, cps, lanes, st);
-        return launch_uneven_bins<float2, MODE_MIXED_FP64>(a, L, offsets, block, cps, lanes, st);
+        if (mode == MODE_PLAIN) return launch_uneven_bins<float2, MODE_PLAIN>(a, L, offsets, block, cps, lanes, pw, st);
+        if (mode == MODE_MIXED_DF) return launch_uneven_bins<float2, MODE_MIXED_DF>(a, L, offsets, block, cps, lanes, pw, st);
+        return launch_uneven_bins<float2, MODE_MIXED_FP64>(a, L, offsets, block, cps, lanes, pw, st);
     }
-    if (mode == MODE_PLAIN) return launch_uneven_bins<double2, MODE_PLAIN>(a, L, offsets, block, cps, lanes, st);
-    if (mode == MODE_MIXED_DF) return launch_uneven_bins<double2, MODE_MIXED_DF>(a, L, offsets, block, cps, lanes, st);
-    return launch_uneven_bins<double2, MODE_MIXED_FP64>(a, L, offsets, block, cps, lanes, st);
+    if (mode == MODE_PLAIN) return launch_uneven_bins<double2, MODE_PLAIN>(a, L, offsets, block, cps, lanes, pw, st);
+    if (mode == MODE_MIXED_DF) return launch_uneven_bins<double2, MODE_MIXED_DF>(a, L, offsets, block, cps, lanes, pw, st);
+    return launch_uneven_bins<double2, MODE_MIXED_FP64>(a, L, offsets, block, cps, lanes, pw, st);
 }
 
 }  // namespace rd

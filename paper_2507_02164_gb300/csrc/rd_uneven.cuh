@@ -67,9 +67,10 @@ int uneven_join(cudaStream_t st, cudaStream_t side, cudaEvent_t join);
 
 // Solve every degree bin of a packed batch (one persistent kernel per
 // degree, largest degree first) with the per-degree launch shapes
-// block[d], cps[d] and lanes per polynomial lanes[d].
+// block[d], cps[d], lanes per polynomial lanes[d] and polish warps pw[d]
+// (> 0: the warp-specialised form, mixed mode, degrees up to 8).
 template <typename In, int MODE>
 int launch_uneven_bins(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, const int *block,
-                       const int *cps, const int *lanes, cudaStream_t st);
+                       const int *cps, const int *lanes, const int *pw, cudaStream_t st);
 
 }  // namespace rd

@@ -4,7 +4,10 @@
 // of which instantiates it for one storage type and precision mode.
 #pragma once
 
+#include <atomic>
+
 #include "rd_solve2.cuh"
+#include "rd_solve_ws.cuh"
 #include "rd_uneven.cuh"
 
 namespace rd {
@@ -58,6 +61,61 @@ __global__ void __maxnreg__(two_lane_regs(N, MODE))
     stats_end(S, A.stats);
 }
 
+// The warp-specialised form (rd_solve_ws.cuh) of the degree-N bin: sweep
+// warps and polish warps meet at a shared-memory ring; CTA b takes the bin's
+// tasks b, b + G, ... (the bin's size is read on the device). Built for the
+// degrees up to UNEVEN_WS_MAX_DEG, where the split measured faster than the
+// one-role kernel.
+constexpr int UNEVEN_WS_MAX_DEG = 8;
+
+template <int N, typename In, int MAXB, int MODE>
+__global__ void __launch_bounds__(MAXB, 1)
+    uneven_solve_ws_kernel(SolveArgs A, UnevenHeader *hdr, const uint32_t *perm, const char *bins,
+                           const int64_t *offsets, int polish_warps, int slots)
+{
+    const int64_t cnt = hdr->count[N];
+    const PackedMap map{{}, perm + hdr->poly_base[N], offsets};
+    const void *base = bins + (size_t)hdr->coef_base[N] * sizeof(In);
+    ws_cta<N, In, MODE>(A, base, cnt, map, polish_warps, slots);
+}
+
+// Dynamic shared memory above 48 KB needs the kernel's opt-in, per device
+// (raised once per device to the largest size asked for; host calls only).
+template <int N, typename In, int MAXB, int MODE>
+static int uneven_ws_allow_smem(size_t bytes)
+{
+    static std::atomic<size_t> allowed[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return rd_check_launch("cudaGetDevice");
+    if (dev < 0 || dev >= 64) return rd_set_error(RD_EUNSUPPORTED, "device %d: at most 64 devices", dev);
+    if (bytes <= 48 * 1024 || bytes <= allowed[dev].load()) return RD_OK;
+    if (cudaFuncSetAttribute(uneven_solve_ws_kernel<N, In, MAXB, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes) != cudaSuccess)
+        return rd_check_launch("cudaFuncSetAttribute(uneven_solve_ws_kernel)");
+    size_t cur = allowed[dev].load();
+    while (cur < bytes && !allowed[dev].compare_exchange_weak(cur, bytes)) {
+    }
+    return RD_OK;
+}
+
+template <int N, typename In, int MODE>
+static int launch_uneven_ws(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, int block,
+                            int polish_warps, cudaStream_t st)
+{
+    constexpr int MAXB = ws_max_block(N);
+    const int warps = block / 32;
+    const int slots = 2 * warps < WS_MAX_SLOTS ? 2 * warps : WS_MAX_SLOTS;
+    const size_t smem = ws_smem_bytes(N, slots);
+    int rc = uneven_ws_allow_smem<N, In, MAXB, MODE>(smem);
+    if (rc) return rc;
+    auto kern = uneven_solve_ws_kernel<N, In, MAXB, MODE>;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    kern<<<per_sm * rd_sm_count_cached(), block, smem, st>>>(a, L.hdr, L.perm, L.bins, offsets, polish_warps, slots);
+    return rd_check_launch("uneven_solve_ws_kernel");
+}
+
 int lanes_for(int degree, bool mixed, int polish_mode, int requested);
 
 template <typename K>
@@ -76,8 +134,11 @@ static int launch_persistent(K kern, const SolveArgs &a, const UnevenLayout &L, 
 
 template <int N, typename In, int MODE>
 static int launch_degree_bin(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, int block,
-                             int ctas_per_sm, int lanes, cudaStream_t st)
+                             int ctas_per_sm, int lanes, int polish_warps, cudaStream_t st)
 {
+    if constexpr (MODE != MODE_PLAIN && N <= UNEVEN_WS_MAX_DEG) {
+        if (polish_warps > 0) return launch_uneven_ws<N, In, MODE>(a, L, offsets, block, polish_warps, st);
+    }
     if constexpr (N >= 2 && MODE != MODE_MIXED_DF) {
         if (lanes_for(N, MODE != MODE_PLAIN, a.polish_mode, lanes) == 2)
             return launch_persistent(uneven_solve2_kernel<N, In, MODE>, a, L, offsets, block, ctas_per_sm, st,
@@ -96,14 +157,14 @@ static int launch_degree_bin(const SolveArgs &a, const UnevenLayout &L, const in
 // 3 on the helper.
 template <typename In, int MODE>
 int launch_uneven_bins(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, const int *block,
-                       const int *cps, const int *lanes, cudaStream_t st)
+                       const int *cps, const int *lanes, const int *pw, cudaStream_t st)
 {
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
     int rc = uneven_fork(st, &side, &fork, &join);
     if (rc) return rc;
 #define RD_BIN(D, S) \
-    if (!rc) rc = launch_degree_bin<D, In, MODE>(a, L, offsets, block[D], cps[D], lanes[D], S);
+    if (!rc) rc = launch_degree_bin<D, In, MODE>(a, L, offsets, block[D], cps[D], lanes[D], pw[D], S);
     RD_BIN(11, side) RD_BIN(12, st) RD_BIN(10, side) RD_BIN(9, st) RD_BIN(7, side) RD_BIN(8, st)
     RD_BIN(6, side) RD_BIN(5, st) RD_BIN(4, side) RD_BIN(2, st) RD_BIN(3, side) RD_BIN(1, st)
 #undef RD_BIN
@@ -116,5 +177,6 @@ int launch_uneven_bins(const SolveArgs &a, const UnevenLayout &L, const int64_t 
 #define RD_UNEVEN_BINS(IN, MODE)                                                                          \
     namespace rd {                                                                                      \
     template int launch_uneven_bins<IN, MODE>(const SolveArgs &, const UnevenLayout &, const int64_t *, \
-                                              const int *, const int *, const int *, cudaStream_t);     \
+                                              const int *, const int *, const int *, const int *,       \
+                                              cudaStream_t);                                            \
     }

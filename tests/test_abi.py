@@ -41,7 +41,7 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(N.Params) == 72
     assert ctypes.sizeof(N.Window) == 32
     assert ctypes.sizeof(N.Clip) == 64
-    assert ctypes.sizeof(N.UnevenTuning) == 3 * 16 * 4
+    assert ctypes.sizeof(N.UnevenTuning) == 4 * 16 * 4
     assert ctypes.sizeof(N.FieldSpec) == 32 + 8 + 8 + 16 + 26 * 8
     assert N.STATS_WORDS == 15
 

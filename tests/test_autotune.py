@@ -8,11 +8,13 @@ from paper_2507_02164_gb300 import _native as N
 from paper_2507_02164_gb300 import autotune, build
 
 
-def test_uneven_tuning_takes_the_one_role_winner_and_uniform_params_the_overall_one():
-    res = {"degrees": {"6": {"lanes": 1, "block": 512, "ctas_per_sm": 0, "polish_warps": 10, "ms": 1.0,
-                             "one_role": {"lanes": 1, "block": 256, "ctas_per_sm": 2, "ms": 1.1}}}}
+def test_uneven_tuning_takes_the_warp_specialised_winner_up_to_degree_8_else_the_one_role_one():
+    ws = {"lanes": 1, "block": 512, "ctas_per_sm": 0, "polish_warps": 10, "ms": 1.0,
+          "one_role": {"lanes": 1, "block": 256, "ctas_per_sm": 2, "ms": 1.1}}
+    res = {"degrees": {"6": dict(ws), "9": dict(ws, block=256, polish_warps=4)}}
     t = autotune.uneven_tuning(res)
-    assert list(t.block)[6] == 256 and list(t.ctas_per_sm)[6] == 2
+    assert list(t.block)[6] == 512 and list(t.polish_warps)[6] == 10 and list(t.ctas_per_sm)[6] == 0
+    assert list(t.block)[9] == 256 and list(t.polish_warps)[9] == 0 and list(t.ctas_per_sm)[9] == 2
     p = autotune.degree_params(res, 6)
     assert p.block == 512 and p.polish_warps == 10
 

@@ -266,9 +266,11 @@ def test_double_float_polish_matches_oracle(dev, orc, dtype):
 
 # ------------------------------------- full size, in the benchmark's launch shape
 
-def test_full_littlewood_batch_sampled(dev, orc):
+@pytest.mark.parametrize("polish", ["fp64", "df"])
+def test_full_littlewood_batch_sampled(dev, orc, polish):
     """The 2^26-polynomial Littlewood batch exactly as bench.py times it (fused
-    roots + histogram, autotuned launch shape, mixed), with the roots stored:
+    roots + histogram, autotuned launch shape, mixed; the FP64 polish of the
+    headline and the compensated FP32-pipe polish), with the roots stored:
     every counter adds up, the fused histogram equals the standalone binning
     of the stored roots, and 2^16 polynomials spread over the batch match the
     oracle at the 1e-9 bar (mixed) and, for the plain FP64 path on the same
@@ -276,8 +278,8 @@ def test_full_littlewood_batch_sampled(dev, orc):
     from paper_2507_02164_gb300 import autotune
     n = 1 << 26
     coeffs = WL.littlewood_soa_torch(2, 0, n, dev)
-    tuned = autotune.tune("mixed", degrees=[6])
-    p = autotune.degree_params(tuned, 6, "mixed")
+    tuned = autotune.tune("mixed", degrees=[6], polish=polish)
+    p = autotune.degree_params(tuned, 6, "mixed", polish)
     hist = api.new_hist(W, H, dev)
     stats = api.new_stats(dev)
     roots = torch.empty((6, n), dtype=torch.complex128, device=dev)

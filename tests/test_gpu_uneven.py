@@ -268,3 +268,44 @@ def test_malformed_offsets_stay_in_bounds(dev, case):
             assert np.all(np.isfinite(r[slots])), i
     st = api.stats_dict(stats)
     assert st["polys"] == n and st["status_degenerate"] == int((s == 3).sum())
+
+
+@pytest.mark.parametrize("polish", ["fp64", "df"])
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+def test_warp_specialised_bins_bit_identical_to_one_role_bins(dev, polish, dtype):
+    """Degree bins 2..8 in warp-specialised CTAs (rd_uneven_tuning.polish_warps)
+    give the one-role bins' roots, status, image and counters bit for bit;
+    degrees 9..12 stay one-role in both runs."""
+    n = 30000 + 11
+    packed, deg, off = WL.uneven_gaussian(5, n, dtype=np.complex64 if dtype == torch.complex64 else np.complex128)
+    c_t, d_t, o_t = (torch.from_numpy(x).to(dev) for x in (packed, deg, off))
+    ws = api.new_uneven_workspace(n, packed.size, dtype, dev)
+    p = api.params("mixed", polish_mode=polish)
+    shapes = {d: ((512, 8) if d <= 6 else (256, 4)) for d in range(2, 9)}
+    tunings = {"one_role": api.uneven_tuning(block={d: 128 for d in range(2, 13)}),
+               "ws": api.uneven_tuning(block={d: (shapes[d][0] if d in shapes else 128) for d in range(2, 13)},
+                                       polish_warps={d: v[1] for d, v in shapes.items()})}
+    out = {}
+    for name, t in tunings.items():
+        hist = api.new_hist(W, H, dev)
+        stats = api.new_stats(dev)
+        roots, status = api.roots_uneven(c_t, d_t, o_t, ws, mode="mixed", params_=p, tuning=t, window=WIN3,
+                                         hist=hist, stats=stats)
+        torch.cuda.synchronize()
+        out[name] = (torch.view_as_real(roots).view(torch.int64).cpu(), status.cpu(), hist.cpu(),
+                     api.stats_dict(stats))
+    a, b = out["one_role"], out["ws"]
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
+    assert a[3] == b[3] and b[3]["wait_timeouts"] == 0 and b[3]["polys"] == n
+
+
+def test_warp_specialised_bins_argument_checks(dev):
+    packed, deg, off = WL.uneven_gaussian(3, 100)
+    ws = api.new_uneven_workspace(100, packed.size, torch.complex64, dev)
+    args = [torch.from_numpy(x).to(dev) for x in (packed, deg, off)]
+    for kw, mode in ((dict(polish_warps={9: 2}, block={9: 256}), "mixed"),    # degree above 8
+                     (dict(polish_warps={6: 2}, block={6: 128}), "plain"),    # needs RD_MIXED
+                     (dict(polish_warps={6: 4}, block={6: 128}), "mixed"),    # no sweep warp left
+                     (dict(polish_warps={7: 2}, block={7: 512}), "mixed")):   # degree 7: at most 256 threads
+        with pytest.raises(api.N.RootDensityError):
+            api.roots_uneven(*args, ws, mode=mode, tuning=api.uneven_tuning(**kw))
