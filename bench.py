@@ -1078,7 +1078,7 @@ def run_uneven(args, rank: int, world: int, local_rank: int, emit: bool = True):
                                          "status_degenerate")},
         "identical_image": bool(torch.equal(hist_df, hist)) if world == 1 else None,
         "note": "RD_POLISH_DF (Newton steps on the FP32 pipe, compensated Horner; FP64 final residual), one "
-                "graph replay per step, each bin in its tuned one-role shape", "clocks": clk_df.summary()}
+                "graph replay per step, each bin in the shape the tuner picked for this polish", "clocks": clk_df.summary()}
     if e2e is not None:
         line["e2e"] = e2e
     # the oracle's first chunk (polynomials 0..32767 of the stream), solved again
