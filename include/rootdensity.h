@@ -302,7 +302,8 @@ int rd_roots_uneven(const void *coeffs, rd_dtype dtype, const uint8_t *degrees, 
  * an allocator owned by a host framework, loops where cudaMalloc/cudaFree
  * would synchronise the device, deployments with a device-memory budget
  * fixed in advance. It behaves like rd_roots_uneven (same arguments without
- * ws/ws_bytes, same results) but uses a scratch array of
+ * ws/ws_bytes, same results; its degree bins all run on `stream`, so it makes
+ * no helper stream either) but uses a scratch array of
  * RD_STATIC_SCRATCH_BYTES bytes built into the library: that memory is held
  * on every GPU that loads the library until the process exits, and the call
  * itself allocates and frees nothing.

@@ -30,9 +30,13 @@ int l2_nodes_host(int nr, double *r, double *w);
 size_t uneven_workspace_bytes(int64_t n, int64_t n_coeffs, rd_dtype dt);
 int launch_uneven(const SolveArgs &a, rd_dtype dt, const uint8_t *degrees, const int64_t *offsets, int64_t n,
                   int64_t n_coeffs, bool mixed, void *ws, const int *block, const int *cps, const int *lanes,
-                  const int *pw, cudaStream_t st);
+                  const int *pw, bool fork, cudaStream_t st);
 int launch_l2(const double *samples, int64_t n, int nr, int degree, double *coeffs, int precision,
               cudaStream_t st);
+int roots_uneven_common(const void *coeffs, rd_dtype dtype, const uint8_t *degrees, const int64_t *offsets, int64_t n,
+                        int64_t n_coeffs, rd_mode mode, const rd_params *params, const rd_uneven_tuning *tuning,
+                        const rd_window *window, int W, int H, uint32_t *hist, double *roots, uint8_t *status,
+                        rd_stats *stats, void *ws, size_t ws_bytes, bool fork, void *stream);
 int launch_field(const SolveArgs &a, const rd_field_spec &spec, int func, double rho, bool mixed, double *coeffs,
                  int ctas_per_sm, cudaStream_t st);
 int launch_splat(const double *roots, int64_t n, const rd_window &w, int W, int H, double sigma, double scale,
@@ -357,6 +361,21 @@ int rd_roots_uneven(const void *coeffs, rd_dtype dtype, const uint8_t *degrees, 
                     const rd_window *window, int W, int H, uint32_t *hist, double *roots, uint8_t *status,
                     rd_stats *stats, void *ws, size_t ws_bytes, void *stream)
 {
+    return rd::roots_uneven_common(coeffs, dtype, degrees, offsets, n, n_coeffs, mode, params, tuning, window, W, H,
+                                   hist, roots, status, stats, ws, ws_bytes, true, stream);
+}
+
+}  // extern "C"
+
+namespace rd {
+
+// rd_roots_uneven's work; fork = false keeps every degree bin on `stream`
+// (no helper stream is made: the allocation-free entry point).
+int roots_uneven_common(const void *coeffs, rd_dtype dtype, const uint8_t *degrees, const int64_t *offsets, int64_t n,
+                        int64_t n_coeffs, rd_mode mode, const rd_params *params, const rd_uneven_tuning *tuning,
+                        const rd_window *window, int W, int H, uint32_t *hist, double *roots, uint8_t *status,
+                        rd_stats *stats, void *ws, size_t ws_bytes, bool fork, void *stream)
+{
     if (n < 0 || n_coeffs < 0) return rd_set_error(RD_EINVAL, "n and n_coeffs must be >= 0");
     if (n >= ((int64_t)1 << 32)) return rd_set_error(RD_EINVAL, "n must be below 2^32");
     if (n_coeffs > ((int64_t)1 << 40)) return rd_set_error(RD_EINVAL, "n_coeffs must be at most 2^40");
@@ -414,8 +433,12 @@ int rd_roots_uneven(const void *coeffs, rd_dtype dtype, const uint8_t *degrees, 
     a.coeffs = coeffs;
     a.n = n;
     return rd::launch_uneven(a, dtype, degrees, offsets, n, n_coeffs, mode == RD_MIXED, ws, block, cps, lanes, pw,
-                             reinterpret_cast<cudaStream_t>(stream));
+                             fork, reinterpret_cast<cudaStream_t>(stream));
 }
+
+}  // namespace rd
+
+extern "C" {
 
 int rd_roots_backward(const void *coeffs, rd_dtype dtype, int degree, int64_t n, const double *roots,
                       const double *grad_roots, void *grad_coeffs, uint8_t *status, void *stream)

@@ -200,7 +200,7 @@ struct ForkState {
 thread_local ForkState g_fork[64];
 }  // namespace
 
-int uneven_fork(cudaStream_t st, cudaStream_t *side, cudaEvent_t *fork, cudaEvent_t *join)
+int uneven_fork(cudaStream_t st, cudaStream_t *side, cudaEvent_t *fork, cudaEvent_t *join, bool retry)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -225,8 +225,15 @@ int uneven_fork(cudaStream_t st, cudaStream_t *side, cudaEvent_t *fork, cudaEven
         f.join = b;
         f.device = dev;
     }
-    if ((e = cudaEventRecord(f.fork, st)) != cudaSuccess || (e = cudaStreamWaitEvent(f.side, f.fork, 0)) != cudaSuccess)
-        return rd_set_error(RD_ECUDA, "uneven fork: %s", cudaGetErrorString(e));
+    if ((e = cudaEventRecord(f.fork, st)) != cudaSuccess || (e = cudaStreamWaitEvent(f.side, f.fork, 0)) != cudaSuccess) {
+        // handles made before a cudaDeviceReset are gone: forget them (they
+        // cannot be destroyed any more) and make new ones, once
+        if (e != cudaErrorInvalidResourceHandle || retry) return rd_set_error(RD_ECUDA, "uneven fork: %s", cudaGetErrorString(e));
+        cudaGetLastError();
+        f.side = nullptr;
+        f.fork = f.join = nullptr;
+        return uneven_fork(st, side, fork, join, true);
+    }
     *side = f.side;
     *fork = f.fork;
     *join = f.join;
@@ -249,7 +256,7 @@ size_t uneven_workspace_bytes(int64_t n, int64_t n_coeffs, rd_dtype dt)
 
 int launch_uneven(const SolveArgs &a, rd_dtype dt, const uint8_t *degrees, const int64_t *offsets, int64_t n,
                   int64_t n_coeffs, bool mixed, void *ws, const int *block, const int *cps, const int *lanes,
-                  const int *pw, cudaStream_t st)
+                  const int *pw, bool fork, cudaStream_t st)
 {
     UnevenLayout L = uneven_layout(ws, n);
     UnevenArgs U{degrees, offsets, n, n_coeffs};
@@ -275,13 +282,13 @@ int launch_uneven(const SolveArgs &a, rd_dtype dt, const uint8_t *degrees, const
     if ((rc = rd_check_launch("uneven_pack_kernel"))) return rc;
     const int mode = !mixed ? MODE_PLAIN : (a.polish_mode == RD_POLISH_DF ? MODE_MIXED_DF : MODE_MIXED_FP64);
     if (dt == RD_C64) {
-        if (mode == MODE_PLAIN) return launch_uneven_bins<float2, MODE_PLAIN>(a, L, offsets, block, cps, lanes, pw, st);
-        if (mode == MODE_MIXED_DF) return launch_uneven_bins<float2, MODE_MIXED_DF>(a, L, offsets, block, cps, lanes, pw, st);
-        return launch_uneven_bins<float2, MODE_MIXED_FP64>(a, L, offsets, block, cps, lanes, pw, st);
+        if (mode == MODE_PLAIN) return launch_uneven_bins<float2, MODE_PLAIN>(a, L, offsets, block, cps, lanes, pw, fork, st);
+        if (mode == MODE_MIXED_DF) return launch_uneven_bins<float2, MODE_MIXED_DF>(a, L, offsets, block, cps, lanes, pw, fork, st);
+        return launch_uneven_bins<float2, MODE_MIXED_FP64>(a, L, offsets, block, cps, lanes, pw, fork, st);
     }
-    if (mode == MODE_PLAIN) return launch_uneven_bins<double2, MODE_PLAIN>(a, L, offsets, block, cps, lanes, pw, st);
-    if (mode == MODE_MIXED_DF) return launch_uneven_bins<double2, MODE_MIXED_DF>(a, L, offsets, block, cps, lanes, pw, st);
-    return launch_uneven_bins<double2, MODE_MIXED_FP64>(a, L, offsets, block, cps, lanes, pw, st);
+    if (mode == MODE_PLAIN) return launch_uneven_bins<double2, MODE_PLAIN>(a, L, offsets, block, cps, lanes, pw, fork, st);
+    if (mode == MODE_MIXED_DF) return launch_uneven_bins<double2, MODE_MIXED_DF>(a, L, offsets, block, cps, lanes, pw, fork, st);
+    return launch_uneven_bins<double2, MODE_MIXED_FP64>(a, L, offsets, block, cps, lanes, pw, fork, st);
 }
 
 }  // namespace rd

@@ -62,7 +62,7 @@ inline UnevenLayout uneven_layout(void *ws, int64_t n)
 // (created on its first use, non-blocking) made to wait for `st`; join:
 // `st` made to wait for the helper. Both only record and wait on events, so
 // they can be captured into a CUDA graph (as two parallel branches).
-int uneven_fork(cudaStream_t st, cudaStream_t *side, cudaEvent_t *fork, cudaEvent_t *join);
+int uneven_fork(cudaStream_t st, cudaStream_t *side, cudaEvent_t *fork, cudaEvent_t *join, bool retry = false);
 int uneven_join(cudaStream_t st, cudaStream_t side, cudaEvent_t join);
 
 // Solve every degree bin of a packed batch (one persistent kernel per
@@ -71,6 +71,13 @@ int uneven_join(cudaStream_t st, cudaStream_t side, cudaEvent_t join);
 // (> 0: the warp-specialised form, mixed mode, degrees up to 8).
 template <typename In, int MODE>
 int launch_uneven_bins(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, const int *block,
-                       const int *cps, const int *lanes, const int *pw, cudaStream_t st);
+                       const int *cps, const int *lanes, const int *pw, bool fork, cudaStream_t st);
+
+// rd_roots_uneven's argument checks and launch (rd_abi.cu); fork = false
+// keeps every degree bin on `stream` and makes no helper stream.
+int roots_uneven_common(const void *coeffs, rd_dtype dtype, const uint8_t *degrees, const int64_t *offsets, int64_t n,
+                        int64_t n_coeffs, rd_mode mode, const rd_params *params, const rd_uneven_tuning *tuning,
+                        const rd_window *window, int W, int H, uint32_t *hist, double *roots, uint8_t *status,
+                        rd_stats *stats, void *ws, size_t ws_bytes, bool fork, void *stream);
 
 }  // namespace rd

@@ -151,24 +151,25 @@ static int launch_degree_bin(const SolveArgs &a, const UnevenLayout &L, const in
 // The twelve degree bins run as two chains of persistent kernels, forked from
 // the caller's stream onto a helper stream and joined back (under stream
 // capture: two parallel graph branches), so that one chain's kernels take
-// over the SMs the other chain's kernel leaves while its queue drains. Work
+// over the SMs the other chain's kernel leaves while its queue drains
+// (fork_bins = false: all on the caller's stream, no helper stream). Work
 // per bin grows about as d^2.5; the chains hold about equal shares, each
 // largest first: 12, 9, 8, 5, 2, 1 on the caller's stream and 11, 10, 7, 6, 4,
 // 3 on the helper.
 template <typename In, int MODE>
 int launch_uneven_bins(const SolveArgs &a, const UnevenLayout &L, const int64_t *offsets, const int *block,
-                       const int *cps, const int *lanes, const int *pw, cudaStream_t st)
+                       const int *cps, const int *lanes, const int *pw, bool fork_bins, cudaStream_t st)
 {
-    cudaStream_t side = nullptr;
+    cudaStream_t side = st;
     cudaEvent_t fork = nullptr, join = nullptr;
-    int rc = uneven_fork(st, &side, &fork, &join);
+    int rc = fork_bins ? uneven_fork(st, &side, &fork, &join) : RD_OK;
     if (rc) return rc;
 #define RD_BIN(D, S) \
     if (!rc) rc = launch_degree_bin<D, In, MODE>(a, L, offsets, block[D], cps[D], lanes[D], pw[D], S);
     RD_BIN(11, side) RD_BIN(12, st) RD_BIN(10, side) RD_BIN(9, st) RD_BIN(7, side) RD_BIN(8, st)
     RD_BIN(6, side) RD_BIN(5, st) RD_BIN(4, side) RD_BIN(2, st) RD_BIN(3, side) RD_BIN(1, st)
 #undef RD_BIN
-    const int rj = uneven_join(st, side, join);
+    const int rj = fork_bins ? uneven_join(st, side, join) : RD_OK;
     return rc ? rc : rj;
 }
 
@@ -177,6 +178,6 @@ int launch_uneven_bins(const SolveArgs &a, const UnevenLayout &L, const int64_t 
 #define RD_UNEVEN_BINS(IN, MODE)                                                                          \
     namespace rd {                                                                                      \
     template int launch_uneven_bins<IN, MODE>(const SolveArgs &, const UnevenLayout &, const int64_t *, \
-                                              const int *, const int *, const int *, const int *,       \
+                                              const int *, const int *, const int *, const int *, bool, \
                                               cudaStream_t);                                            \
     }

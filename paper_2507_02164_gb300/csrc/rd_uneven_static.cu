@@ -12,7 +12,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "rd_common.cuh"
+#include "rd_uneven.cuh"
 
 // The shared scratch: 32 MiB, enough for the workspace of about 490,000
 // complex64 polynomials of average degree 7. Device code could name it
@@ -77,8 +77,9 @@ extern "C" int rd_roots_uneven_static(const void *coeffs, rd_dtype dtype, const 
     void *ws = nullptr;
     int rc = scratch_address(reinterpret_cast<cudaStream_t>(stream), &ws);
     if (rc) return rc;
-    // the same launch sequence as rd_roots_uneven; its first launch clears the
+    // the launch sequence of rd_roots_uneven, with every degree bin on the
+    // caller's stream (no helper stream is made); its first launch clears the
     // scratch header, every other scratch byte is written before it is read
-    return rd_roots_uneven(coeffs, dtype, degrees, offsets, n, n_coeffs, mode, params, tuning, window, W, H, hist,
-                           roots, status, stats, ws, (size_t)RD_STATIC_SCRATCH_BYTES, stream);
+    return rd::roots_uneven_common(coeffs, dtype, degrees, offsets, n, n_coeffs, mode, params, tuning, window, W, H,
+                                   hist, roots, status, stats, ws, (size_t)RD_STATIC_SCRATCH_BYTES, false, stream);
 }
