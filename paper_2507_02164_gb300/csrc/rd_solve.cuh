@@ -221,6 +221,24 @@ __device__ __forceinline__ cx<T> wilkinson(cx<T> a, cx<T> b, cx<T> c, cx<T> d)
     return sub(d, cdiv(bc, den));
 }
 
+// Deflation test of the trailing 2x2 [[a, b], [c, d]] of the active block.
+// Adaptive: the bottom subdiagonal c is negligible against the diagonal;
+// fixed schedule (Alg. 2): this eigenvalue has had its T sweeps.
+template <typename T>
+__device__ __forceinline__ bool deflates(const SolveArgs &A, T tol, int its, cx<T> a, cx<T> c, cx<T> d)
+{
+    return A.fixed_sweeps > 0 ? (its >= A.fixed_sweeps) : (abs1(c) <= tol * (abs1(a) + abs1(d)));
+}
+
+// The shift of the next sweep: Wilkinson's, or the paper's h[m-1][m-1] with
+// Wilkinson's every exc_period sweeps without deflation.
+template <typename T>
+__device__ __forceinline__ cx<T> pick_shift(const SolveArgs &A, int its, cx<T> a, cx<T> b, cx<T> c, cx<T> d)
+{
+    const bool wilk = (A.shift == RD_SHIFT_WILKINSON) || (A.exc_period > 0 && its > 0 && (its % A.exc_period) == 0);
+    return wilk ? wilkinson(a, b, c, d) : d;
+}
+
 // Where the results of local polynomial i of a solved batch go, and (for
 // the tile clip) the centre and tile of polynomial p, read from the caller's
 // arrays (A.centres, A.tile_index; no tile_index: tile p).
@@ -247,6 +265,52 @@ struct PackedMap : ClipFromArrays {
     __device__ int64_t root(int64_t p, int j) const { return __ldg(offsets + p) - p + j; }
 };
 
+// Load a_0..a_N of local polynomial i (< n: valid) of a coefficient-major
+// batch of n polynomials of degree N (coalesced across a warp) and normalise
+// it to the monic b_0..b_{N-1} in the sweep precision T. Returns true when
+// the polynomial is degenerate (not valid, a coefficient not finite, or
+// a_N = 0); b is then zero or not meaningful.
+template <int N, typename T, typename In, int MODE>
+__device__ __forceinline__ bool load_monic(const void *coeffs, int64_t n, int64_t i, cx<T> (&b)[N])
+{
+    constexpr bool MIXED = MODE != MODE_PLAIN;
+    const bool valid = i < n;
+    bool degenerate = !valid;
+    if (valid) {
+        if constexpr (MIXED && std::is_same<In, float2>::value) {
+            // complex64 storage: FP32 normalisation is exact enough for the sweeps
+            cx<float> a[N + 1];
+#pragma unroll
+            for (int k = 0; k <= N; ++k) a[k] = InLoad<In>::ldf(coeffs, (int64_t)k * n + i);
+#pragma unroll
+            for (int k = 0; k <= N; ++k) degenerate |= !finite_c(a[k]);
+            degenerate |= (a[N].re == 0.0f && a[N].im == 0.0f);
+            cx<float> inv = cdiv(cx<float>{1.0f, 0.0f}, degenerate ? cx<float>{1.0f, 0.0f} : a[N]);
+#pragma unroll
+            for (int k = 0; k < N; ++k) b[k] = mul(a[k], inv);
+        } else {
+            // FP64 coefficients: test and normalise in FP64 (a coefficient outside
+            // the FP32 range is still a valid input), then round for FP32 sweeps
+            cx<double> a[N + 1];
+#pragma unroll
+            for (int k = 0; k <= N; ++k) a[k] = InLoad<In>::ld(coeffs, (int64_t)k * n + i);
+#pragma unroll
+            for (int k = 0; k <= N; ++k) degenerate |= !finite_c(a[k]);
+            degenerate |= (a[N].re == 0.0 && a[N].im == 0.0);
+            cx<double> inv = cdiv(cx<double>{1.0, 0.0}, degenerate ? cx<double>{1.0, 0.0} : a[N]);
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                cx<double> q = mul(a[k], inv);
+                b[k] = {(T)q.re, (T)q.im};
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; ++k) b[k] = {T(0), T(0)};
+    }
+    return degenerate;
+}
+
 // Sweep half of one lane's solve: local polynomial i (< n: valid) of a
 // coefficient-major batch `coeffs` of n polynomials of degree N is loaded,
 // normalised and swept to the diagonal d (its eigenvalues in the sweep
@@ -260,43 +324,8 @@ __device__ __forceinline__ void sweep_lane(const SolveArgs &A, const void *coeff
     constexpr bool MIXED = MODE != MODE_PLAIN;
     const T tol = (T)A.tol;
     {
-        const bool valid = i < n;
-
-        // ---- load a_0..a_N (coefficient-major, coalesced) and normalise
         cx<T> b[N];
-        bool degenerate = !valid;
-        if (valid) {
-            if constexpr (MIXED && std::is_same<In, float2>::value) {
-                // complex64 storage: FP32 normalisation is exact enough for the sweeps
-                cx<float> a[N + 1];
-#pragma unroll
-                for (int k = 0; k <= N; ++k) a[k] = InLoad<In>::ldf(coeffs, (int64_t)k * n + i);
-#pragma unroll
-                for (int k = 0; k <= N; ++k) degenerate |= !finite_c(a[k]);
-                degenerate |= (a[N].re == 0.0f && a[N].im == 0.0f);
-                cx<float> inv = cdiv(cx<float>{1.0f, 0.0f}, degenerate ? cx<float>{1.0f, 0.0f} : a[N]);
-#pragma unroll
-                for (int k = 0; k < N; ++k) b[k] = mul(a[k], inv);
-            } else {
-                // FP64 coefficients: test and normalise in FP64 (a coefficient outside
-                // the FP32 range is still a valid input), then round for FP32 sweeps
-                cx<double> a[N + 1];
-#pragma unroll
-                for (int k = 0; k <= N; ++k) a[k] = InLoad<In>::ld(coeffs, (int64_t)k * n + i);
-#pragma unroll
-                for (int k = 0; k <= N; ++k) degenerate |= !finite_c(a[k]);
-                degenerate |= (a[N].re == 0.0 && a[N].im == 0.0);
-                cx<double> inv = cdiv(cx<double>{1.0, 0.0}, degenerate ? cx<double>{1.0, 0.0} : a[N]);
-#pragma unroll
-                for (int k = 0; k < N; ++k) {
-                    cx<double> q = mul(a[k], inv);
-                    b[k] = {(T)q.re, (T)q.im};
-                }
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < N; ++k) b[k] = {T(0), T(0)};
-        }
+        const bool degenerate = load_monic<N, T, In, MODE>(coeffs, n, i, b);
 
         // ---- Frobenius companion matrix: subdiagonal ones, last column -b
         cx<T> h[N][N];
@@ -319,9 +348,7 @@ __device__ __forceinline__ void sweep_lane(const SolveArgs &A, const void *coeff
             if (m >= 2) {
                 cx<T> ta, tb, tc, td;
                 trailing<N, T>(h, m, ta, tb, tc, td);
-                // adaptive: the bottom subdiagonal is negligible; fixed schedule
-                // (Alg. 2): this eigenvalue has had its T sweeps
-                bool small = A.fixed_sweeps > 0 ? (its >= A.fixed_sweeps) : (abs1(tc) <= tol * (abs1(ta) + abs1(td)));
+                bool small = deflates(A, tol, its, ta, tc, td);
                 if (small || its >= A.max_iters) {
                     not_conv |= !small;
                     m -= 1;
@@ -333,9 +360,7 @@ __device__ __forceinline__ void sweep_lane(const SolveArgs &A, const void *coeff
             if (M < 2) break;
             cx<T> ta, tb, tc, td;
             trailing<N, T>(h, mm >= 2 ? mm : 2, ta, tb, tc, td);
-            bool wilk = (A.shift == RD_SHIFT_WILKINSON) ||
-                        (A.exc_period > 0 && its > 0 && (its % A.exc_period) == 0);
-            cx<T> shift = wilk ? wilkinson(ta, tb, tc, td) : td;
+            cx<T> shift = pick_shift(A, its, ta, tb, tc, td);
             qr_sweep<N, T>(h, mm, M, shift);
             if (mm >= 2) {
                 its += 1;

@@ -110,6 +110,70 @@ __device__ __forceinline__ void ws_publish(volatile unsigned *state, unsigned va
     }
 }
 
+// Put swept task k (its FP32 eigenvalues d and per-lane flags) into ring
+// slot k mod slots once the slot is empty for round k / slots; all 32 lanes
+// call it together. false: the CTA is aborting.
+template <int N>
+__device__ __forceinline__ bool ws_put(WsCtl *ctl, WsSlot<N> *ring, int slots, unsigned k, const cx<float> (&d)[N],
+                                       bool degenerate, bool not_conv, volatile unsigned *abort_flag)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned slot = k % (unsigned)slots, round = k / (unsigned)slots;
+    if (!ws_wait(&ctl->state[slot], 2u * round, abort_flag)) return false;
+    WsSlot<N> &w = ring[slot];
+#pragma unroll
+    for (int j = 0; j < N; ++j) w.d[j][lane] = make_float2(d[j].re, d[j].im);
+    const unsigned dm = __ballot_sync(0xffffffffu, degenerate);
+    const unsigned nm = __ballot_sync(0xffffffffu, not_conv);
+    if (lane == 0) {
+        w.degenerate = dm;
+        w.not_conv = nm;
+    }
+    ws_publish(&ctl->state[slot], 2u * round + 1u);
+    return true;
+}
+
+// The polish role of a warp-specialised CTA: take polish tickets until the
+// CTA's my_tasks tasks are done; each task's slot is emptied and its 32
+// polynomials finished (finish_lane). A task whose slot never fills (the CTA
+// aborted) is reported REJECTED and counted as a wait timeout.
+template <int N, typename In, int MODE, class Map>
+__device__ __forceinline__ void ws_polish_role(const SolveArgs &A, const void *coeffs, int64_t n, const Map &map,
+                                               const CtaStats &S, WsCtl *ctl, const WsSlot<N> *ring, int slots,
+                                               unsigned my_tasks, volatile unsigned *abort_flag)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t G = gridDim.x, b = blockIdx.x;
+    for (;;) {
+        unsigned k = 0;
+        if (lane == 0) k = atomicAdd(&ctl->polish_ticket, 1u);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= my_tasks) break;
+        const int64_t i = (b + (int64_t)k * G) * 32 + lane;
+        const unsigned slot = k % (unsigned)slots, round = k / (unsigned)slots;
+        if (!ws_wait(&ctl->state[slot], 2u * round + 1u, abort_flag)) {
+            // abandoned: its polynomials are reported, not solved
+            const bool valid = i < n;
+            if (valid && A.status) A.status[map.poly(i)] = RD_STATUS_REJECTED;
+            S.add(ST_POLYS, valid ? 1u : 0u);
+            S.add(ST_STATUS0 + RD_STATUS_REJECTED, valid ? 1u : 0u);
+            S.add(ST_TIMEOUT, valid ? 1u : 0u);
+            continue;
+        }
+        const WsSlot<N> &w = ring[slot];
+        cx<float> d[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const float2 v = w.d[j][lane];
+            d[j] = {v.x, v.y};
+        }
+        const bool degenerate = (w.degenerate >> lane) & 1u;
+        const bool not_conv = (w.not_conv >> lane) & 1u;
+        ws_publish(&ctl->state[slot], 2u * round + 2u);
+        finish_lane<N, float, In, MODE>(A, coeffs, n, i, map, S, d, degenerate, not_conv);
+    }
+}
+
 // One warp-specialised CTA over a coefficient-major batch `coeffs` of n
 // polynomials of degree N whose results go where `map` says (a uniform batch,
 // or one degree bin of a packed batch): blockDim.x / 32 warps, the first
@@ -151,48 +215,10 @@ __device__ __forceinline__ void ws_cta(const SolveArgs &A, const void *coeffs, i
             cx<float> d[N];
             bool degenerate, not_conv;
             sweep_lane<N, float, In, MODE>(A, coeffs, n, i, S, d, degenerate, not_conv);
-            const unsigned slot = k % (unsigned)slots, round = k / (unsigned)slots;
-            if (!ws_wait(&ctl->state[slot], 2u * round, abort_flag)) break;
-            WsSlot<N> &w = ring[slot];
-#pragma unroll
-            for (int j = 0; j < N; ++j) w.d[j][lane] = make_float2(d[j].re, d[j].im);
-            const unsigned dm = __ballot_sync(0xffffffffu, degenerate);
-            const unsigned nm = __ballot_sync(0xffffffffu, not_conv);
-            if (lane == 0) {
-                w.degenerate = dm;
-                w.not_conv = nm;
-            }
-            ws_publish(&ctl->state[slot], 2u * round + 1u);
+            if (!ws_put<N>(ctl, ring, slots, k, d, degenerate, not_conv, abort_flag)) break;
         }
     } else {
-        for (;;) {
-            unsigned k = 0;
-            if (lane == 0) k = atomicAdd(&ctl->polish_ticket, 1u);
-            k = __shfl_sync(0xffffffffu, k, 0);
-            if (k >= my_tasks) break;
-            const int64_t i = (b + (int64_t)k * G) * 32 + lane;
-            const unsigned slot = k % (unsigned)slots, round = k / (unsigned)slots;
-            if (!ws_wait(&ctl->state[slot], 2u * round + 1u, abort_flag)) {
-                // abandoned: its polynomials are reported, not solved
-                const bool valid = i < n;
-                if (valid && A.status) A.status[map.poly(i)] = RD_STATUS_REJECTED;
-                S.add(ST_POLYS, valid ? 1u : 0u);
-                S.add(ST_STATUS0 + RD_STATUS_REJECTED, valid ? 1u : 0u);
-                S.add(ST_TIMEOUT, valid ? 1u : 0u);
-                continue;
-            }
-            const WsSlot<N> &w = ring[slot];
-            cx<float> d[N];
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-                const float2 v = w.d[j][lane];
-                d[j] = {v.x, v.y};
-            }
-            const bool degenerate = (w.degenerate >> lane) & 1u;
-            const bool not_conv = (w.not_conv >> lane) & 1u;
-            ws_publish(&ctl->state[slot], 2u * round + 2u);
-            finish_lane<N, float, In, MODE>(A, coeffs, n, i, map, S, d, degenerate, not_conv);
-        }
+        ws_polish_role<N, In, MODE>(A, coeffs, n, map, S, ctl, ring, slots, my_tasks, abort_flag);
     }
     stats_end(S, A.stats);
 }
