@@ -184,6 +184,29 @@ def test_launch_shapes_give_identical_results(dev):
         assert np.array_equal(r, base) and np.array_equal(s, bst)
 
 
+@pytest.mark.parametrize("mode", ["mixed", "plain"])
+@pytest.mark.parametrize("case", ["littlewood6", "real_gauss12", "complex_gauss9"])
+def test_roots_do_not_depend_on_warp_mates(dev, mode, case):
+    """A polynomial's roots are the same bits whichever polynomials share its
+    warp (the sweep size is the warp's largest active block; a frozen lane's
+    rotations are exact identities). Real coefficients included: their
+    imaginary parts are signed zeros throughout the sweeps. The uneven path
+    relies on this, as it packs each degree bin in an unspecified order."""
+    g = np.random.default_rng(17)
+    if case == "littlewood6":
+        co = WL.littlewood(3, 1 << 15)
+    elif case == "real_gauss12":
+        co = g.standard_normal((1 << 13, 13)).astype(np.complex128)
+    else:
+        co = WL.gaussian(9, 1 << 13, 9)
+    perm = g.permutation(co.shape[0])
+    dt = torch.complex64 if mode == "mixed" else torch.complex128
+    ra, sa, _, _ = _solve(to_soa(co, dev, dt), mode)
+    rb, sb, _, _ = _solve(to_soa(co[perm], dev, dt), mode)
+    assert np.array_equal(ra[perm].view(np.int64), rb.view(np.int64))
+    assert np.array_equal(sa[perm], sb)
+
+
 # -------------------------------------------------------- standalone binning
 
 def test_density_accumulate_matches_oracle_bit_for_bit(dev, orc):
