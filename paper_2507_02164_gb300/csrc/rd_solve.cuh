@@ -138,24 +138,36 @@ __device__ __forceinline__ void scale_pow2(cx<double> (&a)[K])
     for (int k = 0; k < K; ++k) a[k] = {a[k].re * f, a[k].im * f};
 }
 
-// One shifted QR sweep of size M (warp-uniform) on h; this lane's rotations
-// r >= m are the identity and its diagonal is shifted only for i < m.
+// Degrees from which qr_sweep leaves its unrolled loops by an early exit
+// at the warp-uniform size M instead of nesting every step in `if (< M)`:
+// the same operations on the same values, but a chain of forward jumps in
+// place of nested blocks that each reconverge. Measured on 2^19 complex-
+// Gaussian polynomials per degree (one-role, FP64 polish): degree 9 3 %,
+// 10 and 11 6 %, 12 11 % faster, warp-specialised degrees 7 and 8 up to
+// 16 %; at degrees 4..6 the nested form measured 0..2.5 % faster.
+constexpr int SWEEP_EARLY_EXIT_MIN = 7;
+
+// One shifted QR sweep of size M (warp-uniform, 2 <= M <= N) on h; this
+// lane's rotations r >= m are the identity and its diagonal is shifted only
+// for i < m.
 template <int N, typename T>
 __device__ __forceinline__ void qr_sweep(cx<T> (&h)[N][N], int m, int M, cx<T> shift)
 {
+    if constexpr (N >= SWEEP_EARLY_EXIT_MIN) {
+        __builtin_assume(M >= 2 && M <= N);
 #pragma unroll
-    for (int i = 0; i < N; ++i)
-        if (i < M) {
+        for (int i = 0; i < N; ++i) {
+            if (i >= M) break;
             bool a = i < m;
             h[i][i].re -= a ? shift.re : T(0);
             h[i][i].im -= a ? shift.im : T(0);
         }
-    T c[N];
-    cx<T> s[N];
-    // left rotations Q_r, r = 1..M-1: zero h[r][r-1], update rows r-1, r
+        T c[N];
+        cx<T> s[N];
+        // left rotations Q_r, r = 1..M-1: zero h[r][r-1], update rows r-1, r
 #pragma unroll
-    for (int r = 1; r < N; ++r) {
-        if (r < M) {
+        for (int r = 1; r < N; ++r) {
+            if (r >= M) break;
             cx<T> top;
             givens(h[r - 1][r - 1], h[r][r - 1], c[r], s[r], top);
             bool act = r < m;
@@ -164,26 +176,68 @@ __device__ __forceinline__ void qr_sweep(cx<T> (&h)[N][N], int m, int M, cx<T> s
             h[r - 1][r - 1] = sel(act, top, h[r - 1][r - 1]);
             h[r][r - 1] = sel(act, cx<T>{T(0), T(0)}, h[r][r - 1]);
 #pragma unroll
-            for (int j = r; j < N; ++j)
-                if (j < M) rot_rows(c[r], s[r], h[r - 1][j], h[r][j]);
+            for (int j = r; j < N; ++j) {
+                if (j >= M) break;
+                rot_rows(c[r], s[r], h[r - 1][j], h[r][j]);
+            }
         }
-    }
-    // right rotations Q_r^H: columns r-1, r over rows 0..r (the matrix is
-    // upper triangular before them, Appendix A)
+        // right rotations Q_r^H: columns r-1, r over rows 0..r (the matrix is
+        // upper triangular before them, Appendix A)
 #pragma unroll
-    for (int r = 1; r < N; ++r) {
-        if (r < M) {
+        for (int r = 1; r < N; ++r) {
+            if (r >= M) break;
 #pragma unroll
             for (int i = 0; i <= r; ++i) rot_cols(c[r], s[r], h[i][r - 1], h[i][r]);
         }
-    }
 #pragma unroll
-    for (int i = 0; i < N; ++i)
-        if (i < M) {
+        for (int i = 0; i < N; ++i) {
+            if (i >= M) break;
             bool a = i < m;
             h[i][i].re += a ? shift.re : T(0);
             h[i][i].im += a ? shift.im : T(0);
         }
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (i < M) {
+                bool a = i < m;
+                h[i][i].re -= a ? shift.re : T(0);
+                h[i][i].im -= a ? shift.im : T(0);
+            }
+        T c[N];
+        cx<T> s[N];
+        // left rotations Q_r, r = 1..M-1: zero h[r][r-1], update rows r-1, r
+#pragma unroll
+        for (int r = 1; r < N; ++r) {
+            if (r < M) {
+                cx<T> top;
+                givens(h[r - 1][r - 1], h[r][r - 1], c[r], s[r], top);
+                bool act = r < m;
+                c[r] = act ? c[r] : T(1);
+                s[r] = sel(act, s[r], cx<T>{T(0), T(0)});
+                h[r - 1][r - 1] = sel(act, top, h[r - 1][r - 1]);
+                h[r][r - 1] = sel(act, cx<T>{T(0), T(0)}, h[r][r - 1]);
+#pragma unroll
+                for (int j = r; j < N; ++j)
+                    if (j < M) rot_rows(c[r], s[r], h[r - 1][j], h[r][j]);
+            }
+        }
+        // right rotations Q_r^H: columns r-1, r over rows 0..r
+#pragma unroll
+        for (int r = 1; r < N; ++r) {
+            if (r < M) {
+#pragma unroll
+                for (int i = 0; i <= r; ++i) rot_cols(c[r], s[r], h[i][r - 1], h[i][r]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (i < M) {
+                bool a = i < m;
+                h[i][i].re += a ? shift.re : T(0);
+                h[i][i].im += a ? shift.im : T(0);
+            }
+    }
 }
 
 // Trailing 2x2 of the active block [[a, b], [c, d]] for this lane's m.
