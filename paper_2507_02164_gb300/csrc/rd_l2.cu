@@ -169,10 +169,31 @@ __global__ void __launch_bounds__(256) l2_kernel(const double2 *__restrict__ sam
 // beyond FP32) and split into hi + lo floats with integer operations, then
 // the scale is applied back to the FP64 coefficients exactly.
 
+// The radial weights are stored as (w, w) pairs: the real and imaginary
+// parts of a sample go through the same operations with the same weight, as
+// the two halves of packed FP32 instructions (FFMA2 / FMUL2 / FADD2, each
+// half rounded as its scalar form), one issue slot for both.
 struct L2TablesDF {
-    float whi[L2_MAX_NR][L2_MAX_DEG + 1], wlo[L2_MAX_NR][L2_MAX_DEG + 1];
+    float2 whi[L2_MAX_NR][L2_MAX_DEG + 1], wlo[L2_MAX_NR][L2_MAX_DEG + 1];
     float thi[L2_MAX_DEG + 1][L2_NT][2], tlo[L2_MAX_DEG + 1][L2_NT][2];
 };
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(r)
+        : "l"(*reinterpret_cast<const unsigned long long *>(&a)), "l"(*reinterpret_cast<const unsigned long long *>(&b)));
+    return *reinterpret_cast<const float2 *>(&r);
+}
+
+// two_sum on both halves: s = a + b and its exact rounding error e
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e)
+{
+    s = __fadd2_rn(a, b);
+    const float2 bb = sub2(s, a);
+    e = __fadd2_rn(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
 
 // NR > 0, DEG >= 0: a build for that radial node count and degree (loops of
 // fixed length, arrays of DEG + 1 coefficients); NR = 0, DEG = -1: the runtime
@@ -206,31 +227,35 @@ __global__ void __launch_bounds__(256, 2) l2_kernel_df(const double2 *__restrict
         }
         emax = __reduce_max_sync(0xffffffffu, emax);
         const int shift = (int)emax - 1023;
-        dfl ur[JMAX + 1], ui[JMAX + 1];
+        // accumulators as (real, imaginary) pairs: ah[j] the high parts, al[j] the low
+        float2 ah[JMAX + 1], al[JMAX + 1];
 #pragma unroll
-        for (int j = 0; j <= JMAX; ++j) ur[j] = ui[j] = dfl{0.0f, 0.0f};
+        for (int j = 0; j <= JMAX; ++j) ah[j] = al[j] = make_float2(0.0f, 0.0f);
 #pragma unroll 4
         for (int p = 0; p < nr; ++p) {
             double2 v = __ldg(g + p * L2_NT + lane);
-            dfl gx = split_scaled(v.x, shift), gy = split_scaled(v.y, shift);
+            const dfl gx = split_scaled(v.x, shift), gy = split_scaled(v.y, shift);
+            const float2 gh = make_float2(gx.hi, gy.hi), gl = make_float2(gx.lo, gy.lo);
 #pragma unroll
             for (int j = 0; j <= JMAX; ++j)
                 if (j <= degree) {
-                    const float wh = T.whi[p][j], wl = T.wlo[p][j];
+                    const float2 wh = T.whi[p][j], wl = T.wlo[p][j];
                     // exact product hi and its error, then TwoSum into the accumulator
-                    float ph = __fmul_rn(wh, gx.hi);
-                    float pe = __fmaf_rn(wh, gx.hi, -ph);
-                    pe = __fmaf_rn(wh, gx.lo, pe);
-                    pe = __fmaf_rn(wl, gx.hi, pe);
-                    dfl t = two_sum(ur[j].hi, ph);
-                    ur[j] = {t.hi, __fadd_rn(ur[j].lo, __fadd_rn(t.lo, pe))};
-                    ph = __fmul_rn(wh, gy.hi);
-                    pe = __fmaf_rn(wh, gy.hi, -ph);
-                    pe = __fmaf_rn(wh, gy.lo, pe);
-                    pe = __fmaf_rn(wl, gy.hi, pe);
-                    t = two_sum(ui[j].hi, ph);
-                    ui[j] = {t.hi, __fadd_rn(ui[j].lo, __fadd_rn(t.lo, pe))};
+                    const float2 ph = __fmul2_rn(wh, gh);
+                    float2 pe = __ffma2_rn(wh, gh, make_float2(-ph.x, -ph.y));
+                    pe = __ffma2_rn(wh, gl, pe);
+                    pe = __ffma2_rn(wl, gh, pe);
+                    float2 t, te;
+                    two_sum2(ah[j], ph, t, te);
+                    ah[j] = t;
+                    al[j] = __fadd2_rn(al[j], __fadd2_rn(te, pe));
                 }
+        }
+        dfl ur[JMAX + 1], ui[JMAX + 1];
+#pragma unroll
+        for (int j = 0; j <= JMAX; ++j) {
+            ur[j] = {ah[j].x, al[j].x};
+            ui[j] = {ah[j].y, al[j].y};
         }
 #pragma unroll
         for (int j0 = 0; j0 <= JMAX; j0 += 8) {
@@ -284,8 +309,9 @@ int launch_l2(const double *samples, int64_t n, int nr, int degree, double *coef
             for (int j = 0; j <= L2_MAX_DEG; ++j) {
                 double v = 0.0;
                 if (p < nr && j <= degree) v = w[p] * std::pow(r[p], j + 1) * (2.0 * pi / L2_NT) * (j + 1) / pi;
-                T.whi[p][j] = (float)v;
-                T.wlo[p][j] = (float)(v - (double)T.whi[p][j]);
+                const float h = (float)v, l = (float)(v - (double)h);
+                T.whi[p][j] = make_float2(h, h);
+                T.wlo[p][j] = make_float2(l, l);
             }
         for (int j = 0; j <= L2_MAX_DEG; ++j)
             for (int q = 0; q < L2_NT; ++q) {
