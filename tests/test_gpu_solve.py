@@ -10,7 +10,7 @@ import pytest
 import torch
 
 from paper_2507_02164_gb300 import api, workloads as WL
-from tests.gpu_common import (check_rejected, compare_roots, edge_distance, hist_np, require_gpu,
+from tests.gpu_common import (check_rejected, compare_roots, edge_distance, hist_np, matched, require_gpu,
                               roots_poly_major, to_soa)
 
 pytestmark = pytest.mark.gpu
@@ -182,6 +182,46 @@ def test_launch_shapes_give_identical_results(dev):
     for block, cps in ((32, 1), (64, 3), (256, 2)):
         r, s, _, _ = _solve(co, "mixed", block=block, ctas_per_sm=cps)
         assert np.array_equal(r, base) and np.array_equal(s, bst)
+
+
+@pytest.mark.parametrize("mode,tol,kcap", [("plain", PLAIN_TOL, KAPPA_PLAIN), ("mixed", MIXED_TOL, KAPPA_MIXED)])
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_roots_at_zero(dev, orc, mode, tol, kcap, k):
+    """p(z) = z^k q(z) (a_0 = .. = a_{k-1} = 0 exactly, q of degree 6 - k with
+    complex-Gaussian coefficients). k = 1: a simple zero root, held to the
+    bar with the others. k >= 2: a k-fold zero. Newton's method converges to
+    it only linearly, so the mixed path's FP64 residual check fails and the
+    polynomial is REJECTED (the condition number as the oracle defines it
+    stays O(1) at a multiple root, so the rule that a rejected polynomial has
+    a root with kappa > 100 does not apply here). The plain path returns the
+    k copies within the eigenvalue perturbation bound eps^(1/k) of 0, and q's
+    roots within 1e-9 of the oracle's (beside the zero cluster the FP64
+    eigenvalue computation of both carries the cluster's splitting into its
+    rounding: measured up to 7e-10 relative to kappa)."""
+    g = np.random.default_rng(40 + k)
+    n = 4096
+    co = np.zeros((n, 7), dtype=np.complex128)
+    co[:, k:] = g.standard_normal((n, 7 - k)) + 1j * g.standard_normal((n, 7 - k))
+    roots, status, _, _ = _solve(to_soa(co, dev), mode)
+    ref, ref_status, _, _ = orc.solve(co, tol=1e-13)
+    assert np.all(status != 1) and np.all(status != 3)
+    if k == 1:
+        check_rejected(co, status, ref, orc)
+        ok = status == 0
+        assert ok.mean() >= 1 - MAX_REJECTED
+        compare_roots(roots[ok], ref[ok], co[ok], orc, tol, kcap)
+        assert np.abs(roots[ok]).min(axis=1).max() <= tol
+        return
+    if mode == "mixed":
+        assert np.all(status == 2), np.bincount(status, minlength=4)
+        return
+    assert np.all(status == 0)
+    by_size = lambda z: np.take_along_axis(z, np.argsort(np.abs(z), axis=1), axis=1)
+    g_, r = by_size(roots), by_size(ref)
+    assert np.abs(g_[:, :k]).max() <= {2: 1e-6, 3: 1e-4}[k], float(np.abs(g_[:, :k]).max())
+    gq = matched(g_[:, k:], r[:, k:])
+    err = np.abs(gq - r[:, k:]) / np.maximum(1.0, np.abs(r[:, k:]))
+    assert err.max() <= 1e-9, float(err.max())
 
 
 @pytest.mark.parametrize("mode", ["mixed", "plain"])
