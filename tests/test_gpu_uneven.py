@@ -68,6 +68,31 @@ def test_uneven_batch_matches_oracle(dev, orc, mode, dtype):
     assert st["status_ok"] == int((s == 0).sum())
 
 
+@pytest.mark.parametrize("mode,dtype,polish", [("mixed", torch.complex128, "fp64"), ("plain", torch.complex64, "fp64"),
+                                               ("mixed", torch.complex64, "df")])
+def test_uneven_degrees_one_to_twelve(dev, orc, mode, dtype, polish):
+    """Every degree 1..12 in one packed batch (degree 1 included, which the
+    benchmark's 2..12 mix leaves out), in the storage / precision pairs the
+    other parity test does not cover, and the compensated polish."""
+    g = np.random.default_rng(29)
+    n = 6000 + 7
+    deg = g.integers(1, 13, n).astype(np.uint8)
+    off = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(deg.astype(np.int64) + 1, out=off[1:])
+    npd = np.complex64 if dtype == torch.complex64 else np.complex128
+    packed = (g.standard_normal(int(off[-1])) + 1j * g.standard_normal(int(off[-1]))).astype(npd)
+    c_t = torch.from_numpy(packed).to(dev)
+    ws = api.new_uneven_workspace(n, packed.size, dtype, dev)
+    p = api.params(mode, polish_mode=polish) if mode == "mixed" else api.params(mode)
+    roots, status = api.roots_uneven(c_t, torch.from_numpy(deg).to(dev), torch.from_numpy(off).to(dev), ws,
+                                     mode=mode, params_=p)
+    torch.cuda.synchronize()
+    tol, kcap = (1e-9, 1e3) if mode == "mixed" else (1e-11, 100.0)
+    _check_against_oracle(orc, packed.astype(np.complex128), deg, off, roots.cpu().numpy(), status.cpu().numpy(),
+                          tol, kcap)
+    assert set(np.unique(deg).tolist()) == set(range(1, 13))
+
+
 def test_invalid_degrees_and_offsets(dev, orc):
     packed, deg, off = WL.uneven_gaussian(3, 200)
     deg = deg.copy()
